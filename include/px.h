@@ -1,0 +1,217 @@
+/*
+ * px.h -- C ABI of the GB300 (sm_103a) wFQ / wFQFmu linear-response library.
+ *
+ * The library solves, for every frequency w of a sweep and every field
+ * polarisation e, the complex linear system of the wFQ model (Eq. 1)
+ *
+ *     [ Kbar T^qq - z_q(w) I_N ] q(w) = -Kbar V(w)
+ *
+ * or of the wFQFmu model (Eq. 7)
+ *
+ *     [ diag(Kbar, I_3N) T - diag(z_q(w) I_N, z_mu(w) I_3N) ] (q; mu)
+ *                                         = diag(Kbar, I_3N) (-V; E),
+ *
+ * with K the Fermi-damped Drude bond weights (Eq. 3, Eq. 4), Kbar its Laplacian
+ * form (Eq. 2), T the Gaussian-smeared Coulomb kernels (Eq. 5 and its
+ * derivatives, Sec. 2.2), z_q the Drude shift (Eq. 6) and z_mu = -1/alpha^IB
+ * (Eq. 8), and returns the induced charges and dipoles, the complex
+ * polarisability alpha_kl = d d_k / d E_l with d = sum q_i r_i (+ sum mu_i) and
+ * the absorption cross-section 4 pi w / (3c) Tr Im alpha (Sec. "Observables").
+ *
+ * All frequencies and polarisations of one call form one block of right-hand
+ * sides that is solved together on the GPU (restarted GMRES with FP64
+ * orthogonalisation and FP64 true-residual refinement around a low-precision
+ * block matvec; Sec. "Solvers" describes the per-frequency GMRES this batches).
+ *
+ * Conventions for every function below:
+ *   - Every function returns px_status; none aborts, throws or exits.
+ *   - Inputs are read (and copied where the handle keeps them) during the call;
+ *     the caller keeps ownership of every buffer it passes.
+ *   - Outputs go to caller-allocated buffers; a NULL output pointer skips that
+ *     output.
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - Units at the boundary: Angstrom for positions, eV for frequencies,
+ *     atomic units for everything else (bohr, hartree, bohr^3 for alpha, bohr^2
+ *     for cross-sections).  Inside, everything is in atomic units.
+ *   - On failure px_last_error(h) holds a human-readable message.
+ *   - One handle must not be used by two host threads at the same time.
+ */
+#ifndef PX_H
+#define PX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PX_ABI_VERSION 1
+
+typedef enum {
+  PX_OK = 0,
+  PX_EINVAL = 1,     /* bad argument: NULL where required, size <= 0, NaN, duplicate atoms */
+  PX_ENOMEM = 2,     /* device allocation failed or the HBM budget is exceeded */
+  PX_ENOTCONV = 3,   /* at least one column missed the tolerance; see status[] */
+  PX_ETIMEOUT = 4,   /* a bounded wait ran out */
+  PX_ECUDA = 5,      /* a CUDA runtime call failed (message in px_last_error) */
+  PX_EBUSY = 6,      /* the server queue is full */
+  PX_ENOTIMPL = 7,   /* valid request that this build does not support */
+  PX_ENOTFOUND = 8   /* unknown request id */
+} px_status;
+
+typedef enum { PX_WFQ = 0, PX_WFQFMU = 1 } px_model;
+
+/* Arithmetic of the block matvec Y = T X inside the Krylov iteration.  The
+ * orthogonalisation, the true residual and the refinement are FP64 in every
+ * mode. */
+typedef enum {
+  PX_FP64 = 0,       /* FP64 matvec (plain double-precision solve) */
+  PX_FP32 = 1,       /* FP32 matvec on the CUDA cores */
+  PX_BF16SPLIT = 2   /* T = T_hi + T_lo, X = X_hi + X_lo in bf16; tcgen05 MMA with FP32
+                        accumulation of T_hi X_hi + T_hi X_lo + T_lo X_hi */
+} px_precision;
+
+typedef enum {
+  PX_MODE_AUTO = 0,         /* materialise T if it fits the HBM budget, else matrix-free */
+  PX_MODE_MATFREE = 1,      /* generate T tiles on the fly inside the matvec ("on the fly") */
+  PX_MODE_MATERIALISED = 2  /* store T once per structure ("on memory") */
+} px_mode;
+
+/* Per-atom-type parameters (Eqs. 3-6 and the Gaussian widths of Secs. 2.1, 2.2).
+ * Pair values of r0, d and s are the arithmetic means of the two atoms' types. */
+typedef struct {
+  double r0_ang;      /* nearest-neighbour distance r^0 of the lattice, Angstrom (Eq. 4) */
+  double d;           /* Fermi steepness d (Eq. 4) */
+  double s;           /* Fermi scale s (Eq. 4) */
+  double area_bohr2;  /* effective area A_i, bohr^2, > 0 (Eq. 3) */
+  double Rq_bohr;     /* Gaussian charge width R_q, bohr, > 0 (Sec. 2.1) */
+  double Rmu_bohr;    /* Gaussian dipole width R_mu, bohr, > 0 (Sec. 2.2; wFQFmu only) */
+  double drude_n_au;  /* density n of Eq. 6, a.u., > 0; equal for all types */
+  double tau_au;      /* scattering time tau of Eq. 6, a.u., > 0; equal for all types */
+} px_atom_type;
+
+typedef struct {
+  int precision;            /* px_precision; default PX_FP32 */
+  int mode;                 /* px_mode; default PX_MODE_AUTO */
+  int restart_m;            /* Krylov basis length per restart cycle; default 100 */
+  int max_iter;             /* cap on matvecs per column over the whole solve; default 20000 */
+  int max_cycles;           /* cap on restart/refinement cycles; default 200 */
+  int gs_passes;            /* Gram-Schmidt passes (1 = CGS, 2 = CGS2); default 2 */
+  double tol_rel;           /* per-column target ||b - A x||_2 / ||b||_2 in FP64; default 1e-7 */
+  double inner_tol;         /* per-cycle reduction asked of the low-precision inner
+                               iteration (ignored in PX_FP64); default 1e-4 */
+  double kcut_eps;          /* keep bond pairs with 1 - f(r) >= kcut_eps; default 1e-6 */
+  int mu_self_term;         /* 1: Gaussian self term on the T^mumu diagonal; default 0 */
+  int profile;              /* 1: time every matvec launch with CUDA events; default 0 */
+  size_t hbm_budget_bytes;  /* device memory the handle may use; 0 = 90% of free memory */
+  double device_wait_limit_s; /* bound on any host wait for device progress; default 600 */
+} px_options;
+
+/* Host-side results of px_solve.  F = n_freq, P = n_pol, N = n_atoms.  Column
+ * (f, p) is one spectrum point.  Every pointer may be NULL. */
+typedef struct {
+  double* alpha;         /* [F][3][P] complex: alpha_kp = d_k / E0 for field along pol p */
+  double* sigma_abs;     /* [F]: 4 pi w/(3c) sum_p Im alpha_pp; only when P == 3 */
+  double* sigma_abs_pol; /* [F][P]: 4 pi w / c Im(e_p . alpha e_p) */
+  double* q;             /* [F][P][N] complex induced charges, caller's atom order */
+  double* mu;            /* [F][P][N][3] complex induced dipoles (wFQFmu) */
+  double* rel_residual;  /* [F][P]: final ||b - A x|| / ||b||, FP64 */
+  int* iters;            /* [F][P]: low-precision matvecs spent on the column */
+  int* status;           /* [F][P]: PX_OK or PX_ENOTCONV */
+} px_result;
+
+/* Timing and work counters of the last px_solve on a handle. */
+typedef struct {
+  double setup_ms;         /* px_set_structure device time (neighbour list, T build) */
+  double solve_ms;         /* px_solve device time, staging to observables */
+  double matvec_ms;        /* summed CUDA-event durations of the low-precision matvec
+                              launches (only with options.profile) */
+  long long matvec_launches;
+  double matvec_flops;     /* algorithmic flops of those launches: 4 n_u^2 B_active each */
+  double matvec_bytes;     /* algorithmic bytes of those launches (T once + X + Y) */
+  double resid_ms;         /* summed durations of the FP64 true-residual matvecs (profile) */
+  long long resid_launches;
+  double resid_flops;
+  long long kernel_launches; /* every kernel this library launched in the last px_solve */
+  int cycles;              /* restart/refinement cycles run */
+  long long total_iters;   /* sum over cycles of the inner iterations run */
+  long long n_unknowns;    /* n_u: N (wFQ) or 4N (wFQFmu) */
+  int used_mode;           /* px_mode actually used */
+  int used_precision;      /* px_precision actually used */
+} px_stats;
+
+typedef struct px_handle px_handle;
+
+/* Library ABI version (PX_ABI_VERSION). */
+int px_abi_version(void);
+
+/* Fill *opt with the defaults listed in px_options.  PX_EINVAL if opt is NULL. */
+px_status px_options_default(px_options* opt);
+
+/* Create a handle on the current CUDA device.  opt may be NULL (defaults).
+ * The handle owns all device memory it allocates and one CUDA stream.
+ * PX_EINVAL for bad options, PX_ECUDA if no device is usable. */
+px_status px_create(px_handle** h, const px_options* opt);
+
+/* Replace the handle's options (validated as in px_create). */
+px_status px_set_options(px_handle* h, const px_options* opt);
+
+/* Load a structure (Sec. "Specify the Nanostructure": atom positions in
+ * Angstrom) and build its device-resident operators: the CSR of K (Eq. 3) with
+ * the diagonal of Kbar (Eq. 2), and T (Eq. 5, Sec. 2.2) in the storage the
+ * options select.
+ *   model     PX_WFQ (n_u = N unknowns) or PX_WFQFMU (n_u = 4N).
+ *   xyz_ang   [n_atoms][3] doubles, Angstrom.
+ *   type_idx  [n_atoms] ints in [0, n_types).
+ *   types     [n_types] parameter records (all share drude_n_au and tau_au).
+ * Errors: PX_EINVAL (NULL, n_atoms < 1, bad type index, non-finite or
+ * non-positive parameter, two atoms closer than 1e-6 Angstrom), PX_ENOMEM,
+ * PX_ECUDA.  Synchronous: returns after the device work finished. */
+px_status px_set_structure(px_handle* h, px_model model, int n_atoms, const double* xyz_ang,
+                           const int* type_idx, const px_atom_type* types, int n_types);
+
+/* Solve the loaded structure for every (frequency, polarisation) column and
+ * write the observables (Sec. "Observables") to host buffers.
+ *   n_freq, omega_ev  [n_freq] frequencies in eV, > 0.
+ *   alpha_ib          [n_types][n_freq] complex interband polarisabilities
+ *                     alpha^IB(w), a.u. (Eq. 8); required for PX_WFQFMU,
+ *                     ignored (may be NULL) for PX_WFQ.
+ *   n_pol, pol_dir    [n_pol][3] unit field directions.
+ *   e0                field amplitude E0, a.u. (> 0; the response is linear).
+ *   out               host result buffers (see px_result).
+ *   cuda_stream       cudaStream_t to order the work on, or NULL for the
+ *                     handle's own stream.  The call is synchronous.
+ * Returns PX_OK, or PX_ENOTCONV when some column missed options.tol_rel within
+ * the iteration caps (its status[] entry says so; its outputs hold the last
+ * iterate), PX_EINVAL, PX_ENOMEM, PX_ECUDA, PX_ETIMEOUT. */
+px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const double* alpha_ib,
+                   int n_pol, const double* pol_dir, double e0, px_result* out,
+                   void* cuda_stream);
+
+/* Same computation, with the per-column results left in DEVICE memory owned by
+ * the caller (for callers that keep results on the GPU, e.g. PyTorch tensors):
+ *   d_alpha   device [F][3][P] complex (may be NULL)
+ *   d_q       device [F][P][N] complex (may be NULL)
+ *   d_mu      device [F][P][N][3] complex (may be NULL)
+ *   d_relres  device [F][P] doubles (may be NULL)
+ * Host-side inputs are as in px_solve.  Returns after the device work finished. */
+px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
+                          const double* alpha_ib, int n_pol, const double* pol_dir, double e0,
+                          double* d_alpha, double* d_q, double* d_mu, double* d_relres,
+                          void* cuda_stream);
+
+/* Counters of the last px_solve / px_set_structure. */
+px_status px_get_stats(const px_handle* h, px_stats* st);
+
+/* Release all device memory and the stream.  NULL is accepted. */
+px_status px_destroy(px_handle* h);
+
+/* Message of the last failure on h (or of the last failed px_create when h is
+ * NULL).  The string is owned by the library and valid until the next call on h. */
+const char* px_last_error(const px_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PX_H */

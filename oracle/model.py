@@ -366,7 +366,9 @@ def solve(st: Structure, model: str, omega_ev, pol_dirs, alpha_ib=None,
             zmu_atoms = z_mu(alpha_ib[st.type_idx, f])
             A = matrix_wfqfmu(Kb, T, zq, zmu_atoms)
         X = np.linalg.solve(A, B.astype(np.complex128))
-        relres[f] = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+        bn = np.linalg.norm(B, axis=0)
+        rn = np.linalg.norm(B - A @ X, axis=0)
+        relres[f] = np.where(bn > 0, rn / np.where(bn > 0, bn, 1.0), 0.0)
         q = X[:N]
         mu = X[N:].reshape(N, 3, P) if model == "wfqfmu" else None
         alpha[f] = dipole(st, q, mu) / e0

@@ -1,1 +1,160 @@
-"""GB300-native wFQ / wFQFmu plasmonic linear-response solver."""
+"""GB300-native wFQ / wFQFmu plasmonic linear-response solver.
+
+Python front-end of the px C library (include/px.h).  The classes here only
+marshal arguments; every step of the solve runs in the library's CUDA kernels.
+
+    from paper_2510_12731_gb300 import Solver, structures
+    w = structures.ag_sphere_791()
+    with Solver(precision="fp64") as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib)
+    out["alpha"]        # (F, 3, P) complex polarisability, bohr^3
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["Solver", "PxError", "options"]
+
+PxError = L.PxError
+
+
+def options(**kw) -> L.Options:
+    """A px_options record: library defaults, overridden by keyword arguments.
+
+    Keywords: precision ("fp64" | "fp32" | "bf16split"), mode ("auto" |
+    "matfree" | "materialised"), restart_m, max_iter, max_cycles, gs_passes,
+    tol_rel, inner_tol, kcut_eps, mu_self_term, profile, hbm_budget_bytes,
+    device_wait_limit_s.
+    """
+    o = L.Options()
+    L.lib().px_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision":
+            v = L.PRECISIONS[v] if isinstance(v, str) else int(v)
+        elif k == "mode":
+            v = L.MODES[v] if isinstance(v, str) else int(v)
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One px handle: a loaded structure and its device-resident operators."""
+
+    def __init__(self, **opts):
+        self._lib = L.lib()
+        self._h = C.c_void_p()
+        self._opt = options(**opts)
+        st = self._lib.px_create(C.byref(self._h), C.byref(self._opt))
+        if st != L.PX_OK:
+            raise PxError(st, self._lib.px_last_error(None).decode())
+        self.model = None
+        self.natoms = 0
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self):
+        if self._h:
+            self._lib.px_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != L.PX_OK and st not in allow:
+            raise PxError(st, self._lib.px_last_error(self._h).decode())
+        return st
+
+    # ------------------------------------------------------------------ calls
+    def set_options(self, **opts):
+        self._opt = options(**opts)
+        self._check(self._lib.px_set_options(self._h, C.byref(self._opt)))
+
+    def set_structure(self, model, xyz_ang, type_idx, types):
+        xyz = np.ascontiguousarray(xyz_ang, dtype=np.float64).reshape(-1, 3)
+        tidx = np.ascontiguousarray(type_idx, dtype=np.int32).reshape(-1)
+        tarr = (L.AtomType * len(types))(*[
+            L.AtomType(**{k: float(t[k]) for k in (f for f, _ in L.AtomType._fields_)})
+            for t in types])
+        m = L.MODELS[model] if isinstance(model, str) else int(model)
+        self._check(self._lib.px_set_structure(self._h, m, xyz.shape[0], L.dptr(xyz), L.iptr(tidx),
+                                               tarr, len(types)))
+        self.model = m
+        self.natoms = xyz.shape[0]
+
+    def solve(self, omega_ev, pol_dirs, alpha_ib=None, e0=1.0, want_q=True, want_mu=True,
+              stream=None):
+        """Solve every (frequency, polarisation) column; returns a dict of numpy arrays.
+
+        alpha (F, 3, P) complex, sigma_abs (F,) [P == 3], sigma_abs_pol (F, P),
+        q (F, P, N) complex, mu (F, P, N, 3) complex [wFQFmu], rel_residual (F, P),
+        iters (F, P), status (F, P), ok (bool: every column met tol_rel).
+        """
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
+        pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        F, P, N = w.size, pol.shape[0], self.natoms
+        aib = None
+        if alpha_ib is not None:
+            aib = np.ascontiguousarray(np.asarray(alpha_ib, dtype=np.complex128)).view(np.float64)
+        alpha = np.zeros((F, 3, P), dtype=np.complex128)
+        sig = np.zeros(F)
+        sigp = np.zeros((F, P))
+        q = np.zeros((F, P, N), dtype=np.complex128) if want_q else None
+        mu = (np.zeros((F, P, N, 3), dtype=np.complex128)
+              if (want_mu and self.model == L.PX_WFQFMU) else None)
+        rr = np.zeros((F, P))
+        it = np.zeros((F, P), dtype=np.int32)
+        stt = np.zeros((F, P), dtype=np.int32)
+        res = L.Result(alpha.view(np.float64).ctypes.data_as(L._dp), L.dptr(sig), L.dptr(sigp),
+                       q.view(np.float64).ctypes.data_as(L._dp) if q is not None else None,
+                       mu.view(np.float64).ctypes.data_as(L._dp) if mu is not None else None,
+                       L.dptr(rr), L.iptr(it), L.iptr(stt))
+        st = self._lib.px_solve(self._h, F, L.dptr(w), L.dptr(aib) if aib is not None else None, P,
+                                L.dptr(pol), float(e0), C.byref(res),
+                                C.c_void_p(stream) if stream else None)
+        self._check(st, allow=(L.PX_ENOTCONV,))
+        out = {"alpha": alpha, "sigma_abs_pol": sigp, "q": q, "mu": mu, "rel_residual": rr,
+               "iters": it, "status": stt, "ok": st == L.PX_OK}
+        if P == 3:
+            out["sigma_abs"] = sig
+        return out
+
+    def solve_device(self, omega_ev, pol_dirs, alpha_ib=None, e0=1.0, d_alpha=None, d_q=None,
+                     d_mu=None, d_relres=None, stream=None):
+        """Solve with results written to caller-owned device buffers (e.g. torch tensors).
+
+        Each d_* argument is an object with ``data_ptr()`` (a CUDA tensor of the right
+        size, float64 / complex128) or None.  Returns True when every column met tol_rel.
+        """
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
+        pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        aib = None
+        if alpha_ib is not None:
+            aib = np.ascontiguousarray(np.asarray(alpha_ib, dtype=np.complex128)).view(np.float64)
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        st = self._lib.px_solve_device(self._h, w.size, L.dptr(w),
+                                       L.dptr(aib) if aib is not None else None, pol.shape[0],
+                                       L.dptr(pol), float(e0), ptr(d_alpha), ptr(d_q), ptr(d_mu),
+                                       ptr(d_relres), C.c_void_p(stream) if stream else None)
+        self._check(st, allow=(L.PX_ENOTCONV,))
+        return st == L.PX_OK
+
+    def stats(self) -> dict:
+        s = L.Stats()
+        self._check(self._lib.px_get_stats(self._h, C.byref(s)))
+        return s.as_dict()

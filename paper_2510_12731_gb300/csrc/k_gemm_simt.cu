@@ -1,0 +1,171 @@
+// Block matvec Y = T X on the CUDA cores (FP32 and FP64), T materialised.
+//
+// T is symmetric, so the rows of T are also its columns: the A-tile of the
+// product, T[i0:i0+BM][k0:k0+BK], is read as BK contiguous row segments
+// T[k][i0:i0+BM] -- the same access pattern as the X tile X[k][c0:c0+BN].  Both
+// tiles are staged into shared memory with 16-byte cp.async copies, double
+// buffered.  Operands are zero padded to multiples of 128 (rows, columns, K), so
+// the kernels need no bounds checks.
+#include "px_internal.cuh"
+
+namespace px {
+
+namespace {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// FP32: BM = BN = 128, BK = 16, 256 threads, 8 x 8 outputs per thread arranged as
+// rows {ty*4 + r, 64 + ty*4 + r} and columns {tx*4 + c, 64 + tx*4 + c}.
+__global__ void __launch_bounds__(256, 2)
+k_sgemm(const float* __restrict__ T, int ldt, const float* __restrict__ X, int ldx,
+        float* __restrict__ Y, int ldy, int K) {
+  constexpr int BM = 128, BN = 128, BK = 16;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  const float* Ab = T + i0;
+  const float* Bb = X + c0;
+
+  auto load = [&](int st, int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int idx = tid + r * 256;
+      int kk = idx >> 5, cc = (idx & 31) * 4;
+      cp_async16(&As[st][kk][cc], Ab + (size_t)(k0 + kk) * ldt + cc);
+      cp_async16(&Bs[st][kk][cc], Bb + (size_t)(k0 + kk) * ldx + cc);
+    }
+    cp_async_commit();
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+
+  const int nk = K / BK;
+  load(0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) {
+      load((kt + 1) & 1, (kt + 1) * BK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int st = kt & 1;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&As[st][kk][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&As[st][kk][64 + ty * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&Bs[st][kk][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&Bs[st][kk][64 + tx * 4]);
+      float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    int row = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+    float* yr = Y + (size_t)row * ldy + c0;
+    *reinterpret_cast<float4*>(yr + tx * 4) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    *reinterpret_cast<float4*>(yr + 64 + tx * 4) =
+        make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+  }
+}
+
+// FP64: BM = BN = 64, BK = 16, 256 threads, 4 x 4 outputs per thread at rows
+// {ty*2 + r, 32 + ty*2 + r} and columns {tx*2 + c, 32 + tx*2 + c}.
+__global__ void __launch_bounds__(256)
+k_dgemm(const double* __restrict__ T, int ldt, const double* __restrict__ X, int ldx,
+        double* __restrict__ Y, int ldy, int K) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ __align__(16) double As[2][BK][BM];
+  __shared__ __align__(16) double Bs[2][BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  const double* Ab = T + i0;
+  const double* Bb = X + c0;
+  auto load = [&](int st, int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int idx = tid + r * 256;          // 512 16-byte chunks = 16 rows x 32 chunks
+      int kk = idx >> 5, cc = (idx & 31) * 2;
+      cp_async16(&As[st][kk][cc], Ab + (size_t)(k0 + kk) * ldt + cc);
+      cp_async16(&Bs[st][kk][cc], Bb + (size_t)(k0 + kk) * ldx + cc);
+    }
+    cp_async_commit();
+  };
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  const int nk = K / BK;
+  load(0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) {
+      load((kt + 1) & 1, (kt + 1) * BK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int st = kt & 1;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double2 a0 = *reinterpret_cast<const double2*>(&As[st][kk][ty * 2]);
+      double2 a1 = *reinterpret_cast<const double2*>(&As[st][kk][32 + ty * 2]);
+      double2 b0 = *reinterpret_cast<const double2*>(&Bs[st][kk][tx * 2]);
+      double2 b1 = *reinterpret_cast<const double2*>(&Bs[st][kk][32 + tx * 2]);
+      double a[4] = {a0.x, a0.y, a1.x, a1.y};
+      double b[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int row = i0 + (r < 2 ? ty * 2 + r : 32 + ty * 2 + (r - 2));
+    double* yr = Y + (size_t)row * ldy + c0;
+    *reinterpret_cast<double2*>(yr + tx * 2) = make_double2(acc[r][0], acc[r][1]);
+    *reinterpret_cast<double2*>(yr + 32 + tx * 2) = make_double2(acc[r][2], acc[r][3]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float* Y, int ldy,
+                         int ncols, cudaStream_t s, long long* nl) {
+  dim3 grd(ncols / 128, np / 128);
+  k_sgemm<<<grd, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
+                         int ncols, cudaStream_t s, long long* nl) {
+  dim3 grd(ncols / 64, np / 64);
+  k_dgemm<<<grd, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace px

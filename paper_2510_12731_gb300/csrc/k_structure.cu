@@ -1,0 +1,266 @@
+// Structure set-up kernels: neighbour list / CSR of K (Eqs. 2-4) and the dense
+// Gaussian kernels T (Eq. 5 and its derivatives, Sec. 2.2).  Run once per structure.
+#include "px_internal.cuh"
+
+namespace px {
+
+namespace {
+
+constexpr double kTwoOverSqrtPi = 1.1283791670955126;   // 2 / sqrt(pi)
+constexpr double kSqrt2OverPi = 0.7978845608028654;     // sqrt(2 / pi)
+
+__device__ __forceinline__ double dist2(const double* pos, int i, int j) {
+  double dx = pos[3 * i] - pos[3 * j];
+  double dy = pos[3 * i + 1] - pos[3 * j + 1];
+  double dz = pos[3 * i + 2] - pos[3 * j + 2];
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// One warp per row i; lanes sweep j.  A pair is kept when r_ij^2 <= rcut^2 of the
+// two atoms' types (1 - f(r) >= kcut_eps, Eq. 4).
+__global__ void k_neigh_count(const double* __restrict__ pos, int N, const int* __restrict__ type,
+                              int ntypes, const double* __restrict__ rcut2, int* counts) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  int i = warp, ti = type[i];
+  int cnt = 0;
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    int j = j0 + lane;
+    bool keep = false;
+    if (j < N && j != i) keep = dist2(pos, i, j) <= rcut2[ti * ntypes + type[j]];
+    cnt += __popc(__ballot_sync(0xffffffffu, keep));
+  }
+  if (lane == 0) counts[i] = cnt;
+}
+
+// Exclusive scan of counts into rowptr[0..N]; one block.
+__global__ void k_scan(const int* __restrict__ counts, int N, int* rowptr) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < N; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = (i < N) ? counts[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int nw = blockDim.x >> 5;
+      int w = (lane < nw) ? warp_sums[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int prefix = carry + (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+    if (i < N) rowptr[i] = prefix;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = prefix + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rowptr[N] = carry;
+}
+
+// Fill the CSR in increasing j order (deterministic): K_ij = [1 - f(r)] A_i / r (Eq. 3),
+// 1 - f(r) = 1 / (1 + exp[d (r / (s r0) - 1)]) (Eq. 4).
+__global__ void k_neigh_fill(const double* __restrict__ pos, int N, const int* __restrict__ type,
+                             int ntypes, const double* __restrict__ rcut2,
+                             const double* __restrict__ r0t, const double* __restrict__ dt,
+                             const double* __restrict__ st, const double* __restrict__ area,
+                             const int* __restrict__ rowptr, int* col, double* val64,
+                             float* val32) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  int i = warp, ti = type[i];
+  int base = rowptr[i];
+  double Ai = area[i];
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    int j = j0 + lane;
+    bool keep = false;
+    double r2 = 0.0;
+    int tp = 0;
+    if (j < N && j != i) {
+      tp = ti * ntypes + type[j];
+      r2 = dist2(pos, i, j);
+      keep = r2 <= rcut2[tp];
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      int off = __popc(m & ((1u << lane) - 1u));
+      double r = sqrt(r2);
+      double omf = 1.0 / (1.0 + exp(dt[tp] * (r / (st[tp] * r0t[tp]) - 1.0)));
+      double k = omf * Ai / r;
+      col[base + off] = j;
+      val64[base + off] = k;
+      val32[base + off] = (float)k;
+    }
+    base += __popc(m);
+  }
+}
+
+// T^qq (Eq. 5).  Thread per (i, j) atom pair.
+__global__ void k_build_Tqq(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
+                            int ld, double* T) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  double v;
+  if (i == j) {
+    v = kSqrt2OverPi / Rq[i];
+  } else {
+    double r = sqrt(dist2(pos, i, j));
+    double R = sqrt(Rq[i] * Rq[i] + Rq[j] * Rq[j]);
+    v = erf(r / R) / r;
+  }
+  T[(size_t)i * ld + j] = v;
+}
+
+struct Radial { double t0, t1, t2; };   // T, T', T'' of erf(r/R)/r at r
+__device__ __forceinline__ Radial radial(double r, double R) {
+  double x = r / R;
+  double e = erf(x);
+  double g = kTwoOverSqrtPi * exp(-x * x);
+  double ir = 1.0 / r;
+  Radial o;
+  o.t0 = e * ir;
+  o.t1 = (g * x - e) * ir * ir;
+  o.t2 = (2.0 * e - 2.0 * g * x - 2.0 * g * x * x * x) * ir * ir * ir;
+  return o;
+}
+
+// wFQFmu kernel blocks (Sec. 2.2), unknown order (q_1..q_N, mu_1x, mu_1y, mu_1z, ...):
+//   T^qmu_ij  = -T'(r; R_q,i mu,j) rhat           (row i, cols N+3j+b)
+//   T^muq_ij  = +T'(r; R_mu,i q,j) rhat           (rows N+3i+a, col j)
+//   T^mumu_ij = -[T'' rhat rhat + (T'/r)(I - rhat rhat)]   (R_mu,i mu,j)
+// with rhat = (r_i - r_j)/r.  Diagonals: T^qq self limit, T^qmu = T^muq = 0,
+// T^mumu = 0 or the Gaussian self term 4/(3 sqrt(pi) R^3) I, R = sqrt(2) R_mu.
+__global__ void k_build_T4(const double* __restrict__ pos, const double* __restrict__ Rq,
+                           const double* __restrict__ Rmu, int N, int ld, int mu_self,
+                           double* T) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  size_t rq = (size_t)i * ld;
+  if (i == j) {
+    T[rq + j] = kSqrt2OverPi / Rq[i];
+    double self = 0.0;
+    if (mu_self) {
+      double R = 1.4142135623730951 * Rmu[i];
+      double sq_pi = 1.7724538509055159;
+      self = 4.0 / (3.0 * sq_pi * R * R * R);
+    }
+    for (int a = 0; a < 3; ++a) {
+      T[rq + N + 3 * j + a] = 0.0;
+      size_t rm = (size_t)(N + 3 * i + a) * ld;
+      T[rm + j] = 0.0;
+      for (int b = 0; b < 3; ++b) T[rm + N + 3 * j + b] = (a == b) ? self : 0.0;
+    }
+    return;
+  }
+  double dx[3] = {pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1],
+                  pos[3 * i + 2] - pos[3 * j + 2]};
+  double r = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+  double rh[3] = {dx[0] / r, dx[1] / r, dx[2] / r};
+  double Rqq = sqrt(Rq[i] * Rq[i] + Rq[j] * Rq[j]);
+  double Rqm = sqrt(Rq[i] * Rq[i] + Rmu[j] * Rmu[j]);
+  double Rmq = sqrt(Rmu[i] * Rmu[i] + Rq[j] * Rq[j]);
+  double Rmm = sqrt(Rmu[i] * Rmu[i] + Rmu[j] * Rmu[j]);
+  T[rq + j] = erf(r / Rqq) / r;
+  Radial qm = radial(r, Rqm);
+  Radial mq = radial(r, Rmq);
+  Radial mm = radial(r, Rmm);
+  for (int b = 0; b < 3; ++b) T[rq + N + 3 * j + b] = -qm.t1 * rh[b];
+  for (int a = 0; a < 3; ++a) {
+    size_t rm = (size_t)(N + 3 * i + a) * ld;
+    T[rm + j] = mq.t1 * rh[a];
+    for (int b = 0; b < 3; ++b) {
+      double rr = rh[a] * rh[b];
+      double id = (a == b) ? 1.0 : 0.0;
+      T[rm + N + 3 * j + b] = -(mm.t2 * rr + (mm.t1 / r) * (id - rr));
+    }
+  }
+}
+
+__global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32,
+                            __nv_bfloat16* Thi, __nv_bfloat16* Tlo) {
+  size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; k < n; k += stride) {
+    double v = T64[k];
+    if (T32) T32[k] = (float)v;
+    if (Thi) {
+      __nv_bfloat16 hi = __double2bfloat16(v);
+      Thi[k] = hi;
+      Tlo[k] = __double2bfloat16(v - (double)__bfloat162float(hi));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_neigh_count(const double* pos, int N, const int* type, int ntypes,
+                               const double* rcut2, int* counts, cudaStream_t s, long long* nl) {
+  int threads = 256;
+  int blocks = (int)((N * 32LL + threads - 1) / threads);
+  k_neigh_count<<<blocks, threads, 0, s>>>(pos, N, type, ntypes, rcut2, counts);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int* counts, int N, int* rowptr, cudaStream_t s, long long* nl) {
+  k_scan<<<1, 1024, 0, s>>>(counts, N, rowptr);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_neigh_fill(const double* pos, int N, const int* type, int ntypes,
+                              const double* rcut2, const double* r0, const double* dd,
+                              const double* ss, const double* area, const int* rowptr,
+                              int* col, double* val64, float* val32, cudaStream_t s,
+                              long long* nl) {
+  int threads = 256;
+  int blocks = (int)((N * 32LL + threads - 1) / threads);
+  k_neigh_fill<<<blocks, threads, 0, s>>>(pos, N, type, ntypes, rcut2, r0, dd, ss, area, rowptr,
+                                          col, val64, val32);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream_t s,
+                             long long* nl) {
+  cudaError_t e = cudaMemsetAsync(d.T64, 0, sizeof(double) * (size_t)d.np * d.np, s);
+  if (e != cudaSuccess) return e;
+  dim3 blk(32, 8);
+  dim3 grd((d.N + 31) / 32, (d.N + 7) / 8);
+  if (d.model == 0)
+    k_build_Tqq<<<grd, blk, 0, s>>>(d.pos64, d.Rq, d.N, d.np, d.T64);
+  else
+    k_build_T4<<<grd, blk, 0, s>>>(d.pos64, d.Rq, d.Rmu, d.N, d.np, mu_self_term, d.T64);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool bf16, cudaStream_t s,
+                             long long* nl) {
+  size_t n = (size_t)d.np * d.np;
+  int threads = 256;
+  int blocks = 152 * 16;
+  k_convert_T<<<blocks, threads, 0, s>>>(d.T64, n, f32 ? d.T32 : nullptr,
+                                         bf16 ? d.Thi : nullptr, bf16 ? d.Tlo : nullptr);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace px

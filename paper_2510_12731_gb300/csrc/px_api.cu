@@ -1,0 +1,762 @@
+// C ABI of the px library (include/px.h): handle management, input validation,
+// structure set-up and the restarted-GMRES / refinement driver that sequences
+// the device kernels.  All arithmetic of the method runs in the kernels; the
+// host code here only validates, allocates, launches and reads back per-column
+// residual norms between restart cycles.
+#include "px.h"
+#include "px_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using px::round_up;
+
+namespace {
+
+constexpr double kBohrAng = 0.529177210903;     // CODATA 2018
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+struct PxError {
+  px_status st;
+  std::string msg;
+};
+
+}  // namespace
+
+struct px_handle {
+  px_options opt;
+  cudaStream_t own_stream = nullptr;
+  int device = 0;
+  std::string err;
+  px_stats stats;
+  bool have_structure = false;
+  px::DevStructure ds;
+  // structure buffers
+  DevBuf b_pos, b_Rq, b_Rmu, b_area, b_type, b_rowptr, b_col, b_val64, b_val32, b_counts;
+  DevBuf b_pair;   // rcut2, r0, d, s tables
+  DevBuf b_T64, b_T32, b_Thi, b_Tlo;
+  // solve buffers
+  DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
+  DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
+  DevBuf b_X32, b_Y32, b_X64, b_Y64;
+  DevBuf b_alpha, b_q, b_mu;
+  int* h_active = nullptr;      // pinned host copy of d_active [kMaxRestart]
+  int* d_active = nullptr;      // device: unfrozen columns after each Krylov step
+  std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_iter[2] = {nullptr, nullptr};
+  long long nl = 0;
+  double drude_n = 0.0, tau = 0.0;   // shared n, tau of the loaded structure (Eq. 6)
+};
+
+namespace {
+
+void free_all(px_handle* h) {
+  DevBuf* bufs[] = {&h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
+                    &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
+                    &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
+                    &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
+                    &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_alpha, &h->b_q, &h->b_mu};
+  for (DevBuf* b : bufs) b->release();
+}
+
+px_status validate_options(const px_options* o, std::string* msg) {
+  if (o->precision < PX_FP64 || o->precision > PX_BF16SPLIT) { *msg = "bad precision"; return PX_EINVAL; }
+  if (o->mode < PX_MODE_AUTO || o->mode > PX_MODE_MATERIALISED) { *msg = "bad mode"; return PX_EINVAL; }
+  if (o->restart_m < 1 || o->restart_m > px::kMaxRestart) { *msg = "restart_m must be in [1, 400]"; return PX_EINVAL; }
+  if (o->max_iter < 1 || o->max_cycles < 1) { *msg = "max_iter and max_cycles must be >= 1"; return PX_EINVAL; }
+  if (o->gs_passes < 1 || o->gs_passes > 2) { *msg = "gs_passes must be 1 or 2"; return PX_EINVAL; }
+  if (!(o->tol_rel > 0.0) || !(o->tol_rel < 1.0)) { *msg = "tol_rel must be in (0, 1)"; return PX_EINVAL; }
+  if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) { *msg = "inner_tol must be in (0, 1)"; return PX_EINVAL; }
+  if (!(o->kcut_eps >= 0.0) || !(o->kcut_eps < 0.5)) { *msg = "kcut_eps must be in [0, 0.5)"; return PX_EINVAL; }
+  if (!(o->device_wait_limit_s > 0.0)) { *msg = "device_wait_limit_s must be > 0"; return PX_EINVAL; }
+  return PX_OK;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw PxError{e_ == cudaErrorMemoryAllocation ? PX_ENOMEM : PX_ECUDA,          \
+                    std::string(#call) + ": " + cudaGetErrorString(e_)};             \
+  } while (0)
+
+px_status fail(px_handle* h, px_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+// Bounded wait for an event: poll with sleeps so a stuck device cannot hang the
+// caller forever.
+void wait_event(px_handle* h, cudaEvent_t ev) {
+  double limit = h->opt.device_wait_limit_s;
+  double waited = 0.0;
+  while (true) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return;
+    if (e != cudaErrorNotReady) CU(e);
+    if (waited > limit) throw PxError{PX_ETIMEOUT, "device did not finish within device_wait_limit_s"};
+    // short spin first, then back off
+    struct timespec ts = {0, waited < 0.01 ? 20000 : 200000};
+    nanosleep(&ts, nullptr);
+    waited += ts.tv_nsec * 1e-9;
+  }
+}
+
+void sync_stream(px_handle* h, cudaStream_t s) {
+  cudaEvent_t ev = h->ev_iter[0];
+  CU(cudaEventRecord(ev, s));
+  wait_event(h, ev);
+}
+
+cudaEvent_t pool_event(px_handle* h, size_t k) {
+  while (h->ev_pool.size() <= k) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[k];
+}
+
+// ------------------------------------------------------------------ structure
+void set_structure(px_handle* h, int model, int N, const double* xyz, const int* tidx,
+                   const px_atom_type* types, int ntypes) {
+  if (!xyz || !tidx || !types) throw PxError{PX_EINVAL, "NULL input"};
+  if (N < 1) throw PxError{PX_EINVAL, "n_atoms must be >= 1"};
+  if (ntypes < 1) throw PxError{PX_EINVAL, "n_types must be >= 1"};
+  if (model != PX_WFQ && model != PX_WFQFMU) throw PxError{PX_EINVAL, "bad model"};
+  for (int t = 0; t < ntypes; ++t) {
+    const px_atom_type& a = types[t];
+    double v[] = {a.r0_ang, a.d, a.s, a.area_bohr2, a.Rq_bohr, a.Rmu_bohr, a.drude_n_au, a.tau_au};
+    for (double x : v)
+      if (!std::isfinite(x) || !(x > 0.0)) throw PxError{PX_EINVAL, "atom type parameters must be finite and > 0"};
+    if (a.drude_n_au != types[0].drude_n_au || a.tau_au != types[0].tau_au)
+      throw PxError{PX_EINVAL, "all atom types must share drude_n_au and tau_au (Eq. 1 has one z_q)"};
+  }
+  std::vector<double> pos(3 * (size_t)N);
+  for (int i = 0; i < N; ++i) {
+    if (tidx[i] < 0 || tidx[i] >= ntypes) throw PxError{PX_EINVAL, "type index out of range"};
+    for (int k = 0; k < 3; ++k) {
+      double x = xyz[3 * (size_t)i + k];
+      if (!std::isfinite(x)) throw PxError{PX_EINVAL, "non-finite coordinate"};
+      pos[3 * (size_t)i + k] = x / kBohrAng;
+    }
+  }
+  // duplicate atoms: sort by x, compare within a 1e-6 Angstrom window
+  {
+    std::vector<int> ord(N);
+    for (int i = 0; i < N; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return xyz[3 * (size_t)a] < xyz[3 * (size_t)b]; });
+    const double eps = 1e-6;
+    for (int u = 0; u < N; ++u) {
+      const double* pa = xyz + 3 * (size_t)ord[u];
+      for (int v = u + 1; v < N; ++v) {
+        const double* pb = xyz + 3 * (size_t)ord[v];
+        if (pb[0] - pa[0] > eps) break;
+        double dx = pb[0] - pa[0], dy = pb[1] - pa[1], dz = pb[2] - pa[2];
+        if (dx * dx + dy * dy + dz * dz < eps * eps) throw PxError{PX_EINVAL, "two atoms closer than 1e-6 Angstrom"};
+      }
+    }
+  }
+  std::vector<double> Rq(N), Rmu(N), area(N);
+  for (int i = 0; i < N; ++i) {
+    const px_atom_type& a = types[tidx[i]];
+    Rq[i] = a.Rq_bohr;
+    Rmu[i] = a.Rmu_bohr;
+    area[i] = a.area_bohr2;
+  }
+  // pair tables: arithmetic means of the two types' r0, d, s; squared cutoff radius
+  // where 1 - f(r) = kcut_eps (infinite when kcut_eps == 0).
+  std::vector<double> pair(4 * (size_t)ntypes * ntypes);
+  double* rcut2 = pair.data();
+  double* r0t = rcut2 + ntypes * ntypes;
+  double* dt = r0t + ntypes * ntypes;
+  double* st = dt + ntypes * ntypes;
+  double eps = h->opt.kcut_eps;
+  for (int a = 0; a < ntypes; ++a)
+    for (int b = 0; b < ntypes; ++b) {
+      int k = a * ntypes + b;
+      r0t[k] = 0.5 * (types[a].r0_ang + types[b].r0_ang) / kBohrAng;
+      dt[k] = 0.5 * (types[a].d + types[b].d);
+      st[k] = 0.5 * (types[a].s + types[b].s);
+      if (eps > 0.0) {
+        double rc = st[k] * r0t[k] * (1.0 + std::log((1.0 - eps) / eps) / dt[k]);
+        rcut2[k] = rc * rc;
+      } else {
+        rcut2[k] = INFINITY;
+      }
+    }
+
+  cudaStream_t s = h->own_stream;
+  px::DevStructure& d = h->ds;
+  h->have_structure = false;
+  d.model = model;
+  d.N = N;
+  d.nu = model == PX_WFQ ? N : 4 * N;
+  d.np = (int)round_up(d.nu, px::kTile);
+  d.ntypes = ntypes;
+  h->nl = 0;
+  CU(cudaEventRecord(h->ev_a, s));
+  CU(h->b_pos.ensure(sizeof(double) * 3 * N));
+  CU(h->b_Rq.ensure(sizeof(double) * N));
+  CU(h->b_Rmu.ensure(sizeof(double) * N));
+  CU(h->b_area.ensure(sizeof(double) * N));
+  CU(h->b_type.ensure(sizeof(int) * N));
+  CU(h->b_rowptr.ensure(sizeof(int) * (N + 1)));
+  CU(h->b_counts.ensure(sizeof(int) * N));
+  CU(h->b_pair.ensure(sizeof(double) * pair.size()));
+  d.pos64 = h->b_pos.as<double>();
+  d.Rq = h->b_Rq.as<double>();
+  d.Rmu = h->b_Rmu.as<double>();
+  d.area = h->b_area.as<double>();
+  d.type = h->b_type.as<int>();
+  d.rowptr = h->b_rowptr.as<int>();
+  CU(cudaMemcpyAsync(d.pos64, pos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.Rq, Rq.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.Rmu, Rmu.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.area, area.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.type, tidx, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(h->b_pair.p, pair.data(), sizeof(double) * pair.size(), cudaMemcpyHostToDevice, s));
+  const double* dpair = h->b_pair.as<double>();
+  const double* d_rcut2 = dpair;
+  const double* d_r0 = dpair + ntypes * ntypes;
+  const double* d_d = d_r0 + ntypes * ntypes;
+  const double* d_s = d_d + ntypes * ntypes;
+
+  CU(px::launch_neigh_count(d.pos64, N, d.type, ntypes, d_rcut2, h->b_counts.as<int>(), s, &h->nl));
+  CU(px::launch_scan(h->b_counts.as<int>(), N, d.rowptr, s, &h->nl));
+  int nnz = 0;
+  CU(cudaMemcpyAsync(&nnz, d.rowptr + N, sizeof(int), cudaMemcpyDeviceToHost, s));
+  sync_stream(h, s);
+  d.nnz = nnz;
+  size_t nnz_alloc = std::max(nnz, 1);
+  CU(h->b_col.ensure(sizeof(int) * nnz_alloc));
+  CU(h->b_val64.ensure(sizeof(double) * nnz_alloc));
+  CU(h->b_val32.ensure(sizeof(float) * nnz_alloc));
+  d.col = h->b_col.as<int>();
+  d.val64 = h->b_val64.as<double>();
+  d.val32 = h->b_val32.as<float>();
+  CU(px::launch_neigh_fill(d.pos64, N, d.type, ntypes, d_rcut2, d_r0, d_d, d_s, d.area, d.rowptr,
+                           d.col, d.val64, d.val32, s, &h->nl));
+
+  // T storage: this version always materialises T (FP64 for the true residual and the
+  // FP64 matvec, FP32 / bf16 copies for the low-precision matvec).
+  int mode = h->opt.mode;
+  if (mode == PX_MODE_MATFREE) throw PxError{PX_ENOTIMPL, "matrix-free mode is not available in this build"};
+  size_t np2 = (size_t)d.np * d.np;
+  size_t need = np2 * sizeof(double);
+  if (h->opt.precision == PX_FP32) need += np2 * sizeof(float);
+  if (h->opt.precision == PX_BF16SPLIT) need += 2 * np2 * sizeof(__nv_bfloat16);
+  size_t budget = h->opt.hbm_budget_bytes;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    CU(cudaMemGetInfo(&fr, &tot));
+    budget = (size_t)(0.9 * (double)fr) + h->b_T64.bytes + h->b_T32.bytes + h->b_Thi.bytes + h->b_Tlo.bytes;
+  }
+  if (need > budget) throw PxError{PX_ENOMEM, "materialised T does not fit the HBM budget"};
+  if (h->opt.precision == PX_BF16SPLIT) throw PxError{PX_ENOTIMPL, "bf16-split matvec is not available in this build"};
+  CU(h->b_T64.ensure(np2 * sizeof(double)));
+  d.T64 = h->b_T64.as<double>();
+  d.T32 = nullptr;
+  d.Thi = d.Tlo = nullptr;
+  if (h->opt.precision == PX_FP32) {
+    CU(h->b_T32.ensure(np2 * sizeof(float)));
+    d.T32 = h->b_T32.as<float>();
+  }
+  CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
+  if (d.T32) CU(px::launch_convert_T(d, true, false, s, &h->nl));
+  CU(cudaEventRecord(h->ev_b, s));
+  wait_event(h, h->ev_b);
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
+  h->stats.setup_ms = ms;
+  h->stats.n_unknowns = d.nu;
+  h->stats.used_mode = PX_MODE_MATERIALISED;
+  h->drude_n = types[0].drude_n_au;
+  h->tau = types[0].tau_au;
+  h->have_structure = true;
+}
+
+
+// ------------------------------------------------------------------ solve
+struct SolveOut {
+  double2* d_alpha = nullptr;  // device [F][3][P]
+  double2* d_q = nullptr;      // device [F][P][N]
+  double2* d_mu = nullptr;     // device [F][P][N][3]
+  double* d_relres = nullptr;  // device [F][P]
+  double* d_sigma_pol = nullptr;  // device [F][P]
+  double* d_sigma = nullptr;      // device [F] (P == 3)
+  std::vector<double> relres;  // [B]
+  std::vector<int> iters;      // [B]
+  std::vector<int> status;     // [B]
+};
+
+template <typename T>
+T* grow(DevBuf& b, size_t n) {
+  CU(b.ensure(std::max<size_t>(n, 1) * sizeof(T)));
+  return b.as<T>();
+}
+
+px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha_ib, int P,
+                const double* pol, double e0, SolveOut* so, cudaStream_t s) {
+  if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
+  if (F < 1 || P < 1 || !omega_ev || !pol)
+    throw PxError{PX_EINVAL, "need n_freq >= 1, n_pol >= 1, omega_ev and pol_dir"};
+  if (!std::isfinite(e0) || !(e0 > 0.0)) throw PxError{PX_EINVAL, "e0 must be finite and > 0"};
+  const px::DevStructure& d = h->ds;
+  const int model = d.model;
+  if (model == PX_WFQFMU && !alpha_ib) throw PxError{PX_EINVAL, "alpha_ib is required for PX_WFQFMU"};
+  for (int f = 0; f < F; ++f)
+    if (!std::isfinite(omega_ev[f]) || !(omega_ev[f] > 0.0))
+      throw PxError{PX_EINVAL, "frequencies must be finite and > 0"};
+  for (int p = 0; p < P; ++p) {
+    double n2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      double v = pol[3 * p + k];
+      if (!std::isfinite(v)) throw PxError{PX_EINVAL, "non-finite polarisation"};
+      n2 += v * v;
+    }
+    if (std::fabs(std::sqrt(n2) - 1.0) > 1e-6) throw PxError{PX_EINVAL, "polarisation directions must be unit vectors"};
+  }
+  if (model == PX_WFQFMU)
+    for (size_t k = 0; k < 2 * (size_t)d.ntypes * F; ++k)
+      if (!std::isfinite(alpha_ib[k])) throw PxError{PX_EINVAL, "non-finite alpha_ib"};
+  if ((long long)F * P > (1LL << 24)) throw PxError{PX_EINVAL, "too many columns"};
+
+  const int B = F * P;
+  const int nu = d.nu, np = d.np, N = d.N, ntypes = d.ntypes;
+  const px_options& o = h->opt;
+  const int m = std::min(o.restart_m, o.max_iter);
+  const int passes = o.gs_passes;
+  const bool lowp = o.precision != PX_FP64;
+  const double inner_tol = lowp ? o.inner_tol : 0.0;
+  const double tol_frac = lowp ? 0.1 : 0.5;
+  const int nblk = px::reduction_blocks(nu);
+  long long& nl = h->nl;
+  nl = 0;
+  px_stats& st = h->stats;
+  st.matvec_ms = st.resid_ms = 0.0;
+  st.matvec_launches = st.resid_launches = 0;
+  st.matvec_flops = st.matvec_bytes = st.resid_flops = 0.0;
+  st.cycles = 0;
+  st.total_iters = 0;
+  st.used_precision = o.precision;
+  CU(cudaEventRecord(h->ev_a, s));
+
+  // ---- inputs, shifts (Eq. 6, Eq. 8) and right-hand sides
+  double* d_omega = grow<double>(h->b_pol, 3 * (size_t)P + F + 2 * (size_t)ntypes * F);
+  double* d_pol = d_omega + F;
+  double* d_aib = d_pol + 3 * P;
+  CU(cudaMemcpyAsync(d_omega, omega_ev, sizeof(double) * F, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d_pol, pol, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, s));
+  if (model == PX_WFQFMU)
+    CU(cudaMemcpyAsync(d_aib, alpha_ib, sizeof(double) * 2 * ntypes * F, cudaMemcpyHostToDevice, s));
+  double2* zq_all = grow<double2>(h->b_zq, 2 * (size_t)B);          // [B] all, then [B] active
+  double2* zq_act = zq_all + B;
+  double2* zmu_all = grow<double2>(h->b_zmu, 2 * (size_t)ntypes * B);
+  double2* zmu_act = zmu_all + (size_t)ntypes * B;
+  CU(px::launch_shifts(F, P, ntypes, model, d_omega, d_aib, h->drude_n, h->tau, zq_all, zmu_all,
+                       s, &nl));
+  double* b = grow<double>(h->b_b, (size_t)nu * P);
+  CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
+  double* bnorm = grow<double>(h->b_bnorm, P);
+  double* rnorm = grow<double>(h->b_rnorm, B);
+  CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
+  double2* x = grow<double2>(h->b_x, (size_t)nu * B);
+  double2* r = grow<double2>(h->b_r, (size_t)nu * B);
+  int* iters = grow<int>(h->b_iters, B);
+  int* act = grow<int>(h->b_act, B);
+  CU(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)nu * B, s));
+  CU(cudaMemsetAsync(iters, 0, sizeof(int) * B, s));
+  CU(px::launch_init_residual(b, nu, P, B, bnorm, r, rnorm, s, &nl));   // x = 0: r = b
+
+  // ---- Krylov workspace for up to B active columns
+  px::ArnoldiArgs A{};
+  A.nu = nu;
+  A.m = m;
+  A.nblk = nblk;
+  double2* V = grow<double2>(h->b_V, (size_t)(m + 1) * nu * B);
+  double2* W = grow<double2>(h->b_W, (size_t)nu * B);
+  double2* hh = grow<double2>(h->b_h, 2 * (size_t)(m + 1) * B);
+  double* part = grow<double>(h->b_part, 2 * (size_t)nblk * (m + 1) * B);
+  double* normpart = grow<double>(h->b_normpart, (size_t)nblk * B);
+  double2* Rm = grow<double2>(h->b_R, (size_t)m * (m + 1) * B);
+  double2* g = grow<double2>(h->b_g, (size_t)(m + 1) * B);
+  double* cs = grow<double>(h->b_cs, (size_t)m * B);
+  double2* sn = grow<double2>(h->b_sn, (size_t)m * B);
+  double* target = grow<double>(h->b_target, B);
+  int* jconv = grow<int>(h->b_jconv, B);
+  double* invh = grow<double>(h->b_invh, B);
+  double2* yv = grow<double2>(h->b_y, (size_t)m * B);
+  const int ldx = (int)round_up(2 * (size_t)B, px::kTile);
+  float* X32 = nullptr;
+  float* Y32 = nullptr;
+  if (lowp) {
+    X32 = grow<float>(h->b_X32, (size_t)np * ldx);
+    Y32 = grow<float>(h->b_Y32, (size_t)np * ldx);
+  }
+  double* X64 = grow<double>(h->b_X64, (size_t)np * ldx);
+  double* Y64 = grow<double>(h->b_Y64, (size_t)np * ldx);
+
+  std::vector<int> h_act(B), h_iters(B);
+  std::vector<double> h_rnorm(B), h_bnorm(P);
+  CU(cudaMemcpyAsync(h_bnorm.data(), bnorm, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+  sync_stream(h, s);
+  // a column whose right-hand side is zero (e.g. no bond has a component along the
+  // field) has the exact solution x = 0 and needs no iteration
+  int Bact = 0;
+  for (int c = 0; c < B; ++c)
+    if (h_bnorm[c % P] > 0.0) h_act[Bact++] = c;
+
+  size_t prof_k = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv_events, rs_events;
+  for (int cycle = 0; cycle < o.max_cycles && Bact > 0; ++cycle) {
+    st.cycles = cycle + 1;
+    // compact active columns and their shifts
+    CU(cudaMemcpyAsync(act, h_act.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
+    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
+    A.Bact = Bact;
+    A.V = V; A.W = W; A.h = hh; A.part = part; A.normpart = normpart; A.R = Rm; A.g = g;
+    A.cs = cs; A.sn = sn; A.target = target; A.jconv = jconv; A.inv_h = invh; A.y = yv;
+    A.active_count = h->d_active;
+    const int ldxa = (int)round_up(2 * (size_t)Bact, px::kTile);
+    std::memset(h->h_active, 0xff, sizeof(int) * px::kMaxRestart);
+    CU(cudaMemsetAsync(h->d_active, 0, sizeof(int) * px::kMaxRestart, s));
+    if (lowp) CU(cudaMemsetAsync(X32, 0, sizeof(float) * (size_t)np * ldxa, s));
+    else CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
+    CU(px::launch_cycle_init(A, act, rnorm, bnorm, P, inner_tol, tol_frac * o.tol_rel, s, &nl));
+    CU(px::launch_cycle_start(A, act, r, B, rnorm, lowp ? X32 : nullptr, lowp ? nullptr : X64,
+                              ldxa, s, &nl));
+
+    px::ShiftArgs sa{};
+    sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.P = P;
+    sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = d.type;
+    sa.zq = zq_act; sa.zmu = zmu_act; sa.nblk = nblk;
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      // ---- block matvec Y = T X (the dominant kernel)
+      cudaEvent_t e0v = nullptr, e1v = nullptr;
+      if (o.profile) {
+        e0v = pool_event(h, prof_k++);
+        e1v = pool_event(h, prof_k++);
+        CU(cudaEventRecord(e0v, s));
+      }
+      if (lowp) CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
+      else CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+      if (o.profile) {
+        CU(cudaEventRecord(e1v, s));
+        mv_events.push_back({e0v, e1v});
+      }
+      st.matvec_launches++;
+      st.matvec_flops += 4.0 * (double)nu * nu * Bact;
+      st.matvec_bytes += (double)nu * nu * (lowp ? 4.0 : 8.0) + 2.0 * nu * 2.0 * Bact * (lowp ? 4.0 : 8.0);
+      // ---- conductance + shift: W = Kbar Y - z V_j
+      sa.Y = lowp ? (const void*)Y32 : (const void*)Y64;
+      sa.ldy = ldxa;
+      sa.y_is_f32 = lowp;
+      sa.X = V + (size_t)j * nu * Bact;
+      sa.ldx_c = Bact;
+      sa.W = W;
+      sa.ldw_c = Bact;
+      CU(px::launch_shift(sa, 0, s, &nl));
+      // ---- FP64 classical Gram-Schmidt
+      for (int pass = 0; pass < passes; ++pass) {
+        CU(px::launch_dots(A, j, pass, s, &nl));
+        CU(px::launch_update(A, j, pass, pass == passes - 1, s, &nl));
+      }
+      CU(px::launch_givens(A, j, passes, s, &nl));
+      CU(cudaMemcpyAsync(h->h_active + j, h->d_active + j, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(px::launch_normalize(A, j, lowp ? X32 : nullptr, lowp ? nullptr : X64, ldxa, s, &nl));
+      CU(cudaEventRecord(h->ev_iter[j & 1], s));
+      jend = j + 1;
+      // lagged poll: wait for step j-1 and stop once every column is frozen
+      if (j >= 1) {
+        wait_event(h, h->ev_iter[(j - 1) & 1]);
+        if (reinterpret_cast<volatile int*>(h->h_active)[j - 1] == 0) break;
+      }
+    }
+    st.total_iters += jend;
+    CU(px::launch_cycle_end(A, jend, act, x, B, iters, s, &nl));
+
+    // ---- FP64 true residual r = b - A x for the columns of this cycle
+    CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
+    CU(px::launch_gather_x(x, B, act, Bact, nu, X64, ldxa, s, &nl));
+    cudaEvent_t r0e = nullptr, r1e = nullptr;
+    if (o.profile) {
+      r0e = pool_event(h, prof_k++);
+      r1e = pool_event(h, prof_k++);
+      CU(cudaEventRecord(r0e, s));
+    }
+    CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    if (o.profile) {
+      CU(cudaEventRecord(r1e, s));
+      rs_events.push_back({r0e, r1e});
+    }
+    st.resid_launches++;
+    st.resid_flops += 4.0 * (double)nu * nu * Bact;
+    sa.Y = Y64;
+    sa.ldy = ldxa;
+    sa.y_is_f32 = false;
+    sa.X = x;
+    sa.act = act;
+    sa.b = b;
+    sa.R = r;
+    sa.B = B;
+    sa.normpart = normpart;
+    CU(px::launch_shift(sa, 1, s, &nl));
+    CU(px::launch_norm_finish(normpart, nblk, Bact, act, rnorm, s, &nl));
+    CU(cudaMemcpyAsync(h_rnorm.data(), rnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+    sync_stream(h, s);
+    int nb = 0;
+    for (int k = 0; k < Bact; ++k) {
+      int c = h_act[k];
+      if (!std::isfinite(h_rnorm[c])) throw PxError{PX_ECUDA, "non-finite residual"};
+      if (h_rnorm[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_act[nb++] = c;
+    }
+    Bact = nb;
+  }
+
+  // ---- observables (Sec. "Observables")
+  CU(px::launch_observables(N, model, F, P, d.pos64, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
+                            so->d_mu, so->d_sigma_pol, so->d_sigma, s, &nl));
+  if (so->d_relres) CU(px::launch_relres(rnorm, bnorm, B, P, so->d_relres, s, &nl));
+  CU(cudaMemcpyAsync(h_rnorm.data(), rnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  CU(cudaEventRecord(h->ev_b, s));
+  wait_event(h, h->ev_b);
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
+  st.solve_ms = ms;
+  for (auto& pr : mv_events) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, pr.first, pr.second));
+    st.matvec_ms += t;
+  }
+  for (auto& pr : rs_events) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, pr.first, pr.second));
+    st.resid_ms += t;
+  }
+  st.kernel_launches = nl;
+  so->relres.resize(B);
+  so->iters.resize(B);
+  so->status.resize(B);
+  px_status ret = PX_OK;
+  for (int c = 0; c < B; ++c) {
+    so->relres[c] = h_bnorm[c % P] > 0.0 ? h_rnorm[c] / h_bnorm[c % P] : 0.0;
+    so->iters[c] = h_iters[c];
+    so->status[c] = so->relres[c] <= o.tol_rel ? PX_OK : PX_ENOTCONV;
+    if (so->status[c] != PX_OK) ret = PX_ENOTCONV;
+  }
+  if (ret != PX_OK) h->err = "some columns did not reach tol_rel; see status[]";
+  return ret;
+}
+
+void default_options(px_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PX_FP32;
+  o->mode = PX_MODE_AUTO;
+  o->restart_m = 100;
+  o->max_iter = 20000;
+  o->max_cycles = 200;
+  o->gs_passes = 2;
+  o->tol_rel = 1e-7;
+  o->inner_tol = 1e-4;
+  o->kcut_eps = 1e-6;
+  o->mu_self_term = 0;
+  o->profile = 0;
+  o->hbm_budget_bytes = 0;
+  o->device_wait_limit_s = 600.0;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int px_abi_version(void) { return PX_ABI_VERSION; }
+
+px_status px_options_default(px_options* opt) {
+  if (!opt) return PX_EINVAL;
+  default_options(opt);
+  return PX_OK;
+}
+
+px_status px_create(px_handle** out, const px_options* opt) {
+  if (!out) return fail(nullptr, PX_EINVAL, "NULL handle pointer");
+  *out = nullptr;
+  px_options o;
+  if (opt) o = *opt;
+  else default_options(&o);
+  std::string msg;
+  px_status vs = validate_options(&o, &msg);
+  if (vs != PX_OK) return fail(nullptr, vs, msg);
+  px_handle* h = new (std::nothrow) px_handle();
+  if (!h) return fail(nullptr, PX_ENOMEM, "host allocation failed");
+  h->opt = o;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  try {
+    CU(cudaGetDevice(&h->device));
+    CU(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreate(&h->ev_a));
+    CU(cudaEventCreate(&h->ev_b));
+    CU(cudaEventCreateWithFlags(&h->ev_iter[0], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&h->ev_iter[1], cudaEventDisableTiming));
+    CU(cudaHostAlloc((void**)&h->h_active, sizeof(int) * px::kMaxRestart, cudaHostAllocDefault));
+    CU(cudaMalloc((void**)&h->d_active, sizeof(int) * px::kMaxRestart));
+  } catch (const PxError& e) {
+    g_create_error = e.msg;
+    px_destroy(h);
+    return e.st;
+  }
+  *out = h;
+  return PX_OK;
+}
+
+px_status px_set_options(px_handle* h, const px_options* opt) {
+  if (!h || !opt) return fail(h, PX_EINVAL, "NULL argument");
+  std::string msg;
+  px_status vs = validate_options(opt, &msg);
+  if (vs != PX_OK) return fail(h, vs, msg);
+  bool rebuild = h->have_structure && (opt->precision != h->opt.precision || opt->mode != h->opt.mode ||
+                                       opt->kcut_eps != h->opt.kcut_eps ||
+                                       opt->mu_self_term != h->opt.mu_self_term);
+  h->opt = *opt;
+  if (rebuild) {
+    h->have_structure = false;
+    return fail(h, PX_EINVAL, "options that change the operators need px_set_structure again");
+  }
+  return PX_OK;
+}
+
+px_status px_set_structure(px_handle* h, px_model model, int n_atoms, const double* xyz_ang,
+                           const int* type_idx, const px_atom_type* types, int n_types) {
+  if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
+  try {
+    set_structure(h, (int)model, n_atoms, xyz_ang, type_idx, types, n_types);
+  } catch (const PxError& e) {
+    h->have_structure = false;
+    return fail(h, e.st, e.msg);
+  }
+  return PX_OK;
+}
+
+px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const double* alpha_ib,
+                   int n_pol, const double* pol_dir, double e0, px_result* out,
+                   void* cuda_stream) {
+  if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
+  if (!out) return fail(h, PX_EINVAL, "NULL result");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+  try {
+    if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
+    if (n_freq < 1 || n_pol < 1) throw PxError{PX_EINVAL, "need n_freq >= 1 and n_pol >= 1"};
+    const size_t F = n_freq, P = n_pol, N = h->ds.N, B = F * P;
+    SolveOut so;
+    double* obs = grow<double>(h->b_alpha, 2 * F * 3 * P + F * P + F + B);
+    so.d_alpha = reinterpret_cast<double2*>(obs);
+    so.d_sigma_pol = obs + 2 * F * 3 * P;
+    so.d_sigma = so.d_sigma_pol + F * P;
+    so.d_relres = so.d_sigma + F;
+    if (out->q) so.d_q = grow<double2>(h->b_q, B * N);
+    if (out->mu && h->ds.model == PX_WFQFMU) so.d_mu = grow<double2>(h->b_mu, B * N * 3);
+    px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s);
+    if (out->alpha) CU(cudaMemcpyAsync(out->alpha, so.d_alpha, sizeof(double2) * F * 3 * P, cudaMemcpyDeviceToHost, s));
+    if (out->sigma_abs_pol) CU(cudaMemcpyAsync(out->sigma_abs_pol, so.d_sigma_pol, sizeof(double) * F * P, cudaMemcpyDeviceToHost, s));
+    if (out->sigma_abs && P == 3) CU(cudaMemcpyAsync(out->sigma_abs, so.d_sigma, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
+    if (out->rel_residual) CU(cudaMemcpyAsync(out->rel_residual, so.d_relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    if (so.d_q) CU(cudaMemcpyAsync(out->q, so.d_q, sizeof(double2) * B * N, cudaMemcpyDeviceToHost, s));
+    if (so.d_mu) CU(cudaMemcpyAsync(out->mu, so.d_mu, sizeof(double2) * B * N * 3, cudaMemcpyDeviceToHost, s));
+    sync_stream(h, s);
+    for (size_t c = 0; c < B; ++c) {
+      if (out->iters) out->iters[c] = so.iters[c];
+      if (out->status) out->status[c] = so.status[c];
+    }
+    return r == PX_OK ? PX_OK : fail(h, r, h->err);
+  } catch (const PxError& e) {
+    return fail(h, e.st, e.msg);
+  }
+}
+
+px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
+                          const double* alpha_ib, int n_pol, const double* pol_dir, double e0,
+                          double* d_alpha, double* d_q, double* d_mu, double* d_relres,
+                          void* cuda_stream) {
+  if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+  try {
+    if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
+    if (n_freq < 1 || n_pol < 1) throw PxError{PX_EINVAL, "need n_freq >= 1 and n_pol >= 1"};
+    SolveOut so;
+    const size_t F = n_freq, P = n_pol;
+    double* obs = grow<double>(h->b_alpha, 2 * F * 3 * P + F * P + F);
+    so.d_alpha = d_alpha ? (double2*)d_alpha : reinterpret_cast<double2*>(obs);
+    so.d_sigma_pol = obs + 2 * F * 3 * P;
+    so.d_sigma = so.d_sigma_pol + F * P;
+    so.d_q = (double2*)d_q;
+    so.d_mu = h->ds.model == PX_WFQFMU ? (double2*)d_mu : nullptr;
+    so.d_relres = d_relres;
+    px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s);
+    sync_stream(h, s);
+    return r == PX_OK ? PX_OK : fail(h, r, h->err);
+  } catch (const PxError& e) {
+    return fail(h, e.st, e.msg);
+  }
+}
+
+px_status px_get_stats(const px_handle* h, px_stats* st) {
+  if (!h || !st) return PX_EINVAL;
+  *st = h->stats;
+  return PX_OK;
+}
+
+px_status px_destroy(px_handle* h) {
+  if (!h) return PX_OK;
+  free_all(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  for (cudaEvent_t e : h->ev_iter)
+    if (e) cudaEventDestroy(e);
+  if (h->h_active) cudaFreeHost(h->h_active);
+  if (h->d_active) cudaFree(h->d_active);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return PX_OK;
+}
+
+const char* px_last_error(const px_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Internal declarations shared by the px CUDA translation units.
+//
+// Data layout in device memory (one structure, one block of B columns):
+//   positions      pos64 [N][3] double (bohr)
+//   per atom       Rq, Rmu, area [N] double; type [N] int
+//   K (Eq. 3)      CSR of the off-diagonal bond weights: rowptr [N+1], col [nnz],
+//                  val64 [nnz] double, val32 [nnz] float.  The Laplacian form of
+//                  Eq. 2 is applied as (Kbar y)_i = sum_j K_ij (y_j - y_i), which is
+//                  the same sum with the diagonal folded in (exact for constants).
+//   T (Eq. 5 + derivatives)  row-major [np][np], np = n_u rounded up to 128, zero
+//                  padded; T64 (double), T32 (float), Thi/Tlo (bf16 split).
+//   columns        column c = f * P + p (frequency-major).  Work arrays hold only the
+//                  B_act active columns, compacted, column index fastest.
+//   complex data   double2 (re, im); the matvec operands X / Y are real matrices
+//                  [np][ldx] whose columns 2a, 2a+1 are the re / im parts of column a.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace px {
+
+constexpr int kTile = 128;   // padding granularity of T and of the matvec operands
+constexpr int kMaxRestart = 400;  // largest Krylov basis per restart cycle
+
+inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- structure
+struct DevStructure {
+  int model = 0;      // 0 wFQ, 1 wFQFmu
+  int N = 0;          // atoms
+  int nu = 0;         // unknowns
+  int np = 0;         // padded unknowns (multiple of kTile)
+  int ntypes = 0;
+  int nnz = 0;
+  double* pos64 = nullptr;
+  double* Rq = nullptr;
+  double* Rmu = nullptr;
+  double* area = nullptr;
+  int* type = nullptr;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  double* T64 = nullptr;
+  float* T32 = nullptr;
+  __nv_bfloat16* Thi = nullptr;
+  __nv_bfloat16* Tlo = nullptr;
+};
+
+// ---------------------------------------------------------------- launch wrappers
+// Every wrapper enqueues its kernels on `s` and adds the number of kernel
+// launches to *nl.  They never synchronise.
+
+// Neighbour list + CSR of K.  rcut2 / r0 / dd / ss are [ntypes][ntypes] pair tables.
+cudaError_t launch_neigh_count(const double* pos, int N, const int* type, int ntypes,
+                               const double* rcut2, int* counts, cudaStream_t s, long long* nl);
+cudaError_t launch_scan(const int* counts, int N, int* rowptr, cudaStream_t s, long long* nl);
+cudaError_t launch_neigh_fill(const double* pos, int N, const int* type, int ntypes,
+                              const double* rcut2, const double* r0, const double* dd,
+                              const double* ss, const double* area, const int* rowptr,
+                              int* col, double* val64, float* val32, cudaStream_t s,
+                              long long* nl);
+// Dense T in FP64 (Eq. 5; wFQFmu adds the 4x4 blocks of Sec. 2.2).
+cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream_t s,
+                             long long* nl);
+// T32 = float(T64); Thi = bf16(T64), Tlo = bf16(T64 - Thi).
+cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool bf16, cudaStream_t s,
+                             long long* nl);
+
+// Matvec Y[np][ldy] = T[np][np] X[np][ldx], columns ncols (multiple of kTile).
+cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float* Y, int ldy,
+                         int ncols, cudaStream_t s, long long* nl);
+cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
+                         int ncols, cudaStream_t s, long long* nl);
+
+// Conductance + shift (Eq. 1 / Eq. 7 applied to a block).  mode 0 (inner):
+//   W[i][a] = (Kbar Y)_i - z X[i][a]               charge rows (i < N)
+//   W[i][a] = Y_i - z_mu(type) X[i][a]              dipole rows (wFQFmu)
+// mode 1 (true residual): R[i][act[a]] = b[i][pol(act[a])] - (same with X = x[., act[a]]),
+// plus per-block partial sums of |R|^2 in normpart[blk][a].
+struct ShiftArgs {
+  int nu, N, model, Bact, P;
+  const int* rowptr; const int* col; const double* val64; const float* val32;
+  const int* type;
+  const void* Y; int ldy; bool y_is_f32;
+  const double2* X; int ldx_c;                 // complex, column stride in complex units
+  const double2* zq;                            // [Bact]
+  const double2* zmu;                           // [ntypes][Bact] (wFQFmu)
+  double2* W; int ldw_c;                        // inner output
+  // residual mode
+  const int* act; const double* b; double2* R; int B; double* normpart; int nblk;
+};
+cudaError_t launch_shift(const ShiftArgs& a, int mode, cudaStream_t s, long long* nl);
+
+// RHS b[i][p] (real): -Kbar V for charge rows, E0 e_p for dipole rows.
+cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* col,
+                       const double* val64, const double* pos, const double* pol, int P,
+                       double e0, double* b, cudaStream_t s, long long* nl);
+
+// ---------------------------------------------------------------- Arnoldi (FP64)
+struct ArnoldiArgs {
+  int nu, Bact, m;
+  double2* V;          // [m+1][nu][Bact]
+  double2* W;          // [nu][Bact]
+  double2* h;          // [2][m+1][Bact]   per-pass projections
+  double* part;        // scratch partials [nblk][m+1][Bact] (complex as 2 doubles)
+  double* normpart;    // [nblk][Bact]
+  int nblk;            // row blocks of the reductions
+  double2* R;          // [m][m+1][Bact] rotated Hessenberg columns
+  double2* g;          // [m+1][Bact]
+  double* cs;          // [m][Bact]
+  double2* sn;         // [m][Bact]
+  double* target;      // [Bact] inner residual target
+  int* jconv;          // [Bact] basis size when frozen (0 = still running)
+  double* inv_h;       // [Bact] 1 / h_{j+1,j} (0 when frozen)
+  int* active_count;   // [m] unfrozen columns after step j (device or mapped host)
+  double2* y;          // [m][Bact]
+};
+cudaError_t launch_dots(const ArnoldiArgs& a, int j, int pass, cudaStream_t s, long long* nl);
+cudaError_t launch_update(const ArnoldiArgs& a, int j, int pass, bool last, cudaStream_t s,
+                          long long* nl);
+cudaError_t launch_givens(const ArnoldiArgs& a, int j, int passes, cudaStream_t s,
+                          long long* nl);
+// V[j+1] = W * inv_h; also writes the matvec operand X (f32 [np][ldx] or f64) of V[j+1].
+cudaError_t launch_normalize(const ArnoldiArgs& a, int j, float* X32, double* X64, int ldx,
+                             cudaStream_t s, long long* nl);
+// Cycle start: per-column init (g_0 = beta, inner target, freeze flags) and
+// V[0][i][a] = r[i][act[a]] / rnorm[act[a]] with the matching matvec operand X.
+// target[a] = max(inner_tol * beta_a, tol_abs_frac * ||b_a||): the inner residual at
+// which column a stops for this cycle (tol_abs_frac = fraction * tol_rel).
+cudaError_t launch_cycle_init(const ArnoldiArgs& a, const int* act, const double* rnorm,
+                              const double* bnorm, int P, double inner_tol, double tol_abs_frac,
+                              cudaStream_t s, long long* nl);
+cudaError_t launch_cycle_start(const ArnoldiArgs& a, const int* act, const double2* r, int B,
+                               const double* rnorm, float* X32, double* X64, int ldx,
+                               cudaStream_t s, long long* nl);
+// Cycle end: y = R^-1 g per column, x[., act[a]] += V y, iters[act[a]] += used.
+cudaError_t launch_cycle_end(const ArnoldiArgs& a, int jend, const int* act, double2* x, int B,
+                             int* iters, cudaStream_t s, long long* nl);
+// Gather x[., act[a]] into the f64 matvec operand.
+cudaError_t launch_gather_x(const double2* x, int B, const int* act, int Bact, int nu,
+                            double* X64, int ldx, cudaStream_t s, long long* nl);
+// rnorm[act[a]] = sqrt(sum_blk normpart[blk][a])
+cudaError_t launch_norm_finish(const double* normpart, int nblk, int Bact, const int* act,
+                               double* rnorm, cudaStream_t s, long long* nl);
+
+// Per-column shifts z_q(w) = -w (w tau + i) / (2 n tau) (Eq. 6) and, per atom type,
+// z_mu(w) = -1 / alpha^IB(w) (Eq. 8); omega in eV, alpha_ib [ntypes][F] complex.
+cudaError_t launch_shifts(int F, int P, int ntypes, int model, const double* omega_ev,
+                          const double* alpha_ib, double n, double tau, double2* zq,
+                          double2* zmu, cudaStream_t s, long long* nl);
+cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
+                                 const int* act, int Bact, double2* zq_act, double2* zmu_act,
+                                 cudaStream_t s, long long* nl);
+// bnorm[p] = ||b[., p]||_2
+cudaError_t launch_col_norms(const double* b, int nu, int P, double* bnorm, cudaStream_t s,
+                             long long* nl);
+// x = 0: r[i][c] = b[i][c % P], rnorm[c] = bnorm[c % P]
+cudaError_t launch_init_residual(const double* b, int nu, int P, int B, const double* bnorm,
+                                 double2* r, double* rnorm, cudaStream_t s, long long* nl);
+cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P, double* out,
+                          cudaStream_t s, long long* nl);
+
+// ---------------------------------------------------------------- observables
+// alpha[f][k][p] = (sum_i q_i r_ik + sum_i mu_ik) / e0 (Sec. "Observables");
+// sigma_pol[f][p] = 4 pi w / c Im(e_p . alpha e_p); sigma[f] = 4 pi w/(3c) sum_p Im alpha_pp
+// (written when P == 3); q / mu copied out as [F][P][N] / [F][P][N][3].
+cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
+                               const double2* x, double e0, const double* omega_ev,
+                               const double* pol, double2* alpha, double2* qout, double2* muout,
+                               double* sigma_pol, double* sigma, cudaStream_t s, long long* nl);
+
+int reduction_blocks(int nu);
+
+}  // namespace px

@@ -1,0 +1,170 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Sizes span several 128-row tiles with a ragged tail and ragged column blocks;
+edge cases cover the degenerate structures of the method.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from paper_2510_12731_gb300 import structures as S
+
+pytestmark = pytest.mark.gpu
+
+XYZ = np.eye(3)
+
+
+def _solver(**kw):
+    from paper_2510_12731_gb300 import Solver
+    return Solver(**kw)
+
+
+def _oracle(w, **kw):
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    return M.solve(st, w.model, w.omega_ev, w.pol_dirs, alpha_ib=w.alpha_ib, **kw), st
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+def _run(w, **opts):
+    with _solver(**opts) as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib)
+        stats = s.stats()
+    return out, stats
+
+
+def _alpha_err(out, ref):
+    """max over (w, pol) of |alpha_gpu - alpha_ref| / |alpha_ref| (the field-direction column)."""
+    a, r = out["alpha"], ref.alpha
+    num = np.linalg.norm(a - r, axis=1)
+    den = np.linalg.norm(r, axis=1)
+    return float(np.max(num / den))
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+@pytest.mark.parametrize("precision,tol,alpha_tol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-7)])
+def test_small_sphere_parity(model, precision, tol, alpha_tol):
+    # Ag sphere r = 9 A: N = 225 atoms (2 row tiles, ragged), 7 w x 3 pols = 21 columns
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=7, wmin=2.0, wmax=5.5)
+    ref, st = _oracle(w)
+    out, stats = _run(w, precision=precision, tol_rel=tol)
+    assert out["ok"], out["rel_residual"]
+    assert np.all(out["rel_residual"] <= tol)
+    assert _alpha_err(out, ref) <= alpha_tol
+    qerr = np.abs(out["q"] - ref.q).max() / np.abs(ref.q).max()
+    assert qerr <= 10 * alpha_tol
+    if model == "wfqfmu":
+        merr = np.abs(out["mu"] - ref.mu).max() / np.abs(ref.mu).max()
+        assert merr <= 10 * alpha_tol
+    # charge conservation and reciprocity on the GPU outputs
+    assert np.all(np.abs(out["q"].sum(axis=-1)) <= 1e-9 * np.abs(out["q"]).sum(axis=-1))
+    for f in range(w.omega_ev.size):
+        a = out["alpha"][f]
+        assert np.abs(a - a.T).max() <= 1e-6 * np.abs(a).max()
+    assert stats["kernel_launches"] > 0
+
+
+def test_ag_sphere_791_fp64_sweep():
+    """wFQ Ag fcc sphere r = 15 A (N = 791), 60 w in 2.0-4.5 eV, x-polarised, plain FP64."""
+    w = S.ag_sphere_791()
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp64", tol_rel=1e-10)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-8
+    sig_ref = ref.sigma_abs_pol
+    assert np.abs(out["sigma_abs_pol"] - sig_ref).max() <= 1e-8 * np.abs(sig_ref).max()
+
+
+def test_ag_sphere_791_fp32_meets_1e5():
+    w = S.ag_sphere_791()
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision="fp32", tol_rel=1e-7)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-5
+
+
+def test_sigma_abs_three_polarisations():
+    w = S.small_cluster(element="Na", radius=10.0, model="wfq", nfreq=5, wmin=2.5, wmax=4.0)
+    ref, st = _oracle(w)
+    out, _ = _run(w, precision="fp64", tol_rel=1e-11)
+    om = w.omega_ev / M.HARTREE_EV
+    tr = np.einsum("fkk->f", ref.alpha).imag
+    sig = M.sigma_abs(om, tr)
+    assert np.allclose(out["sigma_abs"], sig, rtol=1e-8, atol=0)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _single(model, xyz, element="Ag", nfreq=3):
+    el = S.ELEMENTS[element]
+    om = np.linspace(2.5, 4.0, nfreq)
+    aib = el.alpha_ib(om)[None, :] if model == "wfqfmu" else None
+    return S.Workload("edge", model, np.asarray(xyz, float), np.zeros(len(xyz), np.int32),
+                      [el.atom_type()], om, XYZ, aib)
+
+
+def test_single_atom_wfq_has_zero_response():
+    w = _single("wfq", [[0.0, 0.0, 0.0]])
+    out, _ = _run(w, precision="fp64")
+    assert out["ok"]
+    assert np.abs(out["alpha"]).max() == 0.0
+
+
+def test_single_atom_wfqfmu_is_interband_polarisability():
+    w = _single("wfqfmu", [[0.0, 0.0, 0.0]])
+    out, _ = _run(w, precision="fp64", tol_rel=1e-12)
+    for f in range(3):
+        assert np.allclose(out["alpha"][f], w.alpha_ib[0, f] * np.eye(3), rtol=1e-12, atol=0)
+
+
+def test_two_atom_closed_form_on_gpu():
+    d_ang = 2.892
+    w = _single("wfq", [[-d_ang / 2, 0, 0], [d_ang / 2, 0, 0]])
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp32", tol_rel=1e-12)
+    assert out["ok"]
+    axx, rxx = out["alpha"][:, 0, 0], ref.alpha[:, 0, 0]
+    assert np.abs(axx - rxx).max() <= 1e-10 * np.abs(rxx).max()
+    assert np.abs(out["alpha"][:, 1:, 1:]).max() <= 1e-12 * np.abs(rxx).max()
+
+
+def test_graphene_field_normal_to_sheet_has_zero_rhs():
+    el = S.ELEMENTS["C"]
+    xyz = S.honeycomb_disk(1.42, 16.0)
+    om = np.linspace(0.2, 0.8, 4)
+    w = S.Workload("g", "wfq", xyz, np.zeros(len(xyz), np.int32), [el.atom_type()], om,
+                   np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]]), None)
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp64", tol_rel=1e-10)
+    assert out["ok"]
+    assert np.abs(out["alpha"][:, :, 0]).max() == 0.0
+    assert _alpha_err({"alpha": out["alpha"][:, :, 1:]}, type("R", (), {"alpha": ref.alpha[:, :, 1:]})) <= 1e-8
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2510_12731_gb300 import PxError
+    el = S.ELEMENTS["Ag"]
+    with _solver() as s:
+        with pytest.raises(PxError, match="EINVAL"):
+            s.set_structure("wfq", [[0, 0, 0], [0, 0, 0]], [0, 0], [el.atom_type()])
+        with pytest.raises(PxError, match="EINVAL"):
+            s.set_structure("wfq", [[0, 0, float("nan")]], [0], [el.atom_type()])
+        with pytest.raises(PxError, match="EINVAL"):
+            s.set_structure("wfq", [[0, 0, 0]], [1], [el.atom_type()])
+        s.set_structure("wfq", [[0, 0, 0], [2.9, 0, 0]], [0, 0], [el.atom_type()])
+        with pytest.raises(PxError, match="EINVAL"):
+            s.solve([-1.0], XYZ)
+        with pytest.raises(PxError, match="EINVAL"):
+            s.solve([2.0], [[1.0, 1.0, 0.0]])
+
+
+def test_not_converged_is_reported():
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=3, wmin=2.0, wmax=3.0)
+    out, _ = _run(w, precision="fp64", tol_rel=1e-12, max_iter=2, restart_m=2)
+    assert not out["ok"]
+    assert np.any(out["status"] == 3)
