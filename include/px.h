@@ -134,6 +134,7 @@ typedef struct {
   long long resid_launches;
   double resid_flops;
   long long kernel_launches; /* every kernel this library launched in the last px_solve */
+  long long setup_launches;  /* kernels launched by the last px_set_structure */
   int cycles;              /* restart/refinement cycles run */
   long long total_iters;   /* sum over cycles of the inner iterations run */
   long long n_unknowns;    /* n_u: N (wFQ) or 4N (wFQFmu) */

@@ -97,42 +97,49 @@ class Solver:
         self.model = m
         self.natoms = xyz.shape[0]
 
+    def alloc_outputs(self, n_freq, n_pol, want_q=True, want_mu=True, empty=np.zeros):
+        """Host result arrays for solve(); ``empty`` may allocate pinned memory."""
+        F, P, N = int(n_freq), int(n_pol), self.natoms
+        out = {"alpha": empty((F, 3, P), dtype=np.complex128),
+               "sigma_abs": empty((F,), dtype=np.float64),
+               "sigma_abs_pol": empty((F, P), dtype=np.float64),
+               "q": empty((F, P, N), dtype=np.complex128) if want_q else None,
+               "mu": (empty((F, P, N, 3), dtype=np.complex128)
+                      if (want_mu and self.model == L.PX_WFQFMU) else None),
+               "rel_residual": empty((F, P), dtype=np.float64),
+               "iters": empty((F, P), dtype=np.int32),
+               "status": empty((F, P), dtype=np.int32)}
+        return out
+
     def solve(self, omega_ev, pol_dirs, alpha_ib=None, e0=1.0, want_q=True, want_mu=True,
-              stream=None):
+              stream=None, out=None):
         """Solve every (frequency, polarisation) column; returns a dict of numpy arrays.
 
         alpha (F, 3, P) complex, sigma_abs (F,) [P == 3], sigma_abs_pol (F, P),
         q (F, P, N) complex, mu (F, P, N, 3) complex [wFQFmu], rel_residual (F, P),
         iters (F, P), status (F, P), ok (bool: every column met tol_rel).
+        ``out`` may hold preallocated arrays (see alloc_outputs).
         """
         w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
         pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
-        F, P, N = w.size, pol.shape[0], self.natoms
+        F, P = w.size, pol.shape[0]
         aib = None
         if alpha_ib is not None:
             aib = np.ascontiguousarray(np.asarray(alpha_ib, dtype=np.complex128)).view(np.float64)
-        alpha = np.zeros((F, 3, P), dtype=np.complex128)
-        sig = np.zeros(F)
-        sigp = np.zeros((F, P))
-        q = np.zeros((F, P, N), dtype=np.complex128) if want_q else None
-        mu = (np.zeros((F, P, N, 3), dtype=np.complex128)
-              if (want_mu and self.model == L.PX_WFQFMU) else None)
-        rr = np.zeros((F, P))
-        it = np.zeros((F, P), dtype=np.int32)
-        stt = np.zeros((F, P), dtype=np.int32)
-        res = L.Result(alpha.view(np.float64).ctypes.data_as(L._dp), L.dptr(sig), L.dptr(sigp),
-                       q.view(np.float64).ctypes.data_as(L._dp) if q is not None else None,
-                       mu.view(np.float64).ctypes.data_as(L._dp) if mu is not None else None,
-                       L.dptr(rr), L.iptr(it), L.iptr(stt))
+        o = out if out is not None else self.alloc_outputs(F, P, want_q, want_mu)
+        cptr = lambda a: a.view(np.float64).ctypes.data_as(L._dp) if a is not None else None
+        res = L.Result(cptr(o["alpha"]), L.dptr(o["sigma_abs"]), L.dptr(o["sigma_abs_pol"]),
+                       cptr(o["q"]), cptr(o["mu"]), L.dptr(o["rel_residual"]),
+                       L.iptr(o["iters"]), L.iptr(o["status"]))
         st = self._lib.px_solve(self._h, F, L.dptr(w), L.dptr(aib) if aib is not None else None, P,
                                 L.dptr(pol), float(e0), C.byref(res),
                                 C.c_void_p(stream) if stream else None)
         self._check(st, allow=(L.PX_ENOTCONV,))
-        out = {"alpha": alpha, "sigma_abs_pol": sigp, "q": q, "mu": mu, "rel_residual": rr,
-               "iters": it, "status": stt, "ok": st == L.PX_OK}
-        if P == 3:
-            out["sigma_abs"] = sig
-        return out
+        result = dict(o)
+        result["ok"] = st == L.PX_OK
+        if P != 3:
+            result.pop("sigma_abs", None)
+        return result
 
     def solve_device(self, omega_ev, pol_dirs, alpha_ib=None, e0=1.0, d_alpha=None, d_q=None,
                      d_mu=None, d_relres=None, stream=None):

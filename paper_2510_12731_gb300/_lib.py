@@ -53,7 +53,8 @@ class Stats(C.Structure):
                 ("matvec_launches", C.c_longlong), ("matvec_flops", C.c_double),
                 ("matvec_bytes", C.c_double), ("resid_ms", C.c_double),
                 ("resid_launches", C.c_longlong), ("resid_flops", C.c_double),
-                ("kernel_launches", C.c_longlong), ("cycles", C.c_int),
+                ("kernel_launches", C.c_longlong), ("setup_launches", C.c_longlong),
+                ("cycles", C.c_int),
                 ("total_iters", C.c_longlong), ("n_unknowns", C.c_longlong),
                 ("used_mode", C.c_int), ("used_precision", C.c_int)]
 

@@ -299,6 +299,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   float ms = 0.f;
   CU(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
   h->stats.setup_ms = ms;
+  h->stats.setup_launches = h->nl;
   h->stats.n_unknowns = d.nu;
   h->stats.used_mode = PX_MODE_MATERIALISED;
   h->drude_n = types[0].drude_n_au;

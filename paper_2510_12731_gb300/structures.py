@@ -271,6 +271,14 @@ def ag_rod_3x3x10() -> Workload:
                         np.linspace(2.5, 5.0, 150), XYZ, precision="fp32", tol=1e-7)
 
 
+def na_sphere_r40() -> Workload:
+    """wFQ, Na bcc sphere of radius 40 A (N = 7,119), 100 w in 2-4 eV x 3 polarisations:
+    a mid-size case whose T (205 MB in FP32) is still larger than L2."""
+    el = ELEMENTS["Na"]
+    return _one_element("na_sphere_r40A_wfq", el, "wfq", sphere("bcc", el.a_ang, 40.0),
+                        np.linspace(2.0, 4.0, 100), XYZ, precision="fp32", tol=1e-7)
+
+
 def small_cluster(kind="fcc", element="Ag", radius=6.0, model="wfq", nfreq=8,
                   wmin=2.0, wmax=4.5, pols=XYZ) -> Workload:
     """A small sphere for fast parity checks."""
