@@ -339,7 +339,7 @@ def main():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--mode", default=None)
     ap.add_argument("--restart-m", dest="restart_m", type=int, default=100)
-    ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=2)
+    ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=1)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -96,8 +96,10 @@ typedef struct {
   int mode;                 /* px_mode; default PX_MODE_AUTO */
   int restart_m;            /* Krylov basis length per restart cycle; default 100 */
   int max_iter;             /* cap on matvecs per column over the whole solve; default 20000 */
-  int max_cycles;           /* cap on restart/refinement cycles; default 200 */
-  int gs_passes;            /* Gram-Schmidt passes (1 = CGS, 2 = CGS2); default 2 */
+  int max_cycles;           /* cap on restart cycles (inner cycles of all rounds); default 200 */
+  int max_refine;           /* FP64 refinement rounds after the first low-precision solve;
+                               0 returns the first round's result; default 20 */
+  int gs_passes;            /* Gram-Schmidt passes (1 = CGS, 2 = CGS2); default 1 */
   double tol_rel;           /* per-column target ||b - A x||_2 / ||b||_2 in FP64; default 1e-7 */
   double inner_tol;         /* per-cycle reduction asked of the low-precision inner
                                iteration (ignored in PX_FP64); default 1e-4 */

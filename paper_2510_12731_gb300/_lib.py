@@ -33,7 +33,8 @@ class AtomType(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("mode", C.c_int), ("restart_m", C.c_int),
-                ("max_iter", C.c_int), ("max_cycles", C.c_int), ("gs_passes", C.c_int),
+                ("max_iter", C.c_int), ("max_cycles", C.c_int), ("max_refine", C.c_int),
+                ("gs_passes", C.c_int),
                 ("tol_rel", C.c_double), ("inner_tol", C.c_double), ("kcut_eps", C.c_double),
                 ("mu_self_term", C.c_int), ("profile", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("device_wait_limit_s", C.c_double)]

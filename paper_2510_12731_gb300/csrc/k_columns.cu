@@ -1,0 +1,196 @@
+// Per-column bookkeeping kernels: frequency shifts (Eq. 6, Eq. 8), right-hand-side
+// norms, the x = 0 initial residual, relative residuals and the observables of
+// Sec. "Observables" (dipole, polarisability, absorption cross-section).
+#include "px_internal.cuh"
+
+namespace px {
+
+namespace {
+
+// One block per column c = f * P + p: dipole, polarisability and per-polarisation
+// absorption (Sec. "Observables").
+__global__ void k_observables(int N, int model, int F, int P, const double* __restrict__ pos,
+                              const double2* __restrict__ x, double e0,
+                              const double* __restrict__ omega_ev, const double* __restrict__ pol,
+                              double2* alpha, double2* qout, double2* muout, double* sigma_pol) {
+  const int c = blockIdx.x;
+  const int B = F * P;
+  const int f = c / P, p = c % P;
+  double d[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double2 q = x[(size_t)i * B + c];
+    for (int k = 0; k < 3; ++k) {
+      d[2 * k] += q.x * pos[3 * i + k];
+      d[2 * k + 1] += q.y * pos[3 * i + k];
+    }
+    if (qout) qout[(size_t)c * N + i] = q;
+    if (model == 1) {
+      for (int k = 0; k < 3; ++k) {
+        double2 mu = x[(size_t)(N + 3 * i + k) * B + c];
+        d[2 * k] += mu.x;
+        d[2 * k + 1] += mu.y;
+        if (muout) muout[((size_t)c * N + i) * 3 + k] = mu;
+      }
+    }
+  }
+  __shared__ double sh[6][256];
+  for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = d[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double im = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      double2 a = make_double2(sh[2 * k][0] / e0, sh[2 * k + 1][0] / e0);
+      if (alpha) alpha[((size_t)f * 3 + k) * P + p] = a;
+      im += pol[3 * p + k] * a.y;
+    }
+    const double w = omega_ev[f] / 27.211386245988;
+    const double c_au = 137.035999084;
+    if (sigma_pol) sigma_pol[(size_t)f * P + p] = 4.0 * 3.141592653589793 * w / c_au * im;
+  }
+}
+
+// sigma[f] = (1/3) sum_p sigma_pol[f][p] = 4 pi w / (3c) Tr Im alpha for P = 3 orthonormal fields
+__global__ void k_sigma_total(int F, int P, const double* sigma_pol, double* sigma) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  double t = 0.0;
+  for (int p = 0; p < P; ++p) t += sigma_pol[(size_t)f * P + p];
+  sigma[f] = t / 3.0;
+}
+
+__global__ void k_shifts(int F, int P, int ntypes, int model, const double* omega_ev,
+                         const double* alpha_ib, double n, double tau, double2* zq, double2* zmu) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int B = F * P;
+  if (c >= B) return;
+  int f = c / P;
+  double w = omega_ev[f] / 27.211386245988;
+  // z_q = -w (w tau + i) / (2 n tau)
+  double den = 2.0 * n * tau;
+  zq[c] = make_double2(-w * w * tau / den, -w / den);
+  if (model == 1) {
+    for (int t = 0; t < ntypes; ++t) {
+      double ar = alpha_ib[2 * ((size_t)t * F + f)], ai = alpha_ib[2 * ((size_t)t * F + f) + 1];
+      double m2 = ar * ar + ai * ai;
+      // -1 / (ar + i ai) = (-ar + i ai) / |a|^2
+      zmu[(size_t)t * B + c] = make_double2(-ar / m2, ai / m2);
+    }
+  }
+}
+
+__global__ void k_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
+                                const int* act, int Bact, double2* zq_act, double2* zmu_act) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Bact) return;
+  int c = act[a];
+  zq_act[a] = zq[c];
+  if (zmu)
+    for (int t = 0; t < ntypes; ++t) zmu_act[(size_t)t * Bact + a] = zmu[(size_t)t * B + c];
+}
+
+__global__ void k_col_norms(const double* b, int nu, int P, double* bnorm) {
+  int p = blockIdx.x;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+    double v = b[(size_t)i * P + p];
+    t += v * v;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bnorm[p] = sqrt(sh[0]);
+}
+
+__global__ void k_init_residual(const double* b, int nu, int P, int B, const double* bnorm,
+                                double inner_tol, double tol_abs_frac, double2* r, double* rnorm,
+                                double* beta, double* target_all) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nu * B) return;
+  int i = (int)(idx / B), c = (int)(idx % B);
+  r[idx] = make_double2(b[(size_t)i * P + c % P], 0.0);
+  if (i == 0) {
+    const double bn = bnorm[c % P];
+    rnorm[c] = bn;
+    beta[c] = bn;
+    target_all[c] = fmax(inner_tol * bn, tol_abs_frac * bn);
+  }
+}
+
+__global__ void k_relres(const double* rnorm, const double* bnorm, int B, int P, double* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= B) return;
+  double bn = bnorm[c % P];
+  out[c] = bn > 0.0 ? rnorm[c] / bn : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
+                               const double2* x, double e0, const double* omega_ev,
+                               const double* pol, double2* alpha, double2* qout, double2* muout,
+                               double* sigma_pol, double* sigma, cudaStream_t s, long long* nl) {
+  k_observables<<<F * P, 256, 0, s>>>(N, model, F, P, pos, x, e0, omega_ev, pol, alpha, qout,
+                                      muout, sigma_pol);
+  ++*nl;
+  if (sigma && sigma_pol && P == 3) {
+    k_sigma_total<<<(F + 127) / 128, 128, 0, s>>>(F, P, sigma_pol, sigma);
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shifts(int F, int P, int ntypes, int model, const double* omega_ev,
+                          const double* alpha_ib, double n, double tau, double2* zq,
+                          double2* zmu, cudaStream_t s, long long* nl) {
+  int B = F * P;
+  k_shifts<<<(B + 127) / 128, 128, 0, s>>>(F, P, ntypes, model, omega_ev, alpha_ib, n, tau, zq,
+                                           zmu);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
+                                 const int* act, int Bact, double2* zq_act, double2* zmu_act,
+                                 cudaStream_t s, long long* nl) {
+  k_gather_shifts<<<(Bact + 127) / 128, 128, 0, s>>>(zq, zmu, ntypes, B, act, Bact, zq_act,
+                                                     zmu_act);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_norms(const double* b, int nu, int P, double* bnorm, cudaStream_t s,
+                             long long* nl) {
+  k_col_norms<<<P, 256, 0, s>>>(b, nu, P, bnorm);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_residual(const double* b, int nu, int P, int B, const double* bnorm,
+                                 double inner_tol, double tol_abs_frac, double2* r,
+                                 double* rnorm, double* beta, double* target_all, cudaStream_t s,
+                                 long long* nl) {
+  size_t n = (size_t)nu * B;
+  k_init_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b, nu, P, B, bnorm, inner_tol,
+                                                              tol_abs_frac, r, rnorm, beta,
+                                                              target_all);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P, double* out,
+                          cudaStream_t s, long long* nl) {
+  k_relres<<<(B + 127) / 128, 128, 0, s>>>(rnorm, bnorm, B, P, out);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace px

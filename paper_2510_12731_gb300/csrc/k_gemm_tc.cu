@@ -1,0 +1,326 @@
+// Block matvec Y = T X on the 5th-generation tensor cores (tcgen05), BF16 split:
+//
+//   T = T_hi + T_lo,  X = X_hi + X_lo  (bf16 each; hi = RN(v), lo = RN(v - hi))
+//   Y = T_hi X_hi + T_hi X_lo + T_lo X_hi       (FP32 accumulation in TMEM)
+//
+// which keeps ~16 significant bits of every product (the dropped T_lo X_lo term is
+// below 2^-16 relative).  One CTA computes a 128 x 256 tile of Y:
+//   warp 0   TMA producer: per 64-wide K step, loads T_hi, T_lo (128 x 64) and
+//            X_hi, X_lo (256 x 64, from the transposed operand Xt[c][k]) into a
+//            2-stage ring of 128B-swizzled shared-memory tiles;
+//   warp 1   one elected thread issues 4 x 3 tcgen05.mma (M = 128, N = 256, K = 16)
+//            per K step into one TMEM accumulator and releases the stage with
+//            tcgen05.commit;
+//   warps 4-7 epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, row-major store.
+// Every mbarrier wait is bounded by a clock64 limit; on time-out the kernel sets an
+// error flag, stops issuing work, waits (bounded) for its accumulator, frees its
+// TMEM and returns.
+#include "px_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace px {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 2;
+constexpr int A_TILE = TC_BM * TC_BK * 2;                  // 16 KB
+constexpr int B_TILE = TC_BN * TC_BK * 2;                  // 32 KB
+constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;             // 96 KB
+constexpr int TC_SMEM = TC_STAGES * STAGE + 1024 + 256;    // tiles + alignment slack + barriers
+constexpr int TC_TMEM_COLS = 256;
+constexpr long long kWaitCycles = 4000000000LL;            // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false (and *err set) when the limit ran out or
+// another role of this kernel already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          volatile int* cta_abort) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*cta_abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *cta_abort = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), sm_100 descriptor version.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                            ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+
+#define TMEM_LD32(taddr, v)                                                                      \
+  asm volatile(                                                                                  \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "    \
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "    \
+      "%28, %29, %30, %31}, [%32];"                                                              \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),     \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),               \
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),            \
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),            \
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),            \
+        "=r"(v[31])                                                                              \
+      : "r"(taddr))
+
+__global__ void __launch_bounds__(256, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
+          const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+          float* __restrict__ Y, int ldy, int K, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE);
+  uint64_t* full = bars;                    // [TC_STAGES]
+  uint64_t* empty = bars + TC_STAGES;       // [TC_STAGES]
+  uint64_t* accum = bars + 2 * TC_STAGES;   // [1]
+  __shared__ uint32_t tmem_slot;
+  __shared__ int cta_abort;
+  __shared__ int n_issued, n_consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * TC_BM, c0 = blockIdx.x * TC_BN;
+  const int nk = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    cta_abort = 0;
+    n_issued = 0;
+    n_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_flag = &cta_abort;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      unsigned char* st = base + s * STAGE;
+      mbar_expect_tx(&full[s], STAGE);
+      const int kx = kt * TC_BK;
+      tma_load_2d(st, &mTh, &full[s], kx, i0);
+      tma_load_2d(st + A_TILE, &mTl, &full[s], kx, i0);
+      tma_load_2d(st + 2 * A_TILE, &mXh, &full[s], kx, c0);
+      tma_load_2d(st + 2 * A_TILE + B_TILE, &mXl, &full[s], kx, c0);
+      n_issued = kt + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, err, abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = su32(base + s * STAGE);
+      const uint64_t ah = sdesc(st), al = sdesc(st + A_TILE);
+      const uint64_t bh = sdesc(st + 2 * A_TILE), bl = sdesc(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint64_t dk = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
+        mma_bf16(tmem, ah + dk, bh + dk, (kt | kk) ? 1u : 0u);
+        mma_bf16(tmem, ah + dk, bl + dk, 1u);
+        mma_bf16(tmem, al + dk, bh + dk, 1u);
+      }
+      mma_commit(&empty[s]);
+      n_consumed = kt + 1;
+    }
+    (void)ok;
+    mma_commit(accum);   // arrives once every MMA issued above has completed
+  } else if (warp >= 4) {
+    // ---------------- epilogue: TMEM -> registers -> Y
+    const bool ok = mbar_wait(accum, 0, err, abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int wq = warp & 3;                      // TMEM lanes 32*wq .. 32*wq+31
+    const int row = i0 + wq * 32 + lane;
+    if (ok && !*abort_flag) {
+      float* yr = Y + (size_t)row * ldy + c0;
+#pragma unroll 1
+      for (int cc = 0; cc < TC_BN; cc += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)cc;
+        TMEM_LD32(taddr, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(yr + cc + 4 * q) =
+              make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      }
+    }
+  }
+  // every role is done with TMEM (the accumulator barrier was waited on by the epilogue)
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (cta_abort && threadIdx.x == 0) {
+    // after a time-out: wait (bounded) for TMA loads that were issued but never consumed
+    for (int kt = n_consumed; kt < n_issued; ++kt) {
+      const long long t0 = clock64();
+      while (!mbar_try(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS));
+  }
+}
+
+// Xt_hi[c][k], Xt_lo[c][k] (bf16, K-major) from X[k][c] (FP32, row-major); 32 x 32 tiles.
+__global__ void k_split_xt(const float* __restrict__ X, int ldx, int K, int ncols,
+                           __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl) {
+  __shared__ float tile[32][33];
+  const int k0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = X[(size_t)(k0 + r) * ldx + c0 + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const float v = tile[threadIdx.x][r];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const size_t o = (size_t)(c0 + r) * K + k0 + threadIdx.x;
+    Xh[o] = h;
+    Xl[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+  (void)ncols;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D bf16 tensor [rows][cols] (cols contiguous), box = box_cols x box_rows, 128B swizzle.
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, __nv_bfloat16* Xh,
+                            __nv_bfloat16* Xl, cudaStream_t s, long long* nl) {
+  if (np % 32 || ncols % 32) return cudaErrorInvalidValue;
+  k_split_xt<<<dim3(np / 32, ncols / 32), dim3(32, 8), 0, s>>>(X, ldx, np, ncols, Xh, Xl);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const __nv_bfloat16* Th, const __nv_bfloat16* Tl, int np,
+                           const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int ncols, float* Y,
+                           int ldy, int* err, cudaStream_t s, long long* nl) {
+  // shape contract: M and K tiles of 128 / 64 rows of T, N tiles of 256 operand columns,
+  // 16-byte aligned rows; every TMA x coordinate is a multiple of 64 bf16 (128 bytes).
+  if (np % TC_BM || ncols % TC_BN || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Th) | reinterpret_cast<uintptr_t>(Tl) |
+       reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
+    return cudaErrorMisalignedAddress;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap mTh, mTl, mXh, mXl;
+  if (!make_map(&mTh, Th, np, np, TC_BM) || !make_map(&mTl, Tl, np, np, TC_BM) ||
+      !make_map(&mXh, Xh, ncols, np, TC_BN) || !make_map(&mXl, Xl, ncols, np, TC_BN))
+    return cudaErrorInvalidValue;
+  dim3 grd(ncols / TC_BN, np / TC_BM);
+  k_tc_gemm<<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace px

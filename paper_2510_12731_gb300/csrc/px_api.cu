@@ -10,6 +10,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -65,7 +66,8 @@ struct px_handle {
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
   DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
-  DevBuf b_X32, b_Y32, b_X64, b_Y64;
+  DevBuf b_X32, b_Y32, b_X64, b_Y64, b_Xth, b_Xtl;
+  int* d_err = nullptr;         // device flag: a bounded pipeline wait ran out of time
   DevBuf b_alpha, b_q, b_mu;
   int* h_active = nullptr;      // pinned host copy of d_active [kMaxRestart]
   int* d_active = nullptr;      // device: unfrozen columns after each Krylov step
@@ -73,6 +75,7 @@ struct px_handle {
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_iter[2] = {nullptr, nullptr};
   long long nl = 0;
   double drude_n = 0.0, tau = 0.0;   // shared n, tau of the loaded structure (Eq. 6)
+  bool verbose = false;              // PX_VERBOSE=1: one stderr line per restart cycle
 };
 
 namespace {
@@ -84,7 +87,8 @@ void free_all(px_handle* h) {
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
-                    &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_alpha, &h->b_q, &h->b_mu};
+                    &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl,
+                    &h->b_alpha, &h->b_q, &h->b_mu};
   for (DevBuf* b : bufs) b->release();
 }
 
@@ -93,6 +97,7 @@ px_status validate_options(const px_options* o, std::string* msg) {
   if (o->mode < PX_MODE_AUTO || o->mode > PX_MODE_MATERIALISED) { *msg = "bad mode"; return PX_EINVAL; }
   if (o->restart_m < 1 || o->restart_m > px::kMaxRestart) { *msg = "restart_m must be in [1, 400]"; return PX_EINVAL; }
   if (o->max_iter < 1 || o->max_cycles < 1) { *msg = "max_iter and max_cycles must be >= 1"; return PX_EINVAL; }
+  if (o->max_refine < 0) { *msg = "max_refine must be >= 0"; return PX_EINVAL; }
   if (o->gs_passes < 1 || o->gs_passes > 2) { *msg = "gs_passes must be 1 or 2"; return PX_EINVAL; }
   if (!(o->tol_rel > 0.0) || !(o->tol_rel < 1.0)) { *msg = "tol_rel must be in (0, 1)"; return PX_EINVAL; }
   if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) { *msg = "inner_tol must be in (0, 1)"; return PX_EINVAL; }
@@ -283,7 +288,6 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     budget = (size_t)(0.9 * (double)fr) + h->b_T64.bytes + h->b_T32.bytes + h->b_Thi.bytes + h->b_Tlo.bytes;
   }
   if (need > budget) throw PxError{PX_ENOMEM, "materialised T does not fit the HBM budget"};
-  if (h->opt.precision == PX_BF16SPLIT) throw PxError{PX_ENOTIMPL, "bf16-split matvec is not available in this build"};
   CU(h->b_T64.ensure(np2 * sizeof(double)));
   d.T64 = h->b_T64.as<double>();
   d.T32 = nullptr;
@@ -292,8 +296,14 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     CU(h->b_T32.ensure(np2 * sizeof(float)));
     d.T32 = h->b_T32.as<float>();
   }
+  if (h->opt.precision == PX_BF16SPLIT) {
+    CU(h->b_Thi.ensure(np2 * sizeof(__nv_bfloat16)));
+    CU(h->b_Tlo.ensure(np2 * sizeof(__nv_bfloat16)));
+    d.Thi = h->b_Thi.as<__nv_bfloat16>();
+    d.Tlo = h->b_Tlo.as<__nv_bfloat16>();
+  }
   CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
-  if (d.T32) CU(px::launch_convert_T(d, true, false, s, &h->nl));
+  if (d.T32 || d.Thi) CU(px::launch_convert_T(d, d.T32 != nullptr, d.Thi != nullptr, s, &h->nl));
   CU(cudaEventRecord(h->ev_b, s));
   wait_event(h, h->ev_b);
   float ms = 0.f;
@@ -359,8 +369,13 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const int m = std::min(o.restart_m, o.max_iter);
   const int passes = o.gs_passes;
   const bool lowp = o.precision != PX_FP64;
+  const bool tc = o.precision == PX_BF16SPLIT;
+  const size_t colpad = tc ? 256 : px::kTile;   // operand column padding of the matvec kernel
+  // stopping targets of the inner (low-precision) iteration:
+  //   max(inner_tol * ||r_outer||, tol_frac * tol * ||b||)
   const double inner_tol = lowp ? o.inner_tol : 0.0;
-  const double tol_frac = lowp ? 0.1 : 0.5;
+  const double tol_abs_frac = (lowp ? 0.1 : 0.5) * o.tol_rel;
+  const int max_inner = 50;   // inner cycles per refinement round
   const int nblk = px::reduction_blocks(nu);
   long long& nl = h->nl;
   nl = 0;
@@ -390,7 +405,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   double* b = grow<double>(h->b_b, (size_t)nu * P);
   CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
   double* bnorm = grow<double>(h->b_bnorm, P);
-  double* rnorm = grow<double>(h->b_rnorm, B);
+  double* colv = grow<double>(h->b_rnorm, 3 * (size_t)B);   // rnorm | beta | target_all
+  double* rnorm = colv;
+  double* beta = colv + B;
+  double* target_all = colv + 2 * (size_t)B;
   CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
   double2* x = grow<double2>(h->b_x, (size_t)nu * B);
   double2* r = grow<double2>(h->b_r, (size_t)nu * B);
@@ -398,17 +416,19 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   int* act = grow<int>(h->b_act, B);
   CU(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)nu * B, s));
   CU(cudaMemsetAsync(iters, 0, sizeof(int) * B, s));
-  CU(px::launch_init_residual(b, nu, P, B, bnorm, r, rnorm, s, &nl));   // x = 0: r = b
+  CU(px::launch_init_residual(b, nu, P, B, bnorm, inner_tol, tol_abs_frac, r, rnorm, beta,
+                              target_all, s, &nl));
 
-  // ---- Krylov workspace for up to B active columns
-  px::ArnoldiArgs A{};
+  // ---- Krylov workspace for up to B active columns (16-byte complex elements)
+  px::KrylovArgs A{};
   A.nu = nu;
   A.m = m;
   A.nblk = nblk;
-  double2* V = grow<double2>(h->b_V, (size_t)(m + 1) * nu * B);
-  double2* W = grow<double2>(h->b_W, (size_t)nu * B);
+  A.ff = lowp ? 1 : 0;
+  void* V = grow<double2>(h->b_V, (size_t)(m + 1) * nu * B);
+  void* W = grow<double2>(h->b_W, (size_t)nu * B);
   double2* hh = grow<double2>(h->b_h, 2 * (size_t)(m + 1) * B);
-  double* part = grow<double>(h->b_part, 2 * (size_t)nblk * (m + 1) * B);
+  double2* part = grow<double2>(h->b_part, (size_t)nblk * (m + 1) * B);
   double* normpart = grow<double>(h->b_normpart, (size_t)nblk * B);
   double2* Rm = grow<double2>(h->b_R, (size_t)m * (m + 1) * B);
   double2* g = grow<double2>(h->b_g, (size_t)(m + 1) * B);
@@ -417,98 +437,133 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   double* target = grow<double>(h->b_target, B);
   int* jconv = grow<int>(h->b_jconv, B);
   double* invh = grow<double>(h->b_invh, B);
-  double2* yv = grow<double2>(h->b_y, (size_t)m * B);
-  const int ldx = (int)round_up(2 * (size_t)B, px::kTile);
+  double2* yv = grow<double2>(h->b_y, (size_t)(2 * m + 1) * B);   // y [m][B] | u [m+1][B]
+  const int ldx = (int)round_up(2 * (size_t)B, colpad);
   float* X32 = nullptr;
   float* Y32 = nullptr;
+  __nv_bfloat16* Xth = nullptr;
+  __nv_bfloat16* Xtl = nullptr;
   if (lowp) {
     X32 = grow<float>(h->b_X32, (size_t)np * ldx);
     Y32 = grow<float>(h->b_Y32, (size_t)np * ldx);
   }
+  if (tc) {
+    Xth = grow<__nv_bfloat16>(h->b_Xth, (size_t)np * ldx);
+    Xtl = grow<__nv_bfloat16>(h->b_Xtl, (size_t)np * ldx);
+  }
+  CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   double* X64 = grow<double>(h->b_X64, (size_t)np * ldx);
   double* Y64 = grow<double>(h->b_Y64, (size_t)np * ldx);
+  A.V = V; A.W = W; A.h = hh; A.part = part; A.normpart = normpart; A.R = Rm; A.g = g;
+  A.cs = cs; A.sn = sn; A.target = target; A.jconv = jconv; A.inv_h = invh;
+  A.y = yv; A.u = yv + (size_t)m * B;
+  A.active_count = h->d_active;
 
-  std::vector<int> h_act(B), h_iters(B);
-  std::vector<double> h_rnorm(B), h_bnorm(P);
+  std::vector<int> h_outer(B), h_inner(B), h_iters(B);
+  std::vector<double> h_col(3 * (size_t)B), h_bnorm(P);
   CU(cudaMemcpyAsync(h_bnorm.data(), bnorm, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
   sync_stream(h, s);
   // a column whose right-hand side is zero (e.g. no bond has a component along the
   // field) has the exact solution x = 0 and needs no iteration
-  int Bact = 0;
+  int Bout = 0;
   for (int c = 0; c < B; ++c)
-    if (h_bnorm[c % P] > 0.0) h_act[Bact++] = c;
+    if (h_bnorm[c % P] > 0.0) h_outer[Bout++] = c;
 
   size_t prof_k = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv_events, rs_events;
-  for (int cycle = 0; cycle < o.max_cycles && Bact > 0; ++cycle) {
-    st.cycles = cycle + 1;
-    // compact active columns and their shifts
-    CU(cudaMemcpyAsync(act, h_act.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
-    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
-    A.Bact = Bact;
-    A.V = V; A.W = W; A.h = hh; A.part = part; A.normpart = normpart; A.R = Rm; A.g = g;
-    A.cs = cs; A.sn = sn; A.target = target; A.jconv = jconv; A.inv_h = invh; A.y = yv;
-    A.active_count = h->d_active;
-    const int ldxa = (int)round_up(2 * (size_t)Bact, px::kTile);
-    std::memset(h->h_active, 0xff, sizeof(int) * px::kMaxRestart);
-    CU(cudaMemsetAsync(h->d_active, 0, sizeof(int) * px::kMaxRestart, s));
-    if (lowp) CU(cudaMemsetAsync(X32, 0, sizeof(float) * (size_t)np * ldxa, s));
-    else CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
-    CU(px::launch_cycle_init(A, act, rnorm, bnorm, P, inner_tol, tol_frac * o.tol_rel, s, &nl));
-    CU(px::launch_cycle_start(A, act, r, B, rnorm, lowp ? X32 : nullptr, lowp ? nullptr : X64,
-                              ldxa, s, &nl));
-
-    px::ShiftArgs sa{};
-    sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.P = P;
-    sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = d.type;
-    sa.zq = zq_act; sa.zmu = zmu_act; sa.nblk = nblk;
-    int jend = 0;
-    for (int j = 0; j < m; ++j) {
-      // ---- block matvec Y = T X (the dominant kernel)
-      cudaEvent_t e0v = nullptr, e1v = nullptr;
-      if (o.profile) {
-        e0v = pool_event(h, prof_k++);
-        e1v = pool_event(h, prof_k++);
-        CU(cudaEventRecord(e0v, s));
-      }
-      if (lowp) CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
-      else CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
-      if (o.profile) {
-        CU(cudaEventRecord(e1v, s));
-        mv_events.push_back({e0v, e1v});
-      }
-      st.matvec_launches++;
-      st.matvec_flops += 4.0 * (double)nu * nu * Bact;
-      st.matvec_bytes += (double)nu * nu * (lowp ? 4.0 : 8.0) + 2.0 * nu * 2.0 * Bact * (lowp ? 4.0 : 8.0);
-      // ---- conductance + shift: W = Kbar Y - z V_j
+  int total_cycles = 0;
+  // Refinement rounds: low-precision restarted GMRES on the current residual until every
+  // column reached its inner target, then the FP64 true residual r = b - A x.
+  for (int round = 0; Bout > 0 && total_cycles < o.max_cycles && round <= o.max_refine; ++round) {
+    std::copy(h_outer.begin(), h_outer.begin() + Bout, h_inner.begin());
+    int Bin = Bout;
+    for (int inner = 0; inner < max_inner && Bin > 0 && total_cycles < o.max_cycles; ++inner) {
+      ++total_cycles;
+      const int Bact = Bin;
+      CU(cudaMemcpyAsync(act, h_inner.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
+      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
+      A.Bact = Bact;
+      const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
+      std::memset(h->h_active, 0xff, sizeof(int) * px::kMaxRestart);
+      CU(cudaMemsetAsync(h->d_active, 0, sizeof(int) * px::kMaxRestart, s));
+      if (lowp) CU(cudaMemsetAsync(X32, 0, sizeof(float) * (size_t)np * ldxa, s));
+      else CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
+      CU(px::launch_cycle_start(A, act, r, B, beta, target_all, lowp ? X32 : nullptr,
+                                lowp ? nullptr : X64, ldxa, s, &nl));
+      px::ShiftArgs sa{};
+      sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.nblk = nblk; sa.ff = A.ff;
+      sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = d.type;
+      sa.zq = zq_act; sa.zmu = zmu_act;
       sa.Y = lowp ? (const void*)Y32 : (const void*)Y64;
       sa.ldy = ldxa;
       sa.y_is_f32 = lowp;
-      sa.X = V + (size_t)j * nu * Bact;
-      sa.ldx_c = Bact;
+      sa.jconv = jconv;
       sa.W = W;
-      sa.ldw_c = Bact;
-      CU(px::launch_shift(sa, 0, s, &nl));
-      // ---- FP64 classical Gram-Schmidt
-      for (int pass = 0; pass < passes; ++pass) {
-        CU(px::launch_dots(A, j, pass, s, &nl));
-        CU(px::launch_update(A, j, pass, pass == passes - 1, s, &nl));
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        // ---- block matvec Y = T X (the dominant kernel)
+        cudaEvent_t e0v = nullptr, e1v = nullptr;
+        if (o.profile) {
+          e0v = pool_event(h, prof_k++);
+          e1v = pool_event(h, prof_k++);
+          CU(cudaEventRecord(e0v, s));
+        }
+        if (tc) {
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, s, &nl));
+          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, h->d_err, s, &nl));
+        } else if (lowp) {
+          CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
+        } else {
+          CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+        }
+        if (o.profile) {
+          CU(cudaEventRecord(e1v, s));
+          mv_events.push_back({e0v, e1v});
+        }
+        st.matvec_launches++;
+        st.matvec_flops += 4.0 * (double)nu * nu * Bact;
+        st.matvec_bytes += (double)nu * nu * (lowp ? 4.0 : 8.0) + 2.0 * nu * 2.0 * Bact * (lowp ? 4.0 : 8.0);
+        // ---- conductance + shift: W = Kbar Y - z V_j
+        sa.X = static_cast<const char*>(V) + (size_t)j * nu * Bact * 16;
+        CU(px::launch_shift(sa, s, &nl));
+        // ---- classical Gram-Schmidt, Givens, next basis vector
+        for (int pass = 0; pass < passes; ++pass) {
+          CU(px::launch_dots(A, j, pass, s, &nl));
+          CU(px::launch_update(A, j, pass, pass == passes - 1, s, &nl));
+        }
+        CU(px::launch_givens(A, j, passes, s, &nl));
+        CU(cudaMemcpyAsync(h->h_active + j, h->d_active + j, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(px::launch_normalize(A, j, lowp ? X32 : nullptr, lowp ? nullptr : X64, ldxa, s, &nl));
+        CU(cudaEventRecord(h->ev_iter[j & 1], s));
+        jend = j + 1;
+        // lagged poll: wait for step j-1 and stop once every column has stopped
+        if (j >= 1) {
+          wait_event(h, h->ev_iter[(j - 1) & 1]);
+          if (reinterpret_cast<volatile int*>(h->h_active)[j - 1] == 0) break;
+        }
       }
-      CU(px::launch_givens(A, j, passes, s, &nl));
-      CU(cudaMemcpyAsync(h->h_active + j, h->d_active + j, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CU(px::launch_normalize(A, j, lowp ? X32 : nullptr, lowp ? nullptr : X64, ldxa, s, &nl));
-      CU(cudaEventRecord(h->ev_iter[j & 1], s));
-      jend = j + 1;
-      // lagged poll: wait for step j-1 and stop once every column is frozen
-      if (j >= 1) {
-        wait_event(h, h->ev_iter[(j - 1) & 1]);
-        if (reinterpret_cast<volatile int*>(h->h_active)[j - 1] == 0) break;
+      st.total_iters += jend;
+      if (h->verbose)
+        std::fprintf(stderr, "px: round %d inner %d columns %d steps %d\n", round, inner, Bact, jend);
+      // x += V y, r = V u (inner residual), beta = |gamma|
+      CU(px::launch_cycle_end(A, jend, act, x, r, B, beta, iters, s, &nl));
+      CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+      sync_stream(h, s);
+      int nb = 0;
+      for (int k = 0; k < Bin; ++k) {
+        const int c = h_inner[k];
+        if (!std::isfinite(h_col[B + c])) throw PxError{PX_ECUDA, "non-finite inner residual"};
+        if (h_col[B + c] > h_col[2 * (size_t)B + c] && h_iters[c] < o.max_iter) h_inner[nb++] = c;
       }
+      Bin = nb;
     }
-    st.total_iters += jend;
-    CU(px::launch_cycle_end(A, jend, act, x, B, iters, s, &nl));
 
-    // ---- FP64 true residual r = b - A x for the columns of this cycle
+    // ---- FP64 true residual r = b - A x for the columns of this round
+    const int Bact = Bout;
+    const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
+    CU(cudaMemcpyAsync(act, h_outer.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
+    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
     CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
     CU(px::launch_gather_x(x, B, act, Bact, nu, X64, ldxa, s, &nl));
     cudaEvent_t r0e = nullptr, r1e = nullptr;
@@ -524,33 +579,35 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     }
     st.resid_launches++;
     st.resid_flops += 4.0 * (double)nu * nu * Bact;
-    sa.Y = Y64;
-    sa.ldy = ldxa;
-    sa.y_is_f32 = false;
-    sa.X = x;
-    sa.act = act;
-    sa.b = b;
-    sa.R = r;
-    sa.B = B;
-    sa.normpart = normpart;
-    CU(px::launch_shift(sa, 1, s, &nl));
-    CU(px::launch_norm_finish(normpart, nblk, Bact, act, rnorm, s, &nl));
-    CU(cudaMemcpyAsync(h_rnorm.data(), rnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    if (h->verbose) std::fprintf(stderr, "px: round %d true residual of %d columns\n", round, Bact);
+    px::ResidArgs ra{};
+    ra.nu = nu; ra.N = N; ra.model = model; ra.Bact = Bact; ra.P = P; ra.B = B; ra.nblk = nblk;
+    ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = d.type;
+    ra.Y = Y64; ra.ldy = ldxa; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act; ra.zmu = zmu_act;
+    ra.R = r; ra.normpart = normpart;
+    CU(px::launch_resid(ra, s, &nl));
+    CU(px::launch_norm_finish(normpart, nblk, Bact, act, P, bnorm, inner_tol, tol_abs_frac, rnorm,
+                              beta, target_all, s, &nl));
+    CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
     sync_stream(h, s);
     int nb = 0;
-    for (int k = 0; k < Bact; ++k) {
-      int c = h_act[k];
-      if (!std::isfinite(h_rnorm[c])) throw PxError{PX_ECUDA, "non-finite residual"};
-      if (h_rnorm[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_act[nb++] = c;
+    for (int k = 0; k < Bout; ++k) {
+      const int c = h_outer[k];
+      if (!std::isfinite(h_col[c])) throw PxError{PX_ECUDA, "non-finite residual"};
+      if (h_col[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
     }
-    Bact = nb;
+    Bout = nb;
   }
+  st.cycles = total_cycles;
 
   // ---- observables (Sec. "Observables")
   CU(px::launch_observables(N, model, F, P, d.pos64, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
                             so->d_mu, so->d_sigma_pol, so->d_sigma, s, &nl));
   if (so->d_relres) CU(px::launch_relres(rnorm, bnorm, B, P, so->d_relres, s, &nl));
+  std::vector<double> h_rnorm(B);
+  int h_err = 0;
+  CU(cudaMemcpyAsync(&h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(h_rnorm.data(), rnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   CU(cudaEventRecord(h->ev_b, s));
@@ -569,6 +626,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     st.resid_ms += t;
   }
   st.kernel_launches = nl;
+  if (h_err) throw PxError{PX_ETIMEOUT, "a tensor-core pipeline wait ran out of time"};
   so->relres.resize(B);
   so->iters.resize(B);
   so->status.resize(B);
@@ -590,7 +648,8 @@ void default_options(px_options* o) {
   o->restart_m = 100;
   o->max_iter = 20000;
   o->max_cycles = 200;
-  o->gs_passes = 2;
+  o->max_refine = 20;
+  o->gs_passes = 1;
   o->tol_rel = 1e-7;
   o->inner_tol = 1e-4;
   o->kcut_eps = 1e-6;
@@ -626,6 +685,10 @@ px_status px_create(px_handle** out, const px_options* opt) {
   if (!h) return fail(nullptr, PX_ENOMEM, "host allocation failed");
   h->opt = o;
   std::memset(&h->stats, 0, sizeof(h->stats));
+  {
+    const char* v = std::getenv("PX_VERBOSE");
+    h->verbose = v && v[0] == '1';
+  }
   try {
     CU(cudaGetDevice(&h->device));
     CU(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
@@ -635,6 +698,7 @@ px_status px_create(px_handle** out, const px_options* opt) {
     CU(cudaEventCreateWithFlags(&h->ev_iter[1], cudaEventDisableTiming));
     CU(cudaHostAlloc((void**)&h->h_active, sizeof(int) * px::kMaxRestart, cudaHostAllocDefault));
     CU(cudaMalloc((void**)&h->d_active, sizeof(int) * px::kMaxRestart));
+    CU(cudaMalloc((void**)&h->d_err, sizeof(int)));
   } catch (const PxError& e) {
     g_create_error = e.msg;
     px_destroy(h);
@@ -750,6 +814,7 @@ px_status px_destroy(px_handle* h) {
     if (e) cudaEventDestroy(e);
   if (h->h_active) cudaFreeHost(h->h_active);
   if (h->d_active) cudaFree(h->d_active);
+  if (h->d_err) cudaFree(h->d_err);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
   return PX_OK;

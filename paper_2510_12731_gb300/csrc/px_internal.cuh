@@ -74,77 +74,105 @@ cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float*
                          int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl);
+// Tensor-core BF16-split matvec Y = (Th + Tl)(Xh + Xl) without the Tl Xl term.
+// Xh / Xl are the transposed operand [ncols][np] (K-major); np % 128 == 0,
+// ncols % 256 == 0.  *err is set to 1 if a pipeline wait ran out of time.
+cudaError_t launch_tc_gemm(const __nv_bfloat16* Th, const __nv_bfloat16* Tl, int np,
+                           const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int ncols, float* Y,
+                           int ldy, int* err, cudaStream_t s, long long* nl);
+// Xh[c][k] = bf16(X[k][c]), Xl[c][k] = bf16(X[k][c] - Xh[c][k]) for k < np, c < ncols.
+cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, __nv_bfloat16* Xh,
+                            __nv_bfloat16* Xl, cudaStream_t s, long long* nl);
 
-// Conductance + shift (Eq. 1 / Eq. 7 applied to a block).  mode 0 (inner):
-//   W[i][a] = (Kbar Y)_i - z X[i][a]               charge rows (i < N)
-//   W[i][a] = Y_i - z_mu(type) X[i][a]              dipole rows (wFQFmu)
-// mode 1 (true residual): R[i][act[a]] = b[i][pol(act[a])] - (same with X = x[., act[a]]),
-// plus per-block partial sums of |R|^2 in normpart[blk][a].
+// ---------------------------------------------------------------- Krylov workspace
+// The Krylov basis V and the work vector W hold complex numbers either in FP64
+// (double2, used by PX_FP64) or in double-FP32 form (float4 = re_hi, im_hi, re_lo,
+// im_lo: value = hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits), used by
+// the low-precision modes so that the Gram-Schmidt arithmetic runs on the FP32 pipe
+// with error-free transformations (GB300's FP64 pipe is 1/64 of its FP32 rate).
+struct KrylovArgs {
+  int nu, Bact, m, nblk;
+  int ff;              // 1: V, W are float4 double-FP32; 0: double2 FP64
+  void* V;             // [m+1][nu][Bact]
+  void* W;             // [nu][Bact]
+  double2* h;          // [2][m+1][Bact] projections of each Gram-Schmidt pass
+  double2* part;       // [nblk][m+1][Bact] per-row-block partial projections
+  double* normpart;    // [nblk][Bact] per-row-block partial |W|^2
+  double2* R;          // [m][m+1][Bact] rotated Hessenberg columns (column-major by step)
+  double2* g;          // [m+1][Bact] rotated right-hand side
+  double* cs;          // [m][Bact] Givens cosines
+  double2* sn;         // [m][Bact] Givens sines
+  double* target;      // [Bact] absolute residual at which a column stops this cycle
+  int* jconv;          // [Bact] basis size used (0 while the column still iterates)
+  double* inv_h;       // [Bact] scale of the next basis vector (0 after the column stopped)
+  int* active_count;   // [m] columns still iterating after step j
+  double2* y;          // [m][Bact] least-squares solution
+  double2* u;          // [m+1][Bact] coefficients of the implicit residual V u
+};
+
+// Conductance + shift apply of one Krylov step (Eq. 1 / Eq. 7 on a block):
+//   W[i][a] = (Kbar Y)_i - z_q X[i][a]         charge rows (i < N)
+//   W[i][a] = Y_i - z_mu(type) X[i][a]         dipole rows (wFQFmu)
+// with X = V_j and Y = T X from the matvec ([np][ldy] real, re/im in columns 2a, 2a+1).
 struct ShiftArgs {
-  int nu, N, model, Bact, P;
+  int nu, N, model, Bact, nblk, ff;
   const int* rowptr; const int* col; const double* val64; const float* val32;
   const int* type;
   const void* Y; int ldy; bool y_is_f32;
-  const double2* X; int ldx_c;                 // complex, column stride in complex units
+  const void* X;                                // V_j (float4 or double2), stride Bact
   const double2* zq;                            // [Bact]
   const double2* zmu;                           // [ntypes][Bact] (wFQFmu)
-  double2* W; int ldw_c;                        // inner output
-  // residual mode
-  const int* act; const double* b; double2* R; int B; double* normpart; int nblk;
+  const int* jconv;                             // columns with jconv > 0 are skipped
+  void* W;
 };
-cudaError_t launch_shift(const ShiftArgs& a, int mode, cudaStream_t s, long long* nl);
+cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl);
+
+// FP64 true residual of the active columns: R[i][act[a]] = b[i][pol] - (A x)[i] with
+// (A x) from Y = T64 x (FP64), plus per-row-block partial |R|^2 in normpart.
+struct ResidArgs {
+  int nu, N, model, Bact, P, B, nblk;
+  const int* rowptr; const int* col; const double* val64; const int* type;
+  const double* Y; int ldy;
+  const double2* x; const int* act; const double* b;
+  const double2* zq; const double2* zmu;
+  double2* R; double* normpart;
+};
+cudaError_t launch_resid(const ResidArgs& a, cudaStream_t s, long long* nl);
 
 // RHS b[i][p] (real): -Kbar V for charge rows, E0 e_p for dipole rows.
 cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* col,
                        const double* val64, const double* pos, const double* pol, int P,
                        double e0, double* b, cudaStream_t s, long long* nl);
 
-// ---------------------------------------------------------------- Arnoldi (FP64)
-struct ArnoldiArgs {
-  int nu, Bact, m;
-  double2* V;          // [m+1][nu][Bact]
-  double2* W;          // [nu][Bact]
-  double2* h;          // [2][m+1][Bact]   per-pass projections
-  double* part;        // scratch partials [nblk][m+1][Bact] (complex as 2 doubles)
-  double* normpart;    // [nblk][Bact]
-  int nblk;            // row blocks of the reductions
-  double2* R;          // [m][m+1][Bact] rotated Hessenberg columns
-  double2* g;          // [m+1][Bact]
-  double* cs;          // [m][Bact]
-  double2* sn;         // [m][Bact]
-  double* target;      // [Bact] inner residual target
-  int* jconv;          // [Bact] basis size when frozen (0 = still running)
-  double* inv_h;       // [Bact] 1 / h_{j+1,j} (0 when frozen)
-  int* active_count;   // [m] unfrozen columns after step j (device or mapped host)
-  double2* y;          // [m][Bact]
-};
-cudaError_t launch_dots(const ArnoldiArgs& a, int j, int pass, cudaStream_t s, long long* nl);
-cudaError_t launch_update(const ArnoldiArgs& a, int j, int pass, bool last, cudaStream_t s,
+// ---------------------------------------------------------------- Arnoldi
+cudaError_t launch_dots(const KrylovArgs& a, int j, int pass, cudaStream_t s, long long* nl);
+cudaError_t launch_update(const KrylovArgs& a, int j, int pass, bool last, cudaStream_t s,
                           long long* nl);
-cudaError_t launch_givens(const ArnoldiArgs& a, int j, int passes, cudaStream_t s,
+cudaError_t launch_givens(const KrylovArgs& a, int j, int passes, cudaStream_t s,
                           long long* nl);
-// V[j+1] = W * inv_h; also writes the matvec operand X (f32 [np][ldx] or f64) of V[j+1].
-cudaError_t launch_normalize(const ArnoldiArgs& a, int j, float* X32, double* X64, int ldx,
+// V[j+1] = W * inv_h; also writes the matvec operand of V[j+1] (X32 hi parts, or X64).
+cudaError_t launch_normalize(const KrylovArgs& a, int j, float* X32, double* X64, int ldx,
                              cudaStream_t s, long long* nl);
-// Cycle start: per-column init (g_0 = beta, inner target, freeze flags) and
-// V[0][i][a] = r[i][act[a]] / rnorm[act[a]] with the matching matvec operand X.
-// target[a] = max(inner_tol * beta_a, tol_abs_frac * ||b_a||): the inner residual at
-// which column a stops for this cycle (tol_abs_frac = fraction * tol_rel).
-cudaError_t launch_cycle_init(const ArnoldiArgs& a, const int* act, const double* rnorm,
-                              const double* bnorm, int P, double inner_tol, double tol_abs_frac,
-                              cudaStream_t s, long long* nl);
-cudaError_t launch_cycle_start(const ArnoldiArgs& a, const int* act, const double2* r, int B,
-                               const double* rnorm, float* X32, double* X64, int ldx,
-                               cudaStream_t s, long long* nl);
-// Cycle end: y = R^-1 g per column, x[., act[a]] += V y, iters[act[a]] += used.
-cudaError_t launch_cycle_end(const ArnoldiArgs& a, int jend, const int* act, double2* x, int B,
-                             int* iters, cudaStream_t s, long long* nl);
+// Cycle start: g_0 = beta[act[a]], target[a] = target_all[act[a]], freeze flags, and
+// V[0][i][a] = r[i][act[a]] / beta[act[a]] with its matvec operand.
+cudaError_t launch_cycle_start(const KrylovArgs& a, const int* act, const double2* r, int B,
+                               const double* beta, const double* target_all, float* X32,
+                               double* X64, int ldx, cudaStream_t s, long long* nl);
+// Cycle end: y = R^-1 g, u = Omega^H (0..0, gamma) per column; x[., act[a]] += V y,
+// r[., act[a]] = V u (the residual of the inner iteration), beta[act[a]] = |gamma|,
+// iters[act[a]] += basis size used.
+cudaError_t launch_cycle_end(const KrylovArgs& a, int jend, const int* act, double2* x,
+                             double2* r, int B, double* beta, int* iters, cudaStream_t s,
+                             long long* nl);
+// rnorm[act[a]] = sqrt(sum_blk normpart[blk][a]); beta[act[a]] = rnorm[act[a]];
+// target_all[act[a]] = max(inner_tol * rnorm, tol_abs_frac * ||b_p||).
+cudaError_t launch_norm_finish(const double* normpart, int nblk, int Bact, const int* act,
+                               int P, const double* bnorm, double inner_tol, double tol_abs_frac,
+                               double* rnorm, double* beta, double* target_all, cudaStream_t s,
+                               long long* nl);
 // Gather x[., act[a]] into the f64 matvec operand.
 cudaError_t launch_gather_x(const double2* x, int B, const int* act, int Bact, int nu,
                             double* X64, int ldx, cudaStream_t s, long long* nl);
-// rnorm[act[a]] = sqrt(sum_blk normpart[blk][a])
-cudaError_t launch_norm_finish(const double* normpart, int nblk, int Bact, const int* act,
-                               double* rnorm, cudaStream_t s, long long* nl);
 
 // Per-column shifts z_q(w) = -w (w tau + i) / (2 n tau) (Eq. 6) and, per atom type,
 // z_mu(w) = -1 / alpha^IB(w) (Eq. 8); omega in eV, alpha_ib [ntypes][F] complex.
@@ -157,9 +185,12 @@ cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntyp
 // bnorm[p] = ||b[., p]||_2
 cudaError_t launch_col_norms(const double* b, int nu, int P, double* bnorm, cudaStream_t s,
                              long long* nl);
-// x = 0: r[i][c] = b[i][c % P], rnorm[c] = bnorm[c % P]
+// x = 0: r[i][c] = b[i][c % P], rnorm[c] = beta[c] = bnorm[c % P],
+// target_all[c] = max(inner_tol * rnorm[c], tol_abs_frac * bnorm[c % P]).
 cudaError_t launch_init_residual(const double* b, int nu, int P, int B, const double* bnorm,
-                                 double2* r, double* rnorm, cudaStream_t s, long long* nl);
+                                 double inner_tol, double tol_abs_frac, double2* r,
+                                 double* rnorm, double* beta, double* target_all, cudaStream_t s,
+                                 long long* nl);
 cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P, double* out,
                           cudaStream_t s, long long* nl);
 

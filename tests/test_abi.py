@@ -65,7 +65,7 @@ def test_defaults_and_version_without_gpu(libpath):
     assert lib.px_abi_version() == 1
     o = L.Options()
     assert lib.px_options_default(C.byref(o)) == L.PX_OK
-    assert o.restart_m == 100 and o.gs_passes == 2 and o.tol_rel == 1e-7
+    assert o.restart_m == 100 and o.gs_passes == 1 and o.tol_rel == 1e-7
     assert lib.px_options_default(None) == L.PX_EINVAL
     assert lib.px_destroy(None) == L.PX_OK
 

@@ -168,3 +168,42 @@ def test_not_converged_is_reported():
     out, _ = _run(w, precision="fp64", tol_rel=1e-12, max_iter=2, restart_m=2)
     assert not out["ok"]
     assert np.any(out["status"] == 3)
+
+
+# ------------------------------------------------------------------ tensor-core BF16 split
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_bf16split_parity_after_refinement(model):
+    # N = 225 (2 row tiles of 128, ragged); 50 w x 3 pols = 150 columns -> 300 real
+    # operand columns -> 2 column tiles of 256 (ragged)
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=50, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision="bf16split", tol_rel=1e-9)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-6
+    assert stats["used_precision"] == 2
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_bf16split_before_refinement_within_1e3(model):
+    """One low-precision round (no FP64 refinement): the BF16-split operator alone."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=12, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="bf16split", tol_rel=1e-9, inner_tol=1e-8, max_refine=0,
+                  restart_m=200)
+    assert _alpha_err(out, ref) <= 1e-3
+
+
+def test_bf16split_multi_k_tiles_sphere():
+    """Na sphere r = 20 A (N = 893: 7 row tiles, 14 K steps), 40 w x 3 pols."""
+    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=40, wmin=2.0, wmax=4.0)
+    w.tol = 1e-8
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    from oracle import spectral as SP
+    md = SP.modes(st)
+    a_ref = SP.alpha(st, md, w.omega_ev, w.pol_dirs)
+    out, _ = _run(w, precision="bf16split", tol_rel=1e-8)
+    assert out["ok"]
+    num = np.linalg.norm(out["alpha"] - a_ref, axis=1)
+    den = np.linalg.norm(a_ref, axis=1)
+    assert np.max(num / den) <= 1e-5
