@@ -40,6 +40,38 @@ UNIT = "points/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                return json.load(f), "of measured"
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+def _roofline(prec, flops_per_launch, avg_launch_s, launches):
+    """Roofline entry of the block matvec (the dominant kernel) for the precision used."""
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    if prec in ("bf16split", "fp16split"):
+        peaks, src = _measured_peaks()
+        peak = float(peaks["bf16_tflops_sustained"])
+        traffic, _ = _profile_traffic("k_gemm_tc.cu", "k_tc_gemm_bf16.md")
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_tc_gemm (tcgen05 {prec} block matvec, 3 MMAs per product)",
+                "peak_source": f"bf16 dense sustained ({src}); algorithmic flops 4 n_u^2 B, "
+                               "executed tensor flops are 3x",
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
+    traffic, _ = _profile_traffic("k_gemm_simt.cu", "k_sgemm_fp32.md")
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
+            "kernel": "k_sgemm (FP32 CUDA-core block matvec on the materialised T)",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+            "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
+
+
 def _workload(name):
     from paper_2510_12731_gb300 import structures as S
     table = {
@@ -192,6 +224,8 @@ def run_ours(args, rank, world, local_rank):
     F, P, N = wl.omega_ev.size, wl.pol_dirs.shape[0], wl.natoms
     opts = dict(precision=args.precision or wl.precision, tol_rel=wl.tol, profile=1,
                 restart_m=args.restart_m, gs_passes=args.gs_passes)
+    if args.inner_tol:
+        opts["inner_tol"] = args.inner_tol
     if args.mode:
         opts["mode"] = args.mode
     solver = Solver(**opts)
@@ -291,13 +325,35 @@ def run_ours(args, rank, world, local_rank):
     prec = opts["precision"]
     avg_launch_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
     flops_per_launch = mv_flops / mv_n if mv_n else float("nan")
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    traffic, _ = _profile_traffic("k_gemm_simt.cu", "sgemm_fp32_na_ico.md")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_sgemm (FP32 CUDA-core block matvec on the materialised T)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "avg_launch_ms": avg_launch_s * 1e3, "launches": mv_n}
+    roofline = _roofline(prec, flops_per_launch, avg_launch_s, mv_n)
+
+    # ---- plain FP64 GPU solve (P0): one (frequency, polarisation) column at a time, FP64
+    # matvec (GEMV on the FP64 T) and FP64 GMRES, same tolerance; timed on a sample of
+    # columns spread over the sweep (lowest frequency included), set-up excluded.
+    p0 = None
+    if args.p0_cols > 0:
+        p0s = Solver(precision="fp64", tol_rel=wl.tol, restart_m=args.restart_m)
+        p0s.set_structure(wl.model, wl.xyz_ang, wl.type_idx, wl.types)
+        fidx = np.unique(np.linspace(0, F - 1, args.p0_cols).round().astype(int))
+        t_tot, n_ok, its = 0.0, 0, 0
+        d1 = torch.empty((1, 1), dtype=torch.float64, device=dev)
+        for fi in fidx:
+            aib = None if wl.alpha_ib is None else wl.alpha_ib[:, fi:fi + 1]
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record()
+            ok = p0s.solve_device(wl.omega_ev[fi:fi + 1], wl.pol_dirs[:1], aib, d_relres=d1)
+            q1.record()
+            torch.cuda.synchronize()
+            t_tot += q0.elapsed_time(q1) / 1e3
+            n_ok += int(ok)
+            its += p0s.stats()["total_iters"]
+        p0s.close()
+        p0 = {"value": n_ok / t_tot, "unit": UNIT, "columns_timed": int(len(fidx)),
+              "converged": n_ok, "iters_per_column": its / len(fidx),
+              "sample": f"{len(fidx)} columns (w index {fidx.tolist()}, first polarisation), "
+                        "each solved alone with FP64 matvec and FP64 GMRES; set-up excluded"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,6 +375,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk, "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "p0_fp64_gpu": p0, "vs_p0": (value / world / p0["value"]) if p0 else None,
             "points_per_step": points_per_step, "iters_per_step": iters / args.steps,
             "wall_s": wall,
         }
@@ -340,9 +397,11 @@ def main():
     ap.add_argument("--mode", default=None)
     ap.add_argument("--restart-m", dest="restart_m", type=int, default=100)
     ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=1)
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p0-cols", dest="p0_cols", type=int, default=4)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

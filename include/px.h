@@ -68,8 +68,10 @@ typedef enum { PX_WFQ = 0, PX_WFQFMU = 1 } px_model;
 typedef enum {
   PX_FP64 = 0,       /* FP64 matvec (plain double-precision solve) */
   PX_FP32 = 1,       /* FP32 matvec on the CUDA cores */
-  PX_BF16SPLIT = 2   /* T = T_hi + T_lo, X = X_hi + X_lo in bf16; tcgen05 MMA with FP32
-                        accumulation of T_hi X_hi + T_hi X_lo + T_lo X_hi */
+  PX_BF16SPLIT = 2,  /* T = T_hi + T_lo, X = X_hi + X_lo in bf16; tcgen05 MMA with FP32
+                        accumulation of T_hi X_hi + T_hi X_lo + T_lo X_hi (~16 bits) */
+  PX_FP16SPLIT = 3   /* the same three tcgen05 products on power-of-two scaled fp16 parts,
+                        lo parts scaled by 2^11 into a second accumulator (~22 bits) */
 } px_precision;
 
 typedef enum {
@@ -102,7 +104,7 @@ typedef struct {
   int gs_passes;            /* Gram-Schmidt passes (1 = CGS, 2 = CGS2); default 1 */
   double tol_rel;           /* per-column target ||b - A x||_2 / ||b||_2 in FP64; default 1e-7 */
   double inner_tol;         /* per-cycle reduction asked of the low-precision inner
-                               iteration (ignored in PX_FP64); default 1e-4 */
+                               iteration (ignored in PX_FP64); default 1e-3 */
   double kcut_eps;          /* keep bond pairs with 1 - f(r) >= kcut_eps; default 1e-6 */
   int mu_self_term;         /* 1: Gaussian self term on the T^mumu diagonal; default 0 */
   int profile;              /* 1: time every matvec launch with CUDA events; default 0 */

@@ -17,11 +17,12 @@ PX_OK, PX_EINVAL, PX_ENOMEM, PX_ENOTCONV, PX_ETIMEOUT, PX_ECUDA, PX_EBUSY, PX_EN
 STATUS_NAMES = ["PX_OK", "PX_EINVAL", "PX_ENOMEM", "PX_ENOTCONV", "PX_ETIMEOUT", "PX_ECUDA",
                 "PX_EBUSY", "PX_ENOTIMPL", "PX_ENOTFOUND"]
 PX_WFQ, PX_WFQFMU = 0, 1
-PX_FP64, PX_FP32, PX_BF16SPLIT = 0, 1, 2
+PX_FP64, PX_FP32, PX_BF16SPLIT, PX_FP16SPLIT = 0, 1, 2, 3
 PX_MODE_AUTO, PX_MODE_MATFREE, PX_MODE_MATERIALISED = 0, 1, 2
 
 MODELS = {"wfq": PX_WFQ, "wfqfmu": PX_WFQFMU}
-PRECISIONS = {"fp64": PX_FP64, "fp32": PX_FP32, "bf16split": PX_BF16SPLIT}
+PRECISIONS = {"fp64": PX_FP64, "fp32": PX_FP32, "bf16split": PX_BF16SPLIT,
+              "fp16split": PX_FP16SPLIT}
 MODES = {"auto": PX_MODE_AUTO, "matfree": PX_MODE_MATFREE, "materialised": PX_MODE_MATERIALISED}
 
 

@@ -121,7 +121,7 @@ __global__ void k_init_residual(const double* b, int nu, int P, int B, const dou
     const double bn = bnorm[c % P];
     rnorm[c] = bn;
     beta[c] = bn;
-    target_all[c] = fmax(inner_tol * bn, tol_abs_frac * bn);
+    target_all[c] = round_target(inner_tol * bn, tol_abs_frac * bn);
   }
 }
 

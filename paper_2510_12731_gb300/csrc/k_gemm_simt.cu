@@ -150,7 +150,45 @@ k_dgemm(const double* __restrict__ T, int ldt, const double* __restrict__ X, int
   }
 }
 
+// FP64 matvec for a few operand columns (NC real columns, the per-column solve): one
+// warp per row of T, lanes stride along K (coalesced 256-byte row segments), the
+// operand rows come from L1/L2, warp-shuffle reduction.
+template <int NC>
+__global__ void __launch_bounds__(256) k_dgemv(const double* __restrict__ T, int ldt,
+                                               const double* __restrict__ X, int ldx,
+                                               double* __restrict__ Y, int ldy, int nrows, int K) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nrows) return;
+  const double* Tr = T + (size_t)warp * ldt;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const double t = Tr[k];
+    const double* xr = X + (size_t)k * ldx;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = fma(t, xr[c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Y[(size_t)warp * ldy + c] = acc[c];
+}
+
 }  // namespace
+
+cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
+                         int nc, cudaStream_t s, long long* nl) {
+  const int blocks = (int)(((long long)np * 32 + 255) / 256);
+  if (nc <= 2) k_dgemv<2><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  else if (nc <= 4) k_dgemv<4><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  else if (nc <= 8) k_dgemv<8><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  else return cudaErrorInvalidValue;
+  ++*nl;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl) {

@@ -1,10 +1,13 @@
-// Block matvec Y = T X on the 5th-generation tensor cores (tcgen05), BF16 split:
+// Block matvec Y = T X on the 5th-generation tensor cores (tcgen05), split precision.
 //
-//   T = T_hi + T_lo,  X = X_hi + X_lo  (bf16 each; hi = RN(v), lo = RN(v - hi))
-//   Y = T_hi X_hi + T_hi X_lo + T_lo X_hi       (FP32 accumulation in TMEM)
-//
-// which keeps ~16 significant bits of every product (the dropped T_lo X_lo term is
-// below 2^-16 relative).  One CTA computes a 128 x 256 tile of Y:
+// BF16 split:  T = T_hi + T_lo, X = X_hi + X_lo (bf16; hi = RN(v), lo = RN(v - hi)),
+//   Y = T_hi X_hi + T_hi X_lo + T_lo X_hi  in one FP32 TMEM accumulator
+//   (~16 significant bits per product: the dropped T_lo X_lo is below 2^-16 relative).
+// FP16 split:  T' = 2^12 T, X' = 2^8 X (X is a unit vector), hi = RN_fp16(v'),
+//   lo = RN_fp16((v' - hi) 2^11), so that every part stays in fp16's normal range;
+//   D1 = T_hi X_hi and D2 = T_hi X_lo + T_lo X_hi in two TMEM accumulators,
+//   Y = (D1 + 2^-11 D2) 2^-20  (~22 significant bits per product; FP32 accumulation).
+// One CTA computes a 128 x 256 tile of Y:
 //   warp 0   TMA producer: per 64-wide K step, loads T_hi, T_lo (128 x 64) and
 //            X_hi, X_lo (256 x 64, from the transposed operand Xt[c][k]) into a
 //            2-stage ring of 128B-swizzled shared-memory tiles;
@@ -18,6 +21,7 @@
 #include "px_internal.cuh"
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 namespace px {
@@ -29,7 +33,7 @@ constexpr int A_TILE = TC_BM * TC_BK * 2;                  // 16 KB
 constexpr int B_TILE = TC_BN * TC_BK * 2;                  // 32 KB
 constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;             // 96 KB
 constexpr int TC_SMEM = TC_STAGES * STAGE + 1024 + 256;    // tiles + alignment slack + barriers
-constexpr int TC_TMEM_COLS = 256;
+constexpr int TC_TMEM_COLS = 512;   // two 128 x 256 FP32 accumulators (the BF16 mode uses one)
 constexpr long long kWaitCycles = 4000000000LL;            // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -90,15 +94,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                            ((uint32_t)(TC_BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (format 1) or F16 (format 0),
+// both K-major, M = 128, N = 256.
+constexpr uint32_t kIdescBase = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+constexpr uint32_t kIdescBF16 = kIdescBase | (1u << 7) | (1u << 10);
+constexpr uint32_t kIdescF16 = kIdescBase;
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                        uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -119,6 +126,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         "=r"(v[31])                                                                              \
       : "r"(taddr))
 
+template <int F16>
 __global__ void __launch_bounds__(256, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
           const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
@@ -192,10 +200,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUten
       const uint64_t bh = sdesc(st + 2 * A_TILE), bl = sdesc(st + 2 * A_TILE + B_TILE);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        const uint64_t dk = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
-        mma_bf16(tmem, ah + dk, bh + dk, (kt | kk) ? 1u : 0u);
-        mma_bf16(tmem, ah + dk, bl + dk, 1u);
-        mma_bf16(tmem, al + dk, bh + dk, 1u);
+        const uint64_t dk = (uint64_t)(kk * 32) >> 4;   // 16 elements = 32 bytes along K
+        const uint32_t first = (kt | kk) ? 1u : 0u;
+        if (F16) {
+          mma_f16(tmem, ah + dk, bh + dk, kIdescF16, first);
+          mma_f16(tmem + TC_BN, ah + dk, bl + dk, kIdescF16, first);
+          mma_f16(tmem + TC_BN, al + dk, bh + dk, kIdescF16, 1u);
+        } else {
+          mma_f16(tmem, ah + dk, bh + dk, kIdescBF16, first);
+          mma_f16(tmem, ah + dk, bl + dk, kIdescBF16, 1u);
+          mma_f16(tmem, al + dk, bh + dk, kIdescBF16, 1u);
+        }
       }
       mma_commit(&empty[s]);
       n_consumed = kt + 1;
@@ -215,7 +230,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUten
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)cc;
         TMEM_LD32(taddr, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (F16) {
+          uint32_t v2[32];
+          TMEM_LD32(taddr + TC_BN, v2);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const float s1 = 1.0f / 1048576.0f;             // 2^-20
+          const float s2 = 1.0f / 2147483648.0f;          // 2^-31
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            v[q] = __float_as_uint(fmaf(__uint_as_float(v2[q]), s2, __uint_as_float(v[q]) * s1));
+        } else {
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<float4*>(yr + cc + 4 * q) =
@@ -244,21 +270,29 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUten
   }
 }
 
-// Xt_hi[c][k], Xt_lo[c][k] (bf16, K-major) from X[k][c] (FP32, row-major); 32 x 32 tiles.
-__global__ void k_split_xt(const float* __restrict__ X, int ldx, int K, int ncols,
-                           __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl) {
+// Xt_hi[c][k], Xt_lo[c][k] (K-major) from X[k][c] (FP32, row-major); 32 x 32 tiles.
+// BF16: hi = RN(x), lo = RN(x - hi).  FP16: x' = 2^8 x, hi = RN(x'), lo = RN((x' - hi) 2^11).
+template <int F16>
+__global__ void k_split_xt(const float* __restrict__ X, int ldx, int K,
+                           uint16_t* __restrict__ Xh, uint16_t* __restrict__ Xl) {
   __shared__ float tile[32][33];
   const int k0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = X[(size_t)(k0 + r) * ldx + c0 + threadIdx.x];
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const float v = tile[threadIdx.x][r];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const size_t o = (size_t)(c0 + r) * K + k0 + threadIdx.x;
-    Xh[o] = h;
-    Xl[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (F16) {
+      const float vs = v * 256.0f;
+      const __half h = __float2half_rn(vs);
+      Xh[o] = __half_as_ushort(h);
+      Xl[o] = __half_as_ushort(__float2half_rn((vs - __half2float(h)) * 2048.0f));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Xh[o] = __bfloat16_as_ushort(h);
+      Xl[o] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    }
   }
-  (void)ncols;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -274,15 +308,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D bf16 tensor [rows][cols] (cols contiguous), box = box_cols x box_rows, 128B swizzle.
-bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// 2D 16-bit tensor [rows][cols] (cols contiguous), box = 64 x box_rows, 128B swizzle.
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
+              bool f16) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {cols * 2};
   cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -290,35 +326,40 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uin
 
 }  // namespace
 
-cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, __nv_bfloat16* Xh,
-                            __nv_bfloat16* Xl, cudaStream_t s, long long* nl) {
+cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
+                            uint16_t* Xl, bool f16, cudaStream_t s, long long* nl) {
   if (np % 32 || ncols % 32) return cudaErrorInvalidValue;
-  k_split_xt<<<dim3(np / 32, ncols / 32), dim3(32, 8), 0, s>>>(X, ldx, np, ncols, Xh, Xl);
+  dim3 grd(np / 32, ncols / 32), blk(32, 8);
+  if (f16) k_split_xt<1><<<grd, blk, 0, s>>>(X, ldx, np, Xh, Xl);
+  else k_split_xt<0><<<grd, blk, 0, s>>>(X, ldx, np, Xh, Xl);
   ++*nl;
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(const __nv_bfloat16* Th, const __nv_bfloat16* Tl, int np,
-                           const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int ncols, float* Y,
-                           int ldy, int* err, cudaStream_t s, long long* nl) {
+cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
+                           const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
+                           cudaStream_t s, long long* nl) {
   // shape contract: M and K tiles of 128 / 64 rows of T, N tiles of 256 operand columns,
-  // 16-byte aligned rows; every TMA x coordinate is a multiple of 64 bf16 (128 bytes).
+  // 16-byte aligned rows; every TMA x coordinate is a multiple of 64 elements (128 bytes).
   if (np % TC_BM || ncols % TC_BN || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(Th) | reinterpret_cast<uintptr_t>(Tl) |
        reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
     return cudaErrorMisalignedAddress;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   CUtensorMap mTh, mTl, mXh, mXl;
-  if (!make_map(&mTh, Th, np, np, TC_BM) || !make_map(&mTl, Tl, np, np, TC_BM) ||
-      !make_map(&mXh, Xh, ncols, np, TC_BN) || !make_map(&mXl, Xl, ncols, np, TC_BN))
+  if (!make_map(&mTh, Th, np, np, TC_BM, f16) || !make_map(&mTl, Tl, np, np, TC_BM, f16) ||
+      !make_map(&mXh, Xh, ncols, np, TC_BN, f16) || !make_map(&mXl, Xl, ncols, np, TC_BN, f16))
     return cudaErrorInvalidValue;
   dim3 grd(ncols / TC_BN, np / TC_BM);
-  k_tc_gemm<<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
+  if (f16) k_tc_gemm<1><<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
+  else k_tc_gemm<0><<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
   ++*nl;
   return cudaGetLastError();
 }

@@ -307,18 +307,28 @@ __global__ void __launch_bounds__(256) k_dots(KrylovArgs a, int j) {
   const E* V = static_cast<const E*>(a.V);
   const E* W = static_cast<const E*>(a.W);
   const size_t vstride = (size_t)a.nu * a.Bact;
+  // contiguous row range of this block, interleaved over the 8 row lanes
+  const int rows_per_blk = (a.nu + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per_blk;
+  const int r1 = min(a.nu, r0 + rows_per_blk);
   for (int k0 = 0; k0 <= j; k0 += 8) {
-    const int nk = min(8, j + 1 - k0);
+    const int nk = min(8, j + 1 - k0);   // uniform over the block
     typename TT::Acc acc[8];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) acc[kk] = TT::zero();
     if (valid) {
-      for (int i = blockIdx.y * 8 + ty; i < a.nu; i += 8 * gridDim.y) {
+      const E* Vk = V + (size_t)k0 * vstride;
+      for (int i = r0 + ty; i < r1; i += 8) {
         const size_t off = (size_t)i * a.Bact + col;
         const E w = W[off];
+        E v[8];
+        // issue every load of this row before any arithmetic
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          if (kk < nk) TT::conj_mac(acc[kk], V[(size_t)(k0 + kk) * vstride + off], w);
+          if (kk < nk) v[kk] = Vk[(size_t)kk * vstride + off];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          if (kk < nk) TT::conj_mac(acc[kk], v[kk], w);
       }
     }
 #pragma unroll
@@ -368,12 +378,24 @@ __global__ void __launch_bounds__(256) k_update(KrylovArgs a, int j, int pass, i
   E* W = static_cast<E*>(a.W);
   typename TT::Acc nacc = TT::zero();
   const size_t vstride = (size_t)a.nu * a.Bact;
+  const int rows_per_blk = (a.nu + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per_blk;
+  const int r1 = min(a.nu, r0 + rows_per_blk);
   if (valid) {
-    for (int i = blockIdx.y * 8 + ty; i < a.nu; i += 8 * gridDim.y) {
+    for (int i = r0 + ty; i < r1; i += 8) {
       const size_t off = (size_t)i * a.Bact + col;
+      const E w0 = W[off];
       typename TT::Acc acc = TT::zero();
-      for (int k = 0; k <= j; ++k) TT::mac(acc, V[(size_t)k * vstride + off], shh[k * 32 + tx]);
-      const E w = TT::sub(W[off], acc);
+      int k = 0;
+      for (; k + 8 <= j + 1; k += 8) {
+        E v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(k + q) * vstride + off];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) TT::mac(acc, v[q], shh[(k + q) * 32 + tx]);
+      }
+      for (; k <= j; ++k) TT::mac(acc, V[(size_t)k * vstride + off], shh[k * 32 + tx]);
+      const E w = TT::sub(w0, acc);
       W[off] = w;
       if (last) TT::norm_mac(nacc, w);
     }
@@ -406,28 +428,30 @@ __global__ void k_givens(KrylovArgs a, int j, int passes) {
   const double hnext = sqrt(hn2);
   double2* Rc = a.R + (size_t)j * m1 * B;   // column j of the rotated Hessenberg
   double colnorm2 = hn2;
-  for (int k = 0; k <= j; ++k) {
+  auto hcol = [&](int k) {
     double2 hk = a.h[(size_t)k * B + col];
     if (passes > 1) {
-      double2 h2 = a.h[((size_t)m1 + k) * B + col];
+      const double2 h2 = a.h[((size_t)m1 + k) * B + col];
       hk.x += h2.x;
       hk.y += h2.y;
     }
     colnorm2 += hk.x * hk.x + hk.y * hk.y;
-    Rc[(size_t)k * B + col] = hk;
-  }
-  // previous rotations G_k = [c, s; -conj(s), c]
+    return hk;
+  };
+  // previous rotations G_k = [c, s; -conj(s), c]; the rotated entry k+1 is carried in
+  // a register into rotation k+1
+  double2 x0 = hcol(0);
   for (int k = 0; k < j; ++k) {
     const double c = a.cs[(size_t)k * B + col];
     const double2 s = a.sn[(size_t)k * B + col];
-    const double2 x0 = Rc[(size_t)k * B + col], x1 = Rc[(size_t)(k + 1) * B + col];
+    const double2 x1 = hcol(k + 1);
     const double2 sx1 = cmul(s, x1);
     const double2 ncs_x0 = make_double2(-(s.x * x0.x + s.y * x0.y), -(s.x * x0.y - s.y * x0.x));
     Rc[(size_t)k * B + col] = make_double2(c * x0.x + sx1.x, c * x0.y + sx1.y);
-    Rc[(size_t)(k + 1) * B + col] = make_double2(ncs_x0.x + c * x1.x, ncs_x0.y + c * x1.y);
+    x0 = make_double2(ncs_x0.x + c * x1.x, ncs_x0.y + c * x1.y);
   }
-  // new rotation zeroing hnext under Rc[j]
-  const double2 av = Rc[(size_t)j * B + col];
+  // new rotation zeroing hnext under the rotated entry j
+  const double2 av = x0;
   const double aa = sqrt(av.x * av.x + av.y * av.y);
   const double rho = sqrt(aa * aa + hn2);
   double c;
@@ -593,7 +617,7 @@ __global__ void k_norm_finish(const double* normpart, int nblk, int Bact, const 
   const double rn = sqrt(t);
   rnorm[gc] = rn;
   beta[gc] = rn;
-  target_all[gc] = fmax(inner_tol * rn, tol_abs_frac * bnorm[gc % P]);
+  target_all[gc] = round_target(inner_tol * rn, tol_abs_frac * bnorm[gc % P]);
 }
 
 inline dim3 col_grid(int Bact, int nblk) { return dim3((Bact + 31) / 32, nblk); }

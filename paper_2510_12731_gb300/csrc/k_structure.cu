@@ -2,6 +2,8 @@
 // Gaussian kernels T (Eq. 5 and its derivatives, Sec. 2.2).  Run once per structure.
 #include "px_internal.cuh"
 
+#include <cuda_fp16.h>
+
 namespace px {
 
 namespace {
@@ -193,22 +195,49 @@ __global__ void k_build_T4(const double* __restrict__ pos, const double* __restr
   }
 }
 
-__global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32,
-                            __nv_bfloat16* Thi, __nv_bfloat16* Tlo) {
+__global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32, uint16_t* Thi,
+                            uint16_t* Tlo, int f16) {
   size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (; k < n; k += stride) {
     double v = T64[k];
     if (T32) T32[k] = (float)v;
     if (Thi) {
-      __nv_bfloat16 hi = __double2bfloat16(v);
-      Thi[k] = hi;
-      Tlo[k] = __double2bfloat16(v - (double)__bfloat162float(hi));
+      if (f16) {
+        // fp16 split of 2^12 T: both parts stay in the normal fp16 range
+        const float vs = (float)(v * 4096.0);
+        const __half hi = __float2half_rn(vs);
+        const double rem = v * 4096.0 - (double)__half2float(hi);
+        Thi[k] = __half_as_ushort(hi);
+        Tlo[k] = __half_as_ushort(__float2half_rn((float)(rem * 2048.0)));
+      } else {
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        Thi[k] = __bfloat16_as_ushort(hi);
+        Tlo[k] = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hi)));
+      }
     }
   }
 }
 
+__global__ void k_stage_pos4(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
+                             float4* p4f, double* p4d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], r2 = Rq[i] * Rq[i];
+  p4f[i] = make_float4((float)x, (float)y, (float)z, (float)r2);
+  p4d[4 * (size_t)i] = x;
+  p4d[4 * (size_t)i + 1] = y;
+  p4d[4 * (size_t)i + 2] = z;
+  p4d[4 * (size_t)i + 3] = r2;
+}
+
 }  // namespace
+
+cudaError_t launch_stage_pos4(const DevStructure& d, cudaStream_t s, long long* nl) {
+  k_stage_pos4<<<(d.N + 255) / 256, 256, 0, s>>>(d.pos64, d.Rq, d.N, d.pos4f, d.pos4d);
+  ++*nl;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_neigh_count(const double* pos, int N, const int* type, int ntypes,
                                const double* rcut2, int* counts, cudaStream_t s, long long* nl) {
@@ -252,13 +281,13 @@ cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool bf16, cudaStream_t s,
+cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaStream_t s,
                              long long* nl) {
   size_t n = (size_t)d.np * d.np;
   int threads = 256;
   int blocks = 152 * 16;
-  k_convert_T<<<blocks, threads, 0, s>>>(d.T64, n, f32 ? d.T32 : nullptr,
-                                         bf16 ? d.Thi : nullptr, bf16 ? d.Tlo : nullptr);
+  k_convert_T<<<blocks, threads, 0, s>>>(d.T64, n, f32 ? d.T32 : nullptr, split ? d.Thi : nullptr,
+                                         split ? d.Tlo : nullptr, d.t_f16 ? 1 : 0);
   ++*nl;
   return cudaGetLastError();
 }

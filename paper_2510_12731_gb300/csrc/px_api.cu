@@ -62,7 +62,7 @@ struct px_handle {
   // structure buffers
   DevBuf b_pos, b_Rq, b_Rmu, b_area, b_type, b_rowptr, b_col, b_val64, b_val32, b_counts;
   DevBuf b_pair;   // rcut2, r0, d, s tables
-  DevBuf b_T64, b_T32, b_Thi, b_Tlo;
+  DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d;
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
   DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
@@ -83,7 +83,7 @@ namespace {
 void free_all(px_handle* h) {
   DevBuf* bufs[] = {&h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
-                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
@@ -93,7 +93,7 @@ void free_all(px_handle* h) {
 }
 
 px_status validate_options(const px_options* o, std::string* msg) {
-  if (o->precision < PX_FP64 || o->precision > PX_BF16SPLIT) { *msg = "bad precision"; return PX_EINVAL; }
+  if (o->precision < PX_FP64 || o->precision > PX_FP16SPLIT) { *msg = "bad precision"; return PX_EINVAL; }
   if (o->mode < PX_MODE_AUTO || o->mode > PX_MODE_MATERIALISED) { *msg = "bad mode"; return PX_EINVAL; }
   if (o->restart_m < 1 || o->restart_m > px::kMaxRestart) { *msg = "restart_m must be in [1, 400]"; return PX_EINVAL; }
   if (o->max_iter < 1 || o->max_cycles < 1) { *msg = "max_iter and max_cycles must be >= 1"; return PX_EINVAL; }
@@ -167,6 +167,10 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     if (a.drude_n_au != types[0].drude_n_au || a.tau_au != types[0].tau_au)
       throw PxError{PX_EINVAL, "all atom types must share drude_n_au and tau_au (Eq. 1 has one z_q)"};
   }
+  if (h->opt.precision == PX_FP16SPLIT)
+    for (int t = 0; t < ntypes; ++t)
+      if (types[t].Rq_bohr < 0.5 || types[t].Rmu_bohr < 0.5)
+        throw PxError{PX_EINVAL, "fp16split needs Gaussian widths >= 0.5 bohr (fp16 range of 4096 T)"};
   std::vector<double> pos(3 * (size_t)N);
   for (int i = 0; i < N; ++i) {
     if (tidx[i] < 0 || tidx[i] >= ntypes) throw PxError{PX_EINVAL, "type index out of range"};
@@ -273,37 +277,54 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   CU(px::launch_neigh_fill(d.pos64, N, d.type, ntypes, d_rcut2, d_r0, d_d, d_s, d.area, d.rowptr,
                            d.col, d.val64, d.val32, s, &h->nl));
 
-  // T storage: this version always materialises T (FP64 for the true residual and the
-  // FP64 matvec, FP32 / bf16 copies for the low-precision matvec).
-  int mode = h->opt.mode;
-  if (mode == PX_MODE_MATFREE) throw PxError{PX_ENOTIMPL, "matrix-free mode is not available in this build"};
+  // T storage: materialised (FP64 for the true residual, plus the low-precision copy of the
+  // matvec) when it fits the HBM budget, else generated on the fly inside the matvecs.
+  const int prec = h->opt.precision;
+  const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
   size_t np2 = (size_t)d.np * d.np;
   size_t need = np2 * sizeof(double);
-  if (h->opt.precision == PX_FP32) need += np2 * sizeof(float);
-  if (h->opt.precision == PX_BF16SPLIT) need += 2 * np2 * sizeof(__nv_bfloat16);
+  if (prec == PX_FP32) need += np2 * sizeof(float);
+  if (split) need += 2 * np2 * sizeof(uint16_t);
   size_t budget = h->opt.hbm_budget_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
     CU(cudaMemGetInfo(&fr, &tot));
-    budget = (size_t)(0.9 * (double)fr) + h->b_T64.bytes + h->b_T32.bytes + h->b_Thi.bytes + h->b_Tlo.bytes;
+    budget = (size_t)(0.6 * (double)fr) + h->b_T64.bytes + h->b_T32.bytes + h->b_Thi.bytes +
+             h->b_Tlo.bytes;
   }
-  if (need > budget) throw PxError{PX_ENOMEM, "materialised T does not fit the HBM budget"};
-  CU(h->b_T64.ensure(np2 * sizeof(double)));
-  d.T64 = h->b_T64.as<double>();
+  int mode = h->opt.mode;
+  if (mode == PX_MODE_AUTO) mode = need <= budget ? PX_MODE_MATERIALISED : PX_MODE_MATFREE;
+  if (mode == PX_MODE_MATERIALISED && need > budget)
+    throw PxError{PX_ENOMEM, "materialised T does not fit the HBM budget"};
+  d.matfree = mode == PX_MODE_MATFREE;
+  d.T64 = nullptr;
   d.T32 = nullptr;
   d.Thi = d.Tlo = nullptr;
-  if (h->opt.precision == PX_FP32) {
-    CU(h->b_T32.ensure(np2 * sizeof(float)));
-    d.T32 = h->b_T32.as<float>();
+  d.t_f16 = prec == PX_FP16SPLIT;
+  if (d.matfree) {
+    if (model != PX_WFQ) throw PxError{PX_ENOTIMPL, "matrix-free mode supports PX_WFQ only in this build"};
+    if (split) throw PxError{PX_ENOTIMPL, "matrix-free mode runs PX_FP32 or PX_FP64 matvecs"};
+    CU(h->b_pos4f.ensure(sizeof(float4) * N));
+    CU(h->b_pos4d.ensure(sizeof(double) * 4 * N));
+    d.pos4f = h->b_pos4f.as<float4>();
+    d.pos4d = h->b_pos4d.as<double>();
+    CU(px::launch_stage_pos4(d, s, &h->nl));
+  } else {
+    CU(h->b_T64.ensure(np2 * sizeof(double)));
+    d.T64 = h->b_T64.as<double>();
+    if (prec == PX_FP32) {
+      CU(h->b_T32.ensure(np2 * sizeof(float)));
+      d.T32 = h->b_T32.as<float>();
+    }
+    if (split) {
+      CU(h->b_Thi.ensure(np2 * sizeof(uint16_t)));
+      CU(h->b_Tlo.ensure(np2 * sizeof(uint16_t)));
+      d.Thi = h->b_Thi.as<uint16_t>();
+      d.Tlo = h->b_Tlo.as<uint16_t>();
+    }
+    CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
+    if (d.T32 || d.Thi) CU(px::launch_convert_T(d, d.T32 != nullptr, d.Thi != nullptr, s, &h->nl));
   }
-  if (h->opt.precision == PX_BF16SPLIT) {
-    CU(h->b_Thi.ensure(np2 * sizeof(__nv_bfloat16)));
-    CU(h->b_Tlo.ensure(np2 * sizeof(__nv_bfloat16)));
-    d.Thi = h->b_Thi.as<__nv_bfloat16>();
-    d.Tlo = h->b_Tlo.as<__nv_bfloat16>();
-  }
-  CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
-  if (d.T32 || d.Thi) CU(px::launch_convert_T(d, d.T32 != nullptr, d.Thi != nullptr, s, &h->nl));
   CU(cudaEventRecord(h->ev_b, s));
   wait_event(h, h->ev_b);
   float ms = 0.f;
@@ -311,7 +332,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   h->stats.setup_ms = ms;
   h->stats.setup_launches = h->nl;
   h->stats.n_unknowns = d.nu;
-  h->stats.used_mode = PX_MODE_MATERIALISED;
+  h->stats.used_mode = d.matfree ? PX_MODE_MATFREE : PX_MODE_MATERIALISED;
   h->drude_n = types[0].drude_n_au;
   h->tau = types[0].tau_au;
   h->have_structure = true;
@@ -369,7 +390,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const int m = std::min(o.restart_m, o.max_iter);
   const int passes = o.gs_passes;
   const bool lowp = o.precision != PX_FP64;
-  const bool tc = o.precision == PX_BF16SPLIT;
+  const bool tc = o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT;
+  const bool tc_f16 = o.precision == PX_FP16SPLIT;
+  if (tc && d.Thi == nullptr) throw PxError{PX_EINVAL, "precision changed since px_set_structure"};
   const size_t colpad = tc ? 256 : px::kTile;   // operand column padding of the matvec kernel
   // stopping targets of the inner (low-precision) iteration:
   //   max(inner_tol * ||r_outer||, tol_frac * tol * ||b||)
@@ -441,15 +464,15 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const int ldx = (int)round_up(2 * (size_t)B, colpad);
   float* X32 = nullptr;
   float* Y32 = nullptr;
-  __nv_bfloat16* Xth = nullptr;
-  __nv_bfloat16* Xtl = nullptr;
+  uint16_t* Xth = nullptr;
+  uint16_t* Xtl = nullptr;
   if (lowp) {
     X32 = grow<float>(h->b_X32, (size_t)np * ldx);
     Y32 = grow<float>(h->b_Y32, (size_t)np * ldx);
   }
   if (tc) {
-    Xth = grow<__nv_bfloat16>(h->b_Xth, (size_t)np * ldx);
-    Xtl = grow<__nv_bfloat16>(h->b_Xtl, (size_t)np * ldx);
+    Xth = grow<uint16_t>(h->b_Xth, (size_t)np * ldx);
+    Xtl = grow<uint16_t>(h->b_Xtl, (size_t)np * ldx);
   }
   CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   double* X64 = grow<double>(h->b_X64, (size_t)np * ldx);
@@ -508,11 +531,17 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           e1v = pool_event(h, prof_k++);
           CU(cudaEventRecord(e0v, s));
         }
-        if (tc) {
-          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, s, &nl));
-          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, h->d_err, s, &nl));
+        if (d.matfree) {
+          if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
+          else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+        } else if (tc) {
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
+          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
+                                &nl));
         } else if (lowp) {
           CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
+        } else if (2 * Bact <= 8) {
+          CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
         } else {
           CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
         }
@@ -572,7 +601,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       r1e = pool_event(h, prof_k++);
       CU(cudaEventRecord(r0e, s));
     }
-    CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    if (d.matfree) CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    else if (2 * Bact <= 8) CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
+    else CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
     if (o.profile) {
       CU(cudaEventRecord(r1e, s));
       rs_events.push_back({r0e, r1e});
@@ -651,7 +682,7 @@ void default_options(px_options* o) {
   o->max_refine = 20;
   o->gs_passes = 1;
   o->tol_rel = 1e-7;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-3;
   o->kcut_eps = 1e-6;
   o->mu_self_term = 0;
   o->profile = 0;

@@ -45,8 +45,12 @@ struct DevStructure {
   float* val32 = nullptr;
   double* T64 = nullptr;
   float* T32 = nullptr;
-  __nv_bfloat16* Thi = nullptr;
-  __nv_bfloat16* Tlo = nullptr;
+  float4* pos4f = nullptr;     // matrix-free: x, y, z, R_q^2 (FP32)
+  double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
+  bool matfree = false;
+  uint16_t* Thi = nullptr;     // hi part of T: bf16, or fp16 of 2^12 T
+  uint16_t* Tlo = nullptr;     // lo part of T: bf16, or fp16 of (2^12 T - hi) 2^11
+  bool t_f16 = false;
 };
 
 // ---------------------------------------------------------------- launch wrappers
@@ -65,8 +69,9 @@ cudaError_t launch_neigh_fill(const double* pos, int N, const int* type, int nty
 // Dense T in FP64 (Eq. 5; wFQFmu adds the 4x4 blocks of Sec. 2.2).
 cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream_t s,
                              long long* nl);
-// T32 = float(T64); Thi = bf16(T64), Tlo = bf16(T64 - Thi).
-cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool bf16, cudaStream_t s,
+// T32 = float(T64) when f32; Thi / Tlo split of T64 (bf16, or scaled fp16 when d.t_f16)
+// when split.
+cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaStream_t s,
                              long long* nl);
 
 // Matvec Y[np][ldy] = T[np][np] X[np][ldx], columns ncols (multiple of kTile).
@@ -74,15 +79,26 @@ cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float*
                          int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl);
-// Tensor-core BF16-split matvec Y = (Th + Tl)(Xh + Xl) without the Tl Xl term.
-// Xh / Xl are the transposed operand [ncols][np] (K-major); np % 128 == 0,
-// ncols % 256 == 0.  *err is set to 1 if a pipeline wait ran out of time.
-cudaError_t launch_tc_gemm(const __nv_bfloat16* Th, const __nv_bfloat16* Tl, int np,
-                           const __nv_bfloat16* Xh, const __nv_bfloat16* Xl, int ncols, float* Y,
-                           int ldy, int* err, cudaStream_t s, long long* nl);
-// Xh[c][k] = bf16(X[k][c]), Xl[c][k] = bf16(X[k][c] - Xh[c][k]) for k < np, c < ncols.
-cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, __nv_bfloat16* Xh,
-                            __nv_bfloat16* Xl, cudaStream_t s, long long* nl);
+// Matrix-free matvecs: T generated from the staged positions (wFQ, Eq. 5).
+cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, int ldx, float* Y,
+                            int ldy, int ncols, cudaStream_t s, long long* nl);
+cudaError_t launch_dgemm_mf(const double* pos4, int n, int np, const double* X, int ldx,
+                            double* Y, int ldy, int ncols, cudaStream_t s, long long* nl);
+// pos4f / pos4d of a structure from pos64 and R_q.
+cudaError_t launch_stage_pos4(const DevStructure& d, cudaStream_t s, long long* nl);
+// FP64 matvec for nc <= 8 real operand columns (bandwidth/FP64-pipe bound GEMV).
+cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
+                         int nc, cudaStream_t s, long long* nl);
+// Tensor-core split-precision matvec Y = T X from hi/lo 16-bit parts of T and X
+// (bf16, or scaled fp16 when f16).  Xh / Xl are the transposed operand [ncols][np]
+// (K-major); np % 128 == 0, ncols % 256 == 0.  *err is set to 1 if a pipeline wait
+// ran out of time.
+cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
+                           const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
+                           cudaStream_t s, long long* nl);
+// Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
+cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
+                            uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);
 
 // ---------------------------------------------------------------- Krylov workspace
 // The Krylov basis V and the work vector W hold complex numbers either in FP64
@@ -204,5 +220,14 @@ cudaError_t launch_observables(int N, int model, int F, int P, const double* pos
                                double* sigma_pol, double* sigma, cudaStream_t s, long long* nl);
 
 int reduction_blocks(int nu);
+
+// Inner-iteration target of one refinement round: the requested reduction
+// inner_tol * ||r||, but never below the floor (a fraction of tol * ||b||).  Each
+// round contracts the true residual by about max(inner_tol, eps_op * kappa) with
+// eps_op the relative error of the low-precision operator, so a deeper inner solve
+// than that buys nothing.
+__host__ __device__ inline double round_target(double reduce_to, double floor_abs) {
+  return reduce_to > floor_abs ? reduce_to : floor_abs;
+}
 
 }  // namespace px

@@ -207,3 +207,62 @@ def test_bf16split_multi_k_tiles_sphere():
     num = np.linalg.norm(out["alpha"] - a_ref, axis=1)
     den = np.linalg.norm(a_ref, axis=1)
     assert np.max(num / den) <= 1e-5
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_fp16split_parity(model):
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=50, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision="fp16split", tol_rel=1e-9)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-6
+    assert stats["used_precision"] == 3
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_fp16split_before_refinement_beats_bf16split(model):
+    """One low-precision round (no FP64 refinement): the scaled FP16 split keeps ~22
+    bits per product against the BF16 split's ~16, so its unrefined alpha is at least
+    5x closer to the oracle, and within 1e-4."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=12, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    kw = dict(tol_rel=1e-9, inner_tol=1e-8, max_refine=0, restart_m=200)
+    e16 = _alpha_err(_run(w, precision="fp16split", **kw)[0], ref)
+    ebf = _alpha_err(_run(w, precision="bf16split", **kw)[0], ref)
+    assert e16 <= 1e-4
+    assert e16 <= ebf / 5
+
+
+# ------------------------------------------------------------------ matrix-free (on the fly)
+
+@pytest.mark.parametrize("precision,tol,alpha_tol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-7)])
+def test_matfree_parity_small(precision, tol, alpha_tol):
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=9, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision=precision, tol_rel=tol, mode="matfree")
+    assert stats["used_mode"] == 1
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= alpha_tol
+
+
+def test_matfree_matches_materialised_on_multi_tile_sphere():
+    """Na sphere r = 20 A (N = 893: 7 row tiles, ragged), 40 w x 3 pols: the on-the-fly
+    matvec and the materialised one reach the same FP64-refined solution."""
+    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=40, wmin=2.0, wmax=4.0)
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    from oracle import spectral as SP
+    a_ref = SP.alpha(st, SP.modes(st), w.omega_ev, w.pol_dirs)
+    out_mf, _ = _run(w, precision="fp32", tol_rel=1e-8, mode="matfree")
+    out_m, _ = _run(w, precision="fp32", tol_rel=1e-8, mode="materialised")
+    for out in (out_mf, out_m):
+        assert out["ok"]
+        num = np.linalg.norm(out["alpha"] - a_ref, axis=1)
+        assert np.max(num / np.linalg.norm(a_ref, axis=1)) <= 1e-5
+
+
+def test_matfree_wfqfmu_is_not_implemented():
+    from paper_2510_12731_gb300 import PxError
+    w = S.small_cluster(element="Ag", radius=6.0, model="wfqfmu", nfreq=2)
+    with _solver(mode="matfree") as s:
+        with pytest.raises(PxError, match="ENOTIMPL"):
+            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
