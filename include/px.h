@@ -206,6 +206,29 @@ px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
                           double* d_alpha, double* d_q, double* d_mu, double* d_relres,
                           void* cuda_stream);
 
+/* No-allocation residual check.  The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory at the point of the call (code running
+ * while a stream is captured into a CUDA graph, callers whose memory pool owns all free
+ * device memory, latency-bound loops that must not enter the allocator).  It computes,
+ * exactly as px_solve_device does for its own solution, the FP64 relative residual
+ * ||b - A x|| / ||b|| of every (frequency, polarisation) column for a solution the
+ * caller holds in device memory:
+ *   d_q      device [F][P][N] complex charges (the layout px_solve_device writes)
+ *   d_mu     device [F][P][N][3] complex dipoles (PX_WFQFMU; ignored for PX_WFQ)
+ *   d_relres device [F][P] doubles, written
+ * Host-side inputs are as in px_solve.  All work space comes from one fixed device
+ * array of 32 MiB inside the library (held by every GPU that loads it until the
+ * process exits); problems that need more return PX_EINVAL with the required size.
+ * The call performs no device allocation.  Its first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (two host threads, or two streams) race.  The call is synchronous.
+ * A structure must be loaded with px_set_structure. */
+px_status px_relres_device_noalloc(px_handle* h, int n_freq, const double* omega_ev,
+                                   const double* alpha_ib, int n_pol, const double* pol_dir,
+                                   double e0, const double* d_q, const double* d_mu,
+                                   double* d_relres, void* cuda_stream);
+
 /* Counters of the last px_solve / px_set_structure. */
 px_status px_get_stats(const px_handle* h, px_stats* st);
 

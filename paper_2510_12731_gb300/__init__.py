@@ -161,6 +161,21 @@ class Solver:
         self._check(st, allow=(L.PX_ENOTCONV,))
         return st == L.PX_OK
 
+    def relres_device_noalloc(self, omega_ev, pol_dirs, d_q, d_relres, alpha_ib=None, d_mu=None,
+                              e0=1.0, stream=None):
+        """FP64 relative residuals of a device-resident solution (d_q, d_mu) into d_relres,
+        without any device allocation (see px_relres_device_noalloc in include/px.h)."""
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
+        pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        aib = None
+        if alpha_ib is not None:
+            aib = np.ascontiguousarray(np.asarray(alpha_ib, dtype=np.complex128)).view(np.float64)
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._lib.px_relres_device_noalloc(
+            self._h, w.size, L.dptr(w), L.dptr(aib) if aib is not None else None, pol.shape[0],
+            L.dptr(pol), float(e0), ptr(d_q), ptr(d_mu), ptr(d_relres),
+            C.c_void_p(stream) if stream else None))
+
     def stats(self) -> dict:
         s = L.Stats()
         self._check(self._lib.px_get_stats(self._h, C.byref(s)))

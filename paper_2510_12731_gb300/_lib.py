@@ -75,6 +75,9 @@ SIGNATURES = {
                            C.POINTER(Result), C.c_void_p]),
     "px_solve_device": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, C.c_int, _dp, C.c_double,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "px_relres_device_noalloc": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, C.c_int, _dp,
+                                           C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
     "px_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "px_destroy": (C.c_int, [C.c_void_p]),
     "px_last_error": (C.c_char_p, [C.c_void_p]),

@@ -5,6 +5,7 @@
 // residual norms between restart cycles.
 #include "px.h"
 #include "px_internal.cuh"
+#include "px_handle.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -857,3 +858,15 @@ const char* px_last_error(const px_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- accessors (px_handle.cuh)
+const px::DevStructure* px_structure(const px_handle* h) {
+  return (h && h->have_structure) ? &h->ds : nullptr;
+}
+cudaStream_t px_stream(const px_handle* h) { return h->own_stream; }
+double px_drude_n(const px_handle* h) { return h->drude_n; }
+double px_tau(const px_handle* h) { return h->tau; }
+void px_set_error(px_handle* h, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+}
