@@ -51,13 +51,13 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def _roofline(prec, flops_per_launch, avg_launch_s, launches):
+def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches):
     """Roofline entry of the block matvec (the dominant kernel) for the precision used."""
     achieved = flops_per_launch / avg_launch_s / 1e12
     if prec in ("bf16split", "fp16split"):
         peaks, src = _measured_peaks()
         peak = float(peaks["bf16_tflops_sustained"])
-        traffic, _ = _profile_traffic("k_gemm_tc.cu", "k_tc_gemm_bf16.md")
+        traffic, _ = _profile_traffic("k_gemm_tc.cu", f"k_tc_gemm_{prec}.md")
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"k_tc_gemm (tcgen05 {prec} block matvec, 3 MMAs per product)",
@@ -65,6 +65,8 @@ def _roofline(prec, flops_per_launch, avg_launch_s, launches):
                                "executed tensor flops are 3x",
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
     traffic, _ = _profile_traffic("k_gemm_simt.cu", "k_sgemm_fp32.md")
+    if prec == "fp32" and mode == "matfree":
+        traffic, _ = _profile_traffic("k_gemm_mf.cu", "k_sgemm_mf_fp32.md")
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
             "kernel": "k_sgemm (FP32 CUDA-core block matvec on the materialised T)",
@@ -161,6 +163,23 @@ def _profile_traffic(kernel_file, profile_file):
     return float(m_tr.group(1)), sha
 
 
+# ---------------------------------------------------------------- multi-rank helpers
+def max_over_ranks(x, dist=None, device=None):
+    """Largest x over all ranks; x itself without an initialised process group."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(points_per_step, world, ms_per_step_max):
+    """Spectrum points per second of all ranks: every rank (a replica) solves the same
+    number of points per step; the job's step takes as long as the slowest rank."""
+    return world * points_per_step / (ms_per_step_max / 1e3)
+
+
 # ---------------------------------------------------------------- reference arm
 def _oracle_sample(wl, n_freq=1):
     """Time the FP64 CPU checker (dense LU, Eq. 1) on the first n_freq frequencies of
@@ -226,8 +245,7 @@ def run_ours(args, rank, world, local_rank):
                 restart_m=args.restart_m, gs_passes=args.gs_passes)
     if args.inner_tol:
         opts["inner_tol"] = args.inner_tol
-    if args.mode:
-        opts["mode"] = args.mode
+    opts["mode"] = args.mode or wl.mode
     solver = Solver(**opts)
     dev = torch.device("cuda", local_rank)
     d_alpha = torch.empty((F, 3, P), dtype=torch.complex128, device=dev)
@@ -275,12 +293,9 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     barrier()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     points_per_step = converged / args.steps
-    value = world * points_per_step / (ms / args.steps / 1e3)
+    value = whole_job_value(points_per_step, world, ms / args.steps)
 
     # ---- end to end through the host-buffer call, pinned host memory
     def pinned(shape, dtype):
@@ -311,11 +326,8 @@ def run_ours(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * (e2e_pts / e2e_steps) / (e2e_ms / e2e_steps / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e_value = whole_job_value(e2e_pts / e2e_steps, world, e2e_ms / e2e_steps)
     h2d = wl.xyz_ang.nbytes + wl.type_idx.nbytes + wl.omega_ev.nbytes + wl.pol_dirs.nbytes + \
         64 * len(wl.types) + (0 if wl.alpha_ib is None else wl.alpha_ib.nbytes)
     d2h = sum(v.nbytes for k, v in out.items() if isinstance(v, np.ndarray)
@@ -325,7 +337,7 @@ def run_ours(args, rank, world, local_rank):
     prec = opts["precision"]
     avg_launch_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
     flops_per_launch = mv_flops / mv_n if mv_n else float("nan")
-    roofline = _roofline(prec, flops_per_launch, avg_launch_s, mv_n)
+    roofline = _roofline(prec, opts["mode"], flops_per_launch, avg_launch_s, mv_n)
 
     # ---- plain FP64 GPU solve (P0): one (frequency, polarisation) column at a time, FP64
     # matvec (GEMV on the FP64 T) and FP64 GMRES, same tolerance; timed on a sample of
@@ -369,7 +381,8 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": wl.name, "natoms": N, "n_unknowns": N if wl.model == "wfq" else 4 * N,
                        "n_freq": F, "n_pol": P, "columns": F * P, "tol_rel": wl.tol,
-                       "precision": prec, "restart_m": args.restart_m, "gs_passes": args.gs_passes,
+                       "precision": prec, "mode": opts["mode"], "restart_m": args.restart_m,
+                       "gs_passes": args.gs_passes,
                        "l2": "no flush: the per-step working set (T, Krylov basis) is far larger than L2",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -383,6 +396,67 @@ def run_ours(args, rank, world, local_rank):
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- serving mix
+def run_serving(args, rank, world, local_rank):
+    """Continuous batching on a seeded mix: first all requests at once (service
+    capacity), then Poisson arrivals at 0.7x that request rate (latency under load)."""
+    import torch
+    from paper_2510_12731_gb300 import Server
+    from paper_2510_12731_gb300 import structures as S
+
+    torch.cuda.set_device(local_rank)
+    _, descs = S.serving_mix(n_requests=args.serve_requests, seed=12731, nmin=500,
+                             nmax=args.serve_nmax)
+    wls = [S.build_request(d) for d in descs]
+    prec = args.precision or "fp16split"
+
+    def run(arrivals):
+        with Server(max_slots=args.serve_slots, precision=prec, tol_rel=1e-7) as srv:
+            t0 = time.perf_counter()
+            ids = []
+            for wl, ta in zip(wls, arrivals):
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids.append(srv.submit(wl.model, wl.xyz_ang, wl.type_idx, wl.types, wl.omega_ev,
+                                      wl.pol_dirs, wl.alpha_ib))
+            outs = [srv.wait(i, timeout_s=3600) for i in ids]
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        pts = sum(int((o["rel_residual"] <= 1e-7).sum()) for o in outs)
+        return pts, wall, st
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    pts0, wall0, st0 = run([0.0] * len(wls))
+    rate = 0.7 * len(wls) / wall0
+    rng = np.random.Generator(np.random.PCG64(12731))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(wls)))
+    arrivals -= arrivals[0]
+    pts1, wall1, st1 = run(arrivals)
+    clk = clocks.stop()
+    cols = sum(w.ncols for w in wls)
+    line = {"metric": METRIC, "value": pts1 / wall1, "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": wall1 * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving_mix", "requests": len(wls), "columns": cols,
+                       "natoms_range": [min(w.natoms for w in wls), max(w.natoms for w in wls)],
+                       "wfqfmu_requests": sum(w.model == "wfqfmu" for w in wls),
+                       "slots": args.serve_slots, "precision": prec,
+                       "arrivals": f"Poisson, rate 0.7 x measured capacity = {rate:.3f} req/s"},
+            "clocks": clk,
+            "serving": {"capacity_points_per_s": pts0 / wall0, "capacity_wall_s": wall0,
+                        "points": pts1, "p50_latency_ms": st1["p50_latency_ms"],
+                        "p99_latency_ms": st1["p99_latency_ms"],
+                        "max_latency_ms": st1["max_latency_ms"],
+                        "structure_reuses": st1["structure_reuses"],
+                        "peak_reserved_gb": st1["peak_reserved_bytes"] / 1e9,
+                        "saturated_p50_ms": st0["p50_latency_ms"],
+                        "saturated_p99_ms": st0["p99_latency_ms"]}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -402,12 +476,17 @@ def main():
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p0-cols", dest="p0_cols", type=int, default=4)
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=40)
+    ap.add_argument("--serve-nmax", dest="serve_nmax", type=int, default=8000)
+    ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Solver", "PxError", "options"]
+__all__ = ["Solver", "Server", "PxError", "options"]
 
 PxError = L.PxError
 
@@ -179,4 +179,107 @@ class Solver:
     def stats(self) -> dict:
         s = L.Stats()
         self._check(self._lib.px_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+
+def _types_array(types):
+    return (L.AtomType * len(types))(*[
+        L.AtomType(**{k: float(t[k]) for k in (f for f, _ in L.AtomType._fields_)}) for t in types])
+
+
+class Server:
+    """Continuous-batching request loop (include/px_serve.h): slots with their own
+    streams, admission by device footprint, device-resident operators reused for
+    repeated structures."""
+
+    def __init__(self, max_slots=4, hbm_budget_bytes=0, **opts):
+        self._lib = L.lib()
+        self._s = C.c_void_p()
+        self._opt = options(**opts)
+        st = self._lib.px_server_create(C.byref(self._s), C.byref(self._opt), int(max_slots),
+                                        int(hbm_budget_bytes))
+        if st != L.PX_OK:
+            raise PxError(st, "px_server_create failed")
+        self._meta = {}
+        self._keep = {}
+
+    def close(self):
+        if self._s:
+            self._lib.px_server_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, model, xyz_ang, type_idx, types, omega_ev, pol_dirs, alpha_ib=None, e0=1.0):
+        """Queue a request; returns its id.  Inputs are copied by the library."""
+        xyz = np.ascontiguousarray(xyz_ang, dtype=np.float64).reshape(-1, 3)
+        tidx = np.ascontiguousarray(type_idx, dtype=np.int32).reshape(-1)
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
+        pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        tarr = _types_array(types)
+        aib = None
+        if alpha_ib is not None:
+            aib = np.ascontiguousarray(np.asarray(alpha_ib, dtype=np.complex128)).view(np.float64)
+        m = L.MODELS[model] if isinstance(model, str) else int(model)
+        req = L.Request(m, xyz.shape[0], L.dptr(xyz), L.iptr(tidx), tarr, len(types), w.size,
+                        L.dptr(w), L.dptr(aib) if aib is not None else None, pol.shape[0],
+                        L.dptr(pol), float(e0))
+        rid = C.c_uint64()
+        st = self._lib.px_submit(self._s, C.byref(req), C.byref(rid))
+        if st != L.PX_OK:
+            raise PxError(st, "px_submit failed")
+        self._meta[rid.value] = (m, xyz.shape[0], w.size, pol.shape[0])
+        return rid.value
+
+    def _result(self, rid):
+        m, N, F, P = self._meta[rid]
+        out = {"alpha": np.zeros((F, 3, P), np.complex128), "sigma_abs": np.zeros(F),
+               "sigma_abs_pol": np.zeros((F, P)), "q": np.zeros((F, P, N), np.complex128),
+               "mu": np.zeros((F, P, N, 3), np.complex128) if m == L.PX_WFQFMU else None,
+               "rel_residual": np.zeros((F, P)), "iters": np.zeros((F, P), np.int32),
+               "status": np.zeros((F, P), np.int32)}
+        cptr = lambda a: a.view(np.float64).ctypes.data_as(L._dp) if a is not None else None
+        res = L.Result(cptr(out["alpha"]), L.dptr(out["sigma_abs"]), L.dptr(out["sigma_abs_pol"]),
+                       cptr(out["q"]), cptr(out["mu"]), L.dptr(out["rel_residual"]),
+                       L.iptr(out["iters"]), L.iptr(out["status"]))
+        return out, res
+
+    def wait(self, rid, timeout_s=600.0):
+        """Block until request rid finishes; returns its result dict (raises on failure)."""
+        out, res = self._result(rid)
+        st = self._lib.px_wait(self._s, C.c_uint64(rid), C.byref(res), float(timeout_s))
+        if st not in (L.PX_OK, L.PX_ENOTCONV):
+            raise PxError(st, f"request {rid} failed")
+        del self._meta[rid]
+        out["ok"] = st == L.PX_OK
+        return out
+
+    def poll(self, rid):
+        """Result dict if request rid finished, else None."""
+        out, res = self._result(rid)
+        done = C.c_int(0)
+        st = self._lib.px_poll(self._s, C.c_uint64(rid), C.byref(res), C.byref(done))
+        if not done.value:
+            if st != L.PX_OK:
+                raise PxError(st, f"poll of request {rid} failed")
+            return None
+        if st not in (L.PX_OK, L.PX_ENOTCONV):
+            raise PxError(st, f"request {rid} failed")
+        del self._meta[rid]
+        out["ok"] = st == L.PX_OK
+        return out
+
+    def stats(self) -> dict:
+        s = L.ServerStats()
+        self._lib.px_server_get_stats(self._s, C.byref(s))
         return s.as_dict()

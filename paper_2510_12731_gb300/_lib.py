@@ -64,7 +64,26 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-# every function declared in include/px.h, with its ctypes signature
+class Request(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_atoms", C.c_int), ("xyz_ang", _dp), ("type_idx", _ip),
+                ("types", C.POINTER(AtomType)), ("n_types", C.c_int), ("n_freq", C.c_int),
+                ("omega_ev", _dp), ("alpha_ib", _dp), ("n_pol", C.c_int), ("pol_dir", _dp),
+                ("e0", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong),
+                ("failed", C.c_longlong), ("running", C.c_longlong), ("queued", C.c_longlong),
+                ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
+                ("max_latency_ms", C.c_double), ("busy_points", C.c_double),
+                ("wall_s", C.c_double), ("structure_reuses", C.c_longlong),
+                ("peak_reserved_bytes", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every function declared in include/px.h and include/px_serve.h, with its ctypes signature
 SIGNATURES = {
     "px_abi_version": (C.c_int, []),
     "px_options_default": (C.c_int, [C.POINTER(Options)]),
@@ -81,6 +100,12 @@ SIGNATURES = {
     "px_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "px_destroy": (C.c_int, [C.c_void_p]),
     "px_last_error": (C.c_char_p, [C.c_void_p]),
+    "px_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Options), C.c_int, C.c_size_t]),
+    "px_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "px_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]),
+    "px_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_double]),
+    "px_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "px_server_destroy": (C.c_int, [C.c_void_p]),
 }
 
 

@@ -35,14 +35,15 @@ def test_every_declared_symbol_is_exported(libpath):
 
 
 def test_binding_covers_the_header(libpath):
-    assert set(_declared("px.h")) == set(L.SIGNATURES)
+    assert set(_declared("px.h")) | set(_declared("px_serve.h")) == set(L.SIGNATURES)
 
 
 def test_struct_layouts_match_the_header(tmp_path, libpath):
     """Compile a C program against px.h and compare sizeof/offsetof with the ctypes mirror."""
     structs = {"px_atom_type": L.AtomType, "px_options": L.Options, "px_result": L.Result,
-               "px_stats": L.Stats}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "px.h"', "int main(void){"]
+               "px_stats": L.Stats, "px_request": L.Request, "px_server_stats": L.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "px.h"', '#include "px_serve.h"',
+             "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:

@@ -1,0 +1,88 @@
+"""Continuous-batching server: every request's result in a concurrent mix equals the
+same request solved alone, within the solver tolerance; admission respects the budget;
+repeated structures reuse the device-resident operators."""
+import numpy as np
+import pytest
+
+from paper_2510_12731_gb300 import structures as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def _mix():
+    ag, na, au = S.ELEMENTS["Ag"], S.ELEMENTS["Na"], S.ELEMENTS["Au"]
+    reqs = []
+    # (element, shape, model, n_freq, pols)
+    spec = [("Ag", S.sphere("fcc", 4.09, 9.0), "wfq", 11, S.XYZ),
+            ("Au", S.sphere("fcc", 4.08, 8.0), "wfqfmu", 7, S.X_ONLY),
+            ("Na", S.sphere("bcc", 4.23, 14.0), "wfq", 23, S.XYZ),
+            ("Ag", S.cuboid("fcc", 4.09, 5.0, 5.0, 12.0), "wfqfmu", 9, S.XYZ),
+            ("Ag", S.sphere("fcc", 4.09, 9.0), "wfq", 5, S.X_ONLY),      # same structure again
+            ("Na", S.sphere("bcc", 4.23, 10.0), "wfq", 31, S.X_ONLY)]
+    for el_name, xyz, model, nf, pols in spec:
+        el = S.ELEMENTS[el_name]
+        lo, hi = (2.0, 4.0) if el_name == "Na" else (2.0, 5.0)
+        w = np.linspace(lo, hi, nf)
+        aib = el.alpha_ib(w)[None, :] if model == "wfqfmu" else None
+        reqs.append(dict(model=model, xyz_ang=xyz, type_idx=np.zeros(len(xyz), np.int32),
+                         types=[el.atom_type()], omega_ev=w, pol_dirs=pols, alpha_ib=aib))
+    return reqs
+
+
+def _alone(r, **opts):
+    from paper_2510_12731_gb300 import Solver
+    with Solver(**opts) as s:
+        s.set_structure(r["model"], r["xyz_ang"], r["type_idx"], r["types"])
+        return s.solve(r["omega_ev"], r["pol_dirs"], r["alpha_ib"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
+def test_results_alone_equal_results_in_the_mix(precision):
+    from paper_2510_12731_gb300 import Server
+    reqs = _mix()
+    alone = [_alone(r, precision=precision, tol_rel=TOL) for r in reqs]
+    with Server(max_slots=3, precision=precision, tol_rel=TOL) as srv:
+        ids = [srv.submit(**r) for r in reqs]          # all arrive while others run
+        outs = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["structure_reuses"] >= 1
+    assert st["p99_latency_ms"] >= st["p50_latency_ms"] > 0
+    for a, o in zip(alone, outs):
+        assert o["ok"] and a["ok"]
+        num = np.linalg.norm(o["alpha"] - a["alpha"], axis=1)
+        den = np.linalg.norm(a["alpha"], axis=1)
+        assert np.max(num / den) <= 1e-6
+        assert np.all(o["rel_residual"] <= TOL)
+
+
+def test_admission_respects_a_small_budget():
+    """With a budget that holds one request at a time, requests still all finish (they
+    are admitted one by one) and the reserved footprint never exceeds the budget."""
+    from paper_2510_12731_gb300 import Server
+    reqs = _mix()[:3]
+    budget = 160 << 20
+    with Server(max_slots=3, hbm_budget_bytes=budget, precision="fp32", tol_rel=1e-8) as srv:
+        ids = [srv.submit(**r) for r in reqs]
+        outs = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert all(o["ok"] for o in outs)
+    assert st["peak_reserved_bytes"] <= budget
+
+
+def test_poll_and_unknown_ids():
+    from paper_2510_12731_gb300 import PxError, Server
+    r = _mix()[0]
+    with Server(max_slots=1, precision="fp32", tol_rel=1e-8) as srv:
+        rid = srv.submit(**r)
+        out = None
+        import time
+        t0 = time.time()
+        while out is None and time.time() - t0 < 120:
+            out = srv.poll(rid)
+            time.sleep(0.01)
+        assert out is not None and out["ok"]
+        with pytest.raises(KeyError):
+            srv.poll(rid)
