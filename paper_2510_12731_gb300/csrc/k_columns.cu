@@ -84,13 +84,21 @@ __global__ void k_shifts(int F, int P, int ntypes, int model, const double* omeg
 }
 
 __global__ void k_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
-                                const int* act, int Bact, double2* zq_act, double2* zmu_act) {
+                                const int* act, int Bact, double2* zq_act, double2* zmu_act,
+                                double2* amu_act) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= Bact) return;
   int c = act[a];
   zq_act[a] = zq[c];
   if (zmu)
-    for (int t = 0; t < ntypes; ++t) zmu_act[(size_t)t * Bact + a] = zmu[(size_t)t * B + c];
+    for (int t = 0; t < ntypes; ++t) {
+      const double2 z = zmu[(size_t)t * B + c];
+      zmu_act[(size_t)t * Bact + a] = z;
+      if (amu_act) {
+        const double m2 = z.x * z.x + z.y * z.y;   // -1/z = (-zr + i zi) / |z|^2
+        amu_act[(size_t)t * Bact + a] = make_double2(-z.x / m2, z.y / m2);
+      }
+    }
 }
 
 __global__ void k_col_norms(const double* b, int nu, int P, double* bnorm) {
@@ -160,9 +168,9 @@ cudaError_t launch_shifts(int F, int P, int ntypes, int model, const double* ome
 
 cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
                                  const int* act, int Bact, double2* zq_act, double2* zmu_act,
-                                 cudaStream_t s, long long* nl) {
+                                 double2* amu_act, cudaStream_t s, long long* nl) {
   k_gather_shifts<<<(Bact + 127) / 128, 128, 0, s>>>(zq, zmu, ntypes, B, act, Bact, zq_act,
-                                                     zmu_act);
+                                                     zmu_act, amu_act);
   ++*nl;
   return cudaGetLastError();
 }

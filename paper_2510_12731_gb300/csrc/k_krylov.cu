@@ -165,6 +165,23 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Matvec operand of basis entry v in row i of column col: v, or alpha^IB v on the
+// dipole rows when the wFQFmu right preconditioner is on.
+template <class E>
+__device__ __forceinline__ void write_operand(const KrylovArgs& a, int i, int col, E v, float* X32,
+                                              double* X64, int ldx) {
+  using TT = Tr<E>;
+  if (a.amu && i >= a.N) {
+    const double2 m = a.amu[(size_t)a.type[(i - a.N) / 3] * a.Bact + col];
+    const double2 w = cmul(m, TT::to_c(v));
+    if (X32) *reinterpret_cast<float2*>(X32 + (size_t)i * ldx + 2 * col) = make_float2((float)w.x, (float)w.y);
+    if (X64) *reinterpret_cast<double2*>(X64 + (size_t)i * ldx + 2 * col) = w;
+    return;
+  }
+  if (X32) *reinterpret_cast<float2*>(X32 + (size_t)i * ldx + 2 * col) = TT::hi(v);
+  if (X64) *reinterpret_cast<double2*>(X64 + (size_t)i * ldx + 2 * col) = TT::to_c(v);
+}
+
 // ------------------------------------------------------------ conductance + shift
 // (Kbar y)_i = sum_j K_ij (y_j - y_i)  (Eq. 2 with the diagonal folded in).
 template <class E, bool F32Y>
@@ -210,7 +227,10 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
       }
     } else {
       const int atom = (i - a.N) / 3;
-      zz = TT::coef(a.zmu[(size_t)a.type[atom] * a.Bact + col]);
+      // with the dipole preconditioner the operand was alpha^IB v, and
+      // -z_mu alpha^IB v = +v: the shift term becomes +v
+      zz = a.precond_mu ? TT::coef(make_double2(-1.0, 0.0))
+                        : TT::coef(a.zmu[(size_t)a.type[atom] * a.Bact + col]);
       if (F32Y) {
         const float* Y = static_cast<const float*>(a.Y);
         yr = Y[(size_t)i * a.ldy + 2 * col];
@@ -498,8 +518,7 @@ __global__ void __launch_bounds__(256) k_normalize(KrylovArgs a, int j, float* X
     const size_t off = (size_t)i * a.Bact + col;
     const E v = TT::scale(W[off], s);
     Vn[off] = v;
-    if (X32) *reinterpret_cast<float2*>(X32 + (size_t)i * ldx + 2 * col) = TT::hi(v);
-    if (X64) *reinterpret_cast<double2*>(X64 + (size_t)i * ldx + 2 * col) = TT::to_c(v);
+    write_operand<E>(a, i, col, v, X32, X64, ldx);
   }
 }
 
@@ -524,8 +543,7 @@ __global__ void __launch_bounds__(256) k_cycle_start(KrylovArgs a, const int* ac
     const double2 rv = r[(size_t)i * B + gc];
     const E v = TT::from_d2(make_double2(rv.x * s, rv.y * s));
     V0[(size_t)i * a.Bact + col] = v;
-    if (X32) *reinterpret_cast<float2*>(X32 + (size_t)i * ldx + 2 * col) = TT::hi(v);
-    if (X64) *reinterpret_cast<double2*>(X64 + (size_t)i * ldx + 2 * col) = TT::to_c(v);
+    write_operand<E>(a, i, col, v, X32, X64, ldx);
   }
 }
 
@@ -579,7 +597,7 @@ __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, d
   const E* V = static_cast<const E*>(a.V);
   for (int i = blockIdx.y * 8 + threadIdx.y; i < a.nu; i += 8 * gridDim.y) {
     const size_t off = (size_t)i * a.Bact + col;
-    double2 ax = x[(size_t)i * B + gc];
+    double2 dx = make_double2(0.0, 0.0);
     double2 ar = make_double2(0.0, 0.0);
     for (int k = 0; k <= jc; ++k) {
       const double2 v = TT::to_c(V[(size_t)k * vstride + off]);
@@ -588,10 +606,15 @@ __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, d
       ar.y += pu.y;
       if (k < jc) {
         const double2 py = cmul(v, a.y[(size_t)k * a.Bact + col]);
-        ax.x += py.x;
-        ax.y += py.y;
+        dx.x += py.x;
+        dx.y += py.y;
       }
     }
+    // x += M V y with M = alpha^IB on the dipole rows (right preconditioner)
+    if (a.amu && i >= a.N) dx = cmul(a.amu[(size_t)a.type[(i - a.N) / 3] * a.Bact + col], dx);
+    double2 ax = x[(size_t)i * B + gc];
+    ax.x += dx.x;
+    ax.y += dx.y;
     x[(size_t)i * B + gc] = ax;
     if (r) r[(size_t)i * B + gc] = ar;
   }

@@ -422,8 +422,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     CU(cudaMemcpyAsync(d_aib, alpha_ib, sizeof(double) * 2 * ntypes * F, cudaMemcpyHostToDevice, s));
   double2* zq_all = grow<double2>(h->b_zq, 2 * (size_t)B);          // [B] all, then [B] active
   double2* zq_act = zq_all + B;
-  double2* zmu_all = grow<double2>(h->b_zmu, 2 * (size_t)ntypes * B);
+  double2* zmu_all = grow<double2>(h->b_zmu, 3 * (size_t)ntypes * B);
   double2* zmu_act = zmu_all + (size_t)ntypes * B;
+  // wFQFmu right preconditioner diag(I, alpha^IB): alpha^IB of every active column
+  double2* amu_act = model == PX_WFQFMU ? zmu_all + 2 * (size_t)ntypes * B : nullptr;
   CU(px::launch_shifts(F, P, ntypes, model, d_omega, d_aib, h->drude_n, h->tau, zq_all, zmu_all,
                        s, &nl));
   double* b = grow<double>(h->b_b, (size_t)nu * P);
@@ -454,14 +456,15 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   double2* hh = grow<double2>(h->b_h, 2 * (size_t)(m + 1) * B);
   double2* part = grow<double2>(h->b_part, (size_t)nblk * (m + 1) * B);
   double* normpart = grow<double>(h->b_normpart, (size_t)nblk * B);
-  double2* Rm = grow<double2>(h->b_R, (size_t)m * (m + 1) * B);
+  // the rotated Hessenberg is sized for the longest restart a shrunken active set may use
+  double2* Rm = grow<double2>(h->b_R, (size_t)std::max(m, px::kMaxRestart) * (m + 1) * B);
   double2* g = grow<double2>(h->b_g, (size_t)(m + 1) * B);
-  double* cs = grow<double>(h->b_cs, (size_t)m * B);
-  double2* sn = grow<double2>(h->b_sn, (size_t)m * B);
+  double* cs = grow<double>(h->b_cs, (size_t)(m + 1) * B);
+  double2* sn = grow<double2>(h->b_sn, (size_t)(m + 1) * B);
   double* target = grow<double>(h->b_target, B);
   int* jconv = grow<int>(h->b_jconv, B);
   double* invh = grow<double>(h->b_invh, B);
-  double2* yv = grow<double2>(h->b_y, (size_t)(2 * m + 1) * B);   // y [m][B] | u [m+1][B]
+  double2* yv = grow<double2>(h->b_y, (size_t)(2 * m + 2) * B);   // y [m][B] | u [m+1][B]
   const int ldx = (int)round_up(2 * (size_t)B, colpad);
   float* X32 = nullptr;
   float* Y32 = nullptr;
@@ -482,6 +485,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   A.cs = cs; A.sn = sn; A.target = target; A.jconv = jconv; A.inv_h = invh;
   A.y = yv; A.u = yv + (size_t)m * B;
   A.active_count = h->d_active;
+  A.N = N;
+  A.type = d.type;
+  A.amu = amu_act;
 
   std::vector<int> h_outer(B), h_inner(B), h_iters(B);
   std::vector<double> h_col(3 * (size_t)B), h_bnorm(P);
@@ -505,8 +511,16 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       ++total_cycles;
       const int Bact = Bin;
       CU(cudaMemcpyAsync(act, h_inner.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
-      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
+      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, amu_act,
+                                  s, &nl));
       A.Bact = Bact;
+      // restart length of this cycle: the work space holds (m+1) basis vectors of B
+      // columns, so a shrunken active set runs a longer restart (up to kMaxRestart)
+      const int mc = std::max(m, (int)std::min<long long>(px::kMaxRestart,
+                                                          (long long)(m + 1) * B / Bact - 1));
+      A.m = mc;
+      A.y = yv;
+      A.u = yv + (size_t)mc * Bact;
       const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
       std::memset(h->h_active, 0xff, sizeof(int) * px::kMaxRestart);
       CU(cudaMemsetAsync(h->d_active, 0, sizeof(int) * px::kMaxRestart, s));
@@ -522,9 +536,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       sa.ldy = ldxa;
       sa.y_is_f32 = lowp;
       sa.jconv = jconv;
+      sa.precond_mu = amu_act ? 1 : 0;
       sa.W = W;
       int jend = 0;
-      for (int j = 0; j < m; ++j) {
+      for (int j = 0; j < mc; ++j) {
         // ---- block matvec Y = T X (the dominant kernel)
         cudaEvent_t e0v = nullptr, e1v = nullptr;
         if (o.profile) {
@@ -574,7 +589,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       }
       st.total_iters += jend;
       if (h->verbose)
-        std::fprintf(stderr, "px: round %d inner %d columns %d steps %d\n", round, inner, Bact, jend);
+        std::fprintf(stderr, "px: round %d inner %d columns %d steps %d (restart %d)\n", round, inner,
+                     Bact, jend, mc);
       // x += V y, r = V u (inner residual), beta = |gamma|
       CU(px::launch_cycle_end(A, jend, act, x, r, B, beta, iters, s, &nl));
       CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s));
@@ -593,7 +609,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     const int Bact = Bout;
     const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
     CU(cudaMemcpyAsync(act, h_outer.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
-    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, s, &nl));
+    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, nullptr,
+                                s, &nl));
     CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
     CU(px::launch_gather_x(x, B, act, Bact, nu, X64, ldxa, s, &nl));
     cudaEvent_t r0e = nullptr, r1e = nullptr;

@@ -124,6 +124,12 @@ struct KrylovArgs {
   int* active_count;   // [m] columns still iterating after step j
   double2* y;          // [m][Bact] least-squares solution
   double2* u;          // [m+1][Bact] coefficients of the implicit residual V u
+  // wFQFmu right preconditioner M = diag(I_N, alpha^IB I_3N) (mu = alpha^IB nu): the
+  // Krylov space is built for A M; operands of dipole rows are scaled by alpha^IB and
+  // the solution update is M V y.  amu = nullptr disables it (wFQ).
+  int N;               // atoms (dipole rows start at N)
+  const int* type;     // [N] atom types
+  const double2* amu;  // [ntypes][Bact] alpha^IB = -1 / z_mu of each active column
 };
 
 // Conductance + shift apply of one Krylov step (Eq. 1 / Eq. 7 on a block):
@@ -139,6 +145,7 @@ struct ShiftArgs {
   const double2* zq;                            // [Bact]
   const double2* zmu;                           // [ntypes][Bact] (wFQFmu)
   const int* jconv;                             // columns with jconv > 0 are skipped
+  int precond_mu;                               // 1: dipole rows use the right preconditioner
   void* W;
 };
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl);
@@ -195,9 +202,11 @@ cudaError_t launch_gather_x(const double2* x, int B, const int* act, int Bact, i
 cudaError_t launch_shifts(int F, int P, int ntypes, int model, const double* omega_ev,
                           const double* alpha_ib, double n, double tau, double2* zq,
                           double2* zmu, cudaStream_t s, long long* nl);
+// zq_act[a] = zq[act[a]], zmu_act[t][a] = zmu[t][act[a]], and (when amu_act is not null)
+// amu_act[t][a] = -1 / zmu_act[t][a] = alpha^IB.
 cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntypes, int B,
                                  const int* act, int Bact, double2* zq_act, double2* zmu_act,
-                                 cudaStream_t s, long long* nl);
+                                 double2* amu_act, cudaStream_t s, long long* nl);
 // bnorm[p] = ||b[., p]||_2
 cudaError_t launch_col_norms(const double* b, int nu, int P, double* bnorm, cudaStream_t s,
                              long long* nl);

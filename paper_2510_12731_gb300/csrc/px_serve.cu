@@ -122,6 +122,28 @@ size_t reserved_bytes(const px_server* s) {
 // less than 2 s.
 void admit(px_server* s) {
   const double now = seconds_since(s->t0);
+  // structure affinity: a free slot first takes a queued request (among the first 16)
+  // for the structure it already holds, keeping its operators on the device
+  for (Slot* sl : s->slots) {
+    if (sl->req || !sl->h || sl->key == 0) continue;
+    int look = 0;
+    for (auto it = s->queue.begin(); it != s->queue.end() && look < 16; ++it, ++look) {
+      Req* r = *it;
+      if (r->key != sl->key || r->mode != sl->mode) continue;
+      size_t others = 0;
+      for (const Slot* o : s->slots)
+        if (o != sl) others += std::max(o->retained, o->req ? o->req->footprint : 0);
+      if (others + std::max(sl->retained, r->footprint) > s->budget) break;
+      ++s->reuses;
+      sl->req = r;
+      r->state = 1;
+      r->t_start = now;
+      s->peak_reserved = std::max(s->peak_reserved, reserved_bytes(s));
+      s->queue.erase(it);
+      sl->cv.notify_one();
+      break;
+    }
+  }
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     Req* r = *it;
     // free slot, preferring one that already holds this structure

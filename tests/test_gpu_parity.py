@@ -266,3 +266,19 @@ def test_matfree_wfqfmu_is_not_implemented():
     with _solver(mode="matfree") as s:
         with pytest.raises(PxError, match="ENOTIMPL"):
             s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+
+
+def test_wfqfmu_rod_converges_with_dipole_preconditioner():
+    """An Ag rod of N = 1,175 atoms (4,700 unknowns), where unpreconditioned GMRES(100)
+    stalls above 3.5 eV: the diag(I, alpha^IB) right preconditioner converges every
+    column, and alpha matches the oracle's LU."""
+    el = S.ELEMENTS["Ag"]
+    xyz = S.cuboid("fcc", 4.09, 9.0, 9.0, 30.0)
+    w_ev = np.array([2.5, 3.5, 4.5])
+    w = S.Workload("rod", "wfqfmu", xyz, np.zeros(len(xyz), np.int32), [el.atom_type()], w_ev,
+                   np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0]]), el.alpha_ib(w_ev)[None, :])
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision="fp16split", tol_rel=1e-8)
+    assert out["ok"]
+    assert np.max(out["iters"]) < 3000
+    assert _alpha_err(out, ref) <= 1e-5
