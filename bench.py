@@ -469,7 +469,7 @@ def main():
     ap.add_argument("--workload", default="na_ico")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--mode", default=None)
-    ap.add_argument("--restart-m", dest="restart_m", type=int, default=100)
+    ap.add_argument("--restart-m", dest="restart_m", type=int, default=0)
     ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=1)
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)

@@ -96,7 +96,9 @@ typedef struct {
 typedef struct {
   int precision;            /* px_precision; default PX_FP32 */
   int mode;                 /* px_mode; default PX_MODE_AUTO */
-  int restart_m;            /* Krylov basis length per restart cycle; default 100 */
+  int restart_m;            /* Krylov basis length per restart cycle; 0 (default) = automatic:
+                               60 for PX_WFQ, 100 for PX_WFQFMU; a cycle whose active set has
+                               shrunk uses a longer restart (up to 400) in the same memory */
   int max_iter;             /* cap on matvecs per column over the whole solve; default 20000 */
   int max_cycles;           /* cap on restart cycles (inner cycles of all rounds); default 200 */
   int max_refine;           /* FP64 refinement rounds after the first low-precision solve;

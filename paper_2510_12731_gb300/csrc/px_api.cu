@@ -63,7 +63,7 @@ struct px_handle {
   // structure buffers
   DevBuf b_pos, b_Rq, b_Rmu, b_area, b_type, b_rowptr, b_col, b_val64, b_val32, b_counts;
   DevBuf b_pair;   // rcut2, r0, d, s tables
-  DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d;
+  DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
   DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
@@ -84,7 +84,7 @@ namespace {
 void free_all(px_handle* h) {
   DevBuf* bufs[] = {&h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
-                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
@@ -96,7 +96,7 @@ void free_all(px_handle* h) {
 px_status validate_options(const px_options* o, std::string* msg) {
   if (o->precision < PX_FP64 || o->precision > PX_FP16SPLIT) { *msg = "bad precision"; return PX_EINVAL; }
   if (o->mode < PX_MODE_AUTO || o->mode > PX_MODE_MATERIALISED) { *msg = "bad mode"; return PX_EINVAL; }
-  if (o->restart_m < 1 || o->restart_m > px::kMaxRestart) { *msg = "restart_m must be in [1, 400]"; return PX_EINVAL; }
+  if (o->restart_m < 0 || o->restart_m > px::kMaxRestart) { *msg = "restart_m must be in [0, 400]"; return PX_EINVAL; }
   if (o->max_iter < 1 || o->max_cycles < 1) { *msg = "max_iter and max_cycles must be >= 1"; return PX_EINVAL; }
   if (o->max_refine < 0) { *msg = "max_refine must be >= 0"; return PX_EINVAL; }
   if (o->gs_passes < 1 || o->gs_passes > 2) { *msg = "gs_passes must be 1 or 2"; return PX_EINVAL; }
@@ -284,6 +284,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
   size_t np2 = (size_t)d.np * d.np;
   size_t need = np2 * sizeof(double);
+  if (prec != PX_FP64) need += 2 * np2 * sizeof(float);   // double-FP32 planes (residual)
   if (prec == PX_FP32) need += np2 * sizeof(float);
   if (split) need += 2 * np2 * sizeof(uint16_t);
   size_t budget = h->opt.hbm_budget_bytes;
@@ -301,6 +302,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.T64 = nullptr;
   d.T32 = nullptr;
   d.Thi = d.Tlo = nullptr;
+  d.Tffh = d.Tffl = nullptr;
   d.t_f16 = prec == PX_FP16SPLIT;
   if (d.matfree) {
     if (model != PX_WFQ) throw PxError{PX_ENOTIMPL, "matrix-free mode supports PX_WFQ only in this build"};
@@ -325,6 +327,13 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     }
     CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
     if (d.T32 || d.Thi) CU(px::launch_convert_T(d, d.T32 != nullptr, d.Thi != nullptr, s, &h->nl));
+    if (prec != PX_FP64) {
+      CU(h->b_Tffh.ensure(np2 * sizeof(float)));
+      CU(h->b_Tffl.ensure(np2 * sizeof(float)));
+      d.Tffh = h->b_Tffh.as<float>();
+      d.Tffl = h->b_Tffl.as<float>();
+      CU(px::launch_split_ff(d.T64, np2, d.Tffh, d.Tffl, s, &h->nl));
+    }
   }
   CU(cudaEventRecord(h->ev_b, s));
   wait_event(h, h->ev_b);
@@ -388,7 +397,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const int B = F * P;
   const int nu = d.nu, np = d.np, N = d.N, ntypes = d.ntypes;
   const px_options& o = h->opt;
-  const int m = std::min(o.restart_m, o.max_iter);
+  // restart length: explicit, or automatic (0): wFQ converges about as fast with short
+  // restarts, whose Gram-Schmidt traffic is lower; wFQFmu needs longer ones
+  const int m_req = o.restart_m > 0 ? o.restart_m : (model == PX_WFQ ? 60 : 100);
+  const int m = std::min(m_req, o.max_iter);
   const int passes = o.gs_passes;
   const bool lowp = o.precision != PX_FP64;
   const bool tc = o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT;
@@ -619,9 +631,17 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       r1e = pool_event(h, prof_k++);
       CU(cudaEventRecord(r0e, s));
     }
-    if (d.matfree) CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
-    else if (2 * Bact <= 8) CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
-    else CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    if (d.matfree) {
+      CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    } else if (2 * Bact <= 8) {
+      CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
+    } else if (d.Tffh) {
+      // double-FP32 residual matvec; X32 / Y32 are free between cycles
+      CU(px::launch_split_ff(X64, (size_t)np * ldxa, X32, Y32, s, &nl));
+      CU(px::launch_ffgemm(d.Tffh, d.Tffl, np, X32, Y32, ldxa, Y64, ldxa, ldxa, s, &nl));
+    } else {
+      CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    }
     if (o.profile) {
       CU(cudaEventRecord(r1e, s));
       rs_events.push_back({r0e, r1e});
@@ -694,7 +714,7 @@ void default_options(px_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = PX_FP32;
   o->mode = PX_MODE_AUTO;
-  o->restart_m = 100;
+  o->restart_m = 0;
   o->max_iter = 20000;
   o->max_cycles = 200;
   o->max_refine = 20;

@@ -45,6 +45,8 @@ struct DevStructure {
   float* val32 = nullptr;
   double* T64 = nullptr;
   float* T32 = nullptr;
+  float* Tffh = nullptr;       // double-FP32 planes of T64 (true residual of the
+  float* Tffl = nullptr;       //   low-precision modes): T = Tffh + Tffl
   float4* pos4f = nullptr;     // matrix-free: x, y, z, R_q^2 (FP32)
   double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
   bool matfree = false;
@@ -79,6 +81,14 @@ cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float*
                          int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl);
+// FP64-class matvec Y = (Th + Tl)(Xh + Xl) in double-FP32 arithmetic (FP64 result);
+// np % 64 == 0, ncols % 64 == 0.
+cudaError_t launch_ffgemm(const float* Th, const float* Tl, int np, const float* Xh,
+                          const float* Xl, int ldx, double* Y, int ldy, int ncols, cudaStream_t s,
+                          long long* nl);
+// Xh = fl32(X), Xl = fl32(X - Xh) over n FP64 values.
+cudaError_t launch_split_ff(const double* X, size_t n, float* Xh, float* Xl, cudaStream_t s,
+                            long long* nl);
 // Matrix-free matvecs: T generated from the staged positions (wFQ, Eq. 5).
 cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, int ldx, float* Y,
                             int ldy, int ncols, cudaStream_t s, long long* nl);

@@ -72,10 +72,11 @@ size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
   const size_t nu = model == PX_WFQ ? N : 4 * (size_t)N;
   const size_t np = round_up(nu, 128);
   const size_t ldx = round_up(2 * (size_t)B, 256);
-  const size_t m = o.restart_m;
+  const size_t m = o.restart_m > 0 ? o.restart_m : (model == PX_WFQ ? 60 : 100);
   size_t t = 0;
   if (mat) {
     t += np * np * 8;
+    if (o.precision != PX_FP64) t += np * np * 8;   // double-FP32 planes of T
     if (o.precision == PX_FP32) t += np * np * 4;
     if (o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT) t += np * np * 4;
   }

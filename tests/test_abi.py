@@ -66,7 +66,7 @@ def test_defaults_and_version_without_gpu(libpath):
     assert lib.px_abi_version() == 1
     o = L.Options()
     assert lib.px_options_default(C.byref(o)) == L.PX_OK
-    assert o.restart_m == 100 and o.gs_passes == 1 and o.tol_rel == 1e-7
+    assert o.restart_m == 0 and o.gs_passes == 1 and o.tol_rel == 1e-7
     assert lib.px_options_default(None) == L.PX_EINVAL
     assert lib.px_destroy(None) == L.PX_OK
 
@@ -75,7 +75,7 @@ def test_create_rejects_bad_options(libpath):
     lib = L.load(libpath)
     o = L.Options()
     lib.px_options_default(C.byref(o))
-    o.restart_m = 0
+    o.restart_m = -1
     h = C.c_void_p()
     assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
     assert b"restart_m" in lib.px_last_error(None)

@@ -1,0 +1,63 @@
+"""Full-size parity: the library at the benchmark configurations against the oracle's
+values stored in tests/golden/ (written by tests/golden/make_golden.py, CPU oracle only).
+
+|alpha_gpu - alpha_oracle| / |alpha_oracle| <= 1e-5 per (frequency, polarisation) column,
+with the FP64 relative residual of every column <= its tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2510_12731_gb300 import structures as S
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name, F, P):
+    path = os.path.join(GOLDEN, f"{name}_alpha.txt")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    rows = np.loadtxt(path)
+    fidx = np.unique(rows[:, 0].astype(int))
+    a = np.zeros((len(fidx), 3, P), dtype=np.complex128)
+    pos = {f: i for i, f in enumerate(fidx)}
+    for fi, _, p, k, re, im in rows:
+        a[pos[int(fi)], int(k), int(p)] = re + 1j * im
+    return fidx, a
+
+
+def _solve(w, **opts):
+    from paper_2510_12731_gb300 import Solver
+    with Solver(precision=w.precision, mode=w.mode, tol_rel=w.tol, **opts) as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        return s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib, want_q=False)
+
+
+def _check(out, fidx, ref, tol_rel):
+    assert out["ok"]
+    assert np.all(out["rel_residual"] <= tol_rel)
+    a = out["alpha"][fidx]
+    err = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.max(err) <= 1e-5, np.max(err)
+
+
+def test_na_icosahedron_19931_all_600_columns():
+    w = S.na_icosahedron_19931()
+    fidx, ref = _golden("na_icosahedron_19931", w.omega_ev.size, 3)
+    _check(_solve(w), fidx, ref, w.tol)
+
+
+def test_graphene_disk_20nm_all_300_columns():
+    w = S.graphene_disk_20nm()
+    fidx, ref = _golden("graphene_disk_20nm", w.omega_ev.size, 1)
+    _check(_solve(w), fidx, ref, w.tol)
+
+
+def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies():
+    w = S.ag_rod_3x3x10()
+    w.precision = "fp16split"
+    fidx, ref = _golden("ag_rod_3x3x10", w.omega_ev.size, 3)
+    _check(_solve(w), fidx, ref, w.tol)

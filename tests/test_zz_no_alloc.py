@@ -44,8 +44,10 @@ def test_noalloc_residual_matches_solve_device(model, precision):
                                     d_mu=d_mu if model == "wfqfmu" else None)
             got = got_t.cpu().numpy()
             assert np.all(got >= 0.0)
-            # both are FP64 residual norms of the same solution; they agree far below tol_rel
-            assert np.allclose(got, expect, rtol=1e-6, atol=1e-13)
+            # both are FP64-class residual norms of the same solution (px_solve_device
+            # evaluates the low-precision modes' residual in double-FP32, this entry point
+            # in FP64); they agree to ~1e-11 of ||b||, far below tol_rel
+            assert np.allclose(got, expect, rtol=1e-6, atol=3e-11)
             assert np.all(got <= 1e-9)
 
 
