@@ -38,6 +38,7 @@ UNIT = "points/s"
 
 # FP32 CUDA-core peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 
 
 def _measured_peaks():
@@ -63,6 +64,12 @@ def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches):
                 "kernel": f"k_tc_gemm (tcgen05 {prec} block matvec, 3 MMAs per product)",
                 "peak_source": f"bf16 dense sustained ({src}); algorithmic flops 4 n_u^2 B, "
                                "executed tensor flops are 3x",
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
+    if prec == "fp64":
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_dgemm / k_dgemv (FP64 CUDA-core block matvec)",
+                "peak_source": "GB300 dense FP64 rate, 1.25 TFLOP/s nominal",
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
     traffic, _ = _profile_traffic("k_gemm_simt.cu", "k_sgemm_fp32.md")
     if prec == "fp32" and mode == "matfree":
@@ -241,8 +248,13 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     wl = _workload(args.workload)
     F, P, N = wl.omega_ev.size, wl.pol_dirs.shape[0], wl.natoms
-    opts = dict(precision=args.precision or wl.precision, tol_rel=wl.tol, profile=1,
-                restart_m=args.restart_m, gs_passes=args.gs_passes)
+    # profile = 1 times every matvec launch with CUDA events over the timed region (the
+    # roofline's kernel duration); restart cycles then run as per-kernel launches.  With
+    # --graphs the timed region runs each restart cycle as one graph launch and the
+    # kernel duration comes from one profiled step after the timed region.
+    opts = dict(precision=args.precision or wl.precision, tol_rel=wl.tol,
+                profile=0 if args.graphs else 1, cycle_graphs=1 if args.graphs else 0,
+                restart_m=args.restart_m, gs_passes=args.gs_passes, basis=args.basis)
     if args.inner_tol:
         opts["inner_tol"] = args.inner_tol
     opts["mode"] = args.mode or wl.mode
@@ -335,6 +347,16 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (the block matvec)
     prec = opts["precision"]
+    kernel_timing = "CUDA events around every matvec launch over the timed region"
+    if args.graphs:
+        with Solver(**{**opts, "profile": 1, "cycle_graphs": 0}) as ps:
+            ps.set_structure(wl.model, wl.xyz_ang, wl.type_idx, wl.types)
+            ps.solve_device(wl.omega_ev, wl.pol_dirs, wl.alpha_ib, d_alpha=d_alpha, d_q=d_q,
+                            d_relres=d_rr)
+            pst = ps.stats()
+        mv_ms, mv_n, mv_flops = pst["matvec_ms"], pst["matvec_launches"], pst["matvec_flops"]
+        kernel_timing = "CUDA events around every matvec launch of one profiled step after the timed region"
+    graph_launches = st["graph_launches"]
     avg_launch_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
     flops_per_launch = mv_flops / mv_n if mv_n else float("nan")
     roofline = _roofline(prec, opts["mode"], flops_per_launch, avg_launch_s, mv_n)
@@ -382,12 +404,14 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": wl.name, "natoms": N, "n_unknowns": N if wl.model == "wfq" else 4 * N,
                        "n_freq": F, "n_pol": P, "columns": F * P, "tol_rel": wl.tol,
                        "precision": prec, "mode": opts["mode"], "restart_m": args.restart_m,
-                       "gs_passes": args.gs_passes,
+                       "gs_passes": args.gs_passes, "basis": args.basis,
+                       "cycle_graphs": bool(args.graphs),
                        "l2": "no flush: the per-step working set (T, Krylov basis) is far larger than L2",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": launches, "graph_launches_last_step": graph_launches,
+            "roofline": {**roofline, "kernel_timing": kernel_timing}, "cpu_baseline": cpu,
             "p0_fp64_gpu": p0, "vs_p0": (value / world / p0["value"]) if p0 else None,
             "points_per_step": points_per_step, "iters_per_step": iters / args.steps,
             "wall_s": wall,
@@ -471,6 +495,9 @@ def main():
     ap.add_argument("--mode", default=None)
     ap.add_argument("--restart-m", dest="restart_m", type=int, default=0)
     ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=1)
+    ap.add_argument("--basis", default="auto", choices=["auto", "fp64", "ff32", "fp32"])
+    ap.add_argument("--graphs", action="store_true",
+                    help="run restart cycles as graph launches in the timed region")
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)

@@ -63,8 +63,9 @@ typedef enum {
 typedef enum { PX_WFQ = 0, PX_WFQFMU = 1 } px_model;
 
 /* Arithmetic of the block matvec Y = T X inside the Krylov iteration.  The
- * orthogonalisation, the true residual and the refinement are FP64 in every
- * mode. */
+ * Hessenberg least squares, the true residual and the refinement are FP64 (or
+ * double-FP32, ~48 bits) in every mode; the storage of the Krylov basis is
+ * chosen by px_basis. */
 typedef enum {
   PX_FP64 = 0,       /* FP64 matvec (plain double-precision solve) */
   PX_FP32 = 1,       /* FP32 matvec on the CUDA cores */
@@ -73,6 +74,21 @@ typedef enum {
   PX_FP16SPLIT = 3   /* the same three tcgen05 products on power-of-two scaled fp16 parts,
                         lo parts scaled by 2^11 into a second accumulator (~22 bits) */
 } px_precision;
+
+/* Storage and arithmetic of the Krylov basis V and the Gram-Schmidt sweeps over it
+ * (the sweeps are bound by HBM bandwidth, so the element size sets their cost). */
+typedef enum {
+  PX_BASIS_AUTO = 0,  /* PX_FP64: FP64; low-precision matvecs: FP32 for restart cycles of
+                         up to 128 vectors, double-FP32 for longer ones (shrunken active
+                         sets), where classical Gram-Schmidt in FP32 loses orthogonality */
+  PX_BASIS_FP64 = 1,  /* FP64 complex, 16 bytes per entry */
+  PX_BASIS_FF32 = 2,  /* double-FP32 complex (hi + lo pairs, ~48 bits), 16 bytes per
+                         entry; arithmetic on the FP32 pipe with error-free transforms */
+  PX_BASIS_FP32 = 3   /* FP32 complex, 8 bytes per entry; low-precision matvecs only:
+                         each refinement round asks the inner iteration for a modest
+                         reduction (inner_tol), which the FP32 basis delivers, and the
+                         FP64 true residual corrects what it loses */
+} px_basis;
 
 typedef enum {
   PX_MODE_AUTO = 0,         /* materialise T if it fits the HBM budget, else matrix-free */
@@ -97,13 +113,30 @@ typedef struct {
   int precision;            /* px_precision; default PX_FP32 */
   int mode;                 /* px_mode; default PX_MODE_AUTO */
   int restart_m;            /* Krylov basis length per restart cycle; 0 (default) = automatic:
-                               60 for PX_WFQ, 100 for PX_WFQFMU; a cycle whose active set has
-                               shrunk uses a longer restart (up to 400) in the same memory */
+                               60 for low-precision PX_WFQ solves, 100 for PX_WFQFMU and for
+                               PX_FP64 solves; a cycle whose active set has shrunk uses a
+                               longer restart (up to 400) in the same memory */
   int max_iter;             /* cap on matvecs per column over the whole solve; default 20000 */
   int max_cycles;           /* cap on restart cycles (inner cycles of all rounds); default 200 */
   int max_refine;           /* FP64 refinement rounds after the first low-precision solve;
                                0 returns the first round's result; default 20 */
   int gs_passes;            /* Gram-Schmidt passes (1 = CGS, 2 = CGS2); default 1 */
+  int basis;                /* px_basis; default PX_BASIS_AUTO.  PX_FP64 accepts only
+                               AUTO and PX_BASIS_FP64 */
+  int gemm_tiles;           /* tile shape of the tensor-core matvec: 0 (default) = autotuned
+                               per (rows, columns) shape on first use, cached per process;
+                               1 = 128 x 256 tiles, 2-stage ring; 2 = 128 x 128 tiles,
+                               3-stage ring.  Every choice gives bit-identical results */
+  int cycle_graphs;         /* 1 (default): each restart cycle is one CUDA graph launch whose
+                               device-side while loop runs the Krylov steps (matvec, shift,
+                               Gram-Schmidt, Givens, normalisation) until every column stopped
+                               or the basis is full; graphs are cached per handle and shape.
+                               0: one launch per kernel with a per-step host poll.  profile = 1
+                               always uses the latter (events around every matvec) */
+  int sort_atoms;           /* 1 (default): the device reorders atoms along a Morton curve of
+                               their positions (neighbours at nearby indices); per-atom
+                               inputs and outputs stay in the caller's order.  0: keep the
+                               caller's order */
   double tol_rel;           /* per-column target ||b - A x||_2 / ||b||_2 in FP64; default 1e-7 */
   double inner_tol;         /* per-cycle reduction asked of the low-precision inner
                                iteration (ignored in PX_FP64); default 1e-3 */
@@ -146,6 +179,9 @@ typedef struct {
   long long n_unknowns;    /* n_u: N (wFQ) or 4N (wFQFmu) */
   int used_mode;           /* px_mode actually used */
   int used_precision;      /* px_precision actually used */
+  int gemm_tiles_used;     /* tensor-core matvec tile shape of the first (widest) cycle:
+                              1 or 2 as in px_options.gemm_tiles; 0 without that matvec */
+  long long graph_launches; /* restart cycles run as one graph launch each */
 } px_stats;
 
 typedef struct px_handle px_handle;

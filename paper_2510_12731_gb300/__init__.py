@@ -26,10 +26,10 @@ PxError = L.PxError
 def options(**kw) -> L.Options:
     """A px_options record: library defaults, overridden by keyword arguments.
 
-    Keywords: precision ("fp64" | "fp32" | "bf16split"), mode ("auto" |
-    "matfree" | "materialised"), restart_m, max_iter, max_cycles, gs_passes,
-    tol_rel, inner_tol, kcut_eps, mu_self_term, profile, hbm_budget_bytes,
-    device_wait_limit_s.
+    Keywords: precision ("fp64" | "fp32" | "bf16split" | "fp16split"), mode ("auto" |
+    "matfree" | "materialised"), basis ("auto" | "fp64" | "ff32" | "fp32"), restart_m,
+    max_iter, max_cycles, max_refine, gs_passes, tol_rel, inner_tol, kcut_eps,
+    mu_self_term, profile, hbm_budget_bytes, device_wait_limit_s.
     """
     o = L.Options()
     L.lib().px_options_default(C.byref(o))
@@ -38,6 +38,8 @@ def options(**kw) -> L.Options:
             v = L.PRECISIONS[v] if isinstance(v, str) else int(v)
         elif k == "mode":
             v = L.MODES[v] if isinstance(v, str) else int(v)
+        elif k == "basis":
+            v = L.BASES[v] if isinstance(v, str) else int(v)
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)

@@ -19,11 +19,13 @@ STATUS_NAMES = ["PX_OK", "PX_EINVAL", "PX_ENOMEM", "PX_ENOTCONV", "PX_ETIMEOUT",
 PX_WFQ, PX_WFQFMU = 0, 1
 PX_FP64, PX_FP32, PX_BF16SPLIT, PX_FP16SPLIT = 0, 1, 2, 3
 PX_MODE_AUTO, PX_MODE_MATFREE, PX_MODE_MATERIALISED = 0, 1, 2
+PX_BASIS_AUTO, PX_BASIS_FP64, PX_BASIS_FF32, PX_BASIS_FP32 = 0, 1, 2, 3
 
 MODELS = {"wfq": PX_WFQ, "wfqfmu": PX_WFQFMU}
 PRECISIONS = {"fp64": PX_FP64, "fp32": PX_FP32, "bf16split": PX_BF16SPLIT,
               "fp16split": PX_FP16SPLIT}
 MODES = {"auto": PX_MODE_AUTO, "matfree": PX_MODE_MATFREE, "materialised": PX_MODE_MATERIALISED}
+BASES = {"auto": PX_BASIS_AUTO, "fp64": PX_BASIS_FP64, "ff32": PX_BASIS_FF32, "fp32": PX_BASIS_FP32}
 
 
 class AtomType(C.Structure):
@@ -35,7 +37,8 @@ class AtomType(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("mode", C.c_int), ("restart_m", C.c_int),
                 ("max_iter", C.c_int), ("max_cycles", C.c_int), ("max_refine", C.c_int),
-                ("gs_passes", C.c_int),
+                ("gs_passes", C.c_int), ("basis", C.c_int), ("gemm_tiles", C.c_int),
+                ("cycle_graphs", C.c_int), ("sort_atoms", C.c_int),
                 ("tol_rel", C.c_double), ("inner_tol", C.c_double), ("kcut_eps", C.c_double),
                 ("mu_self_term", C.c_int), ("profile", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("device_wait_limit_s", C.c_double)]
@@ -58,7 +61,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_longlong), ("setup_launches", C.c_longlong),
                 ("cycles", C.c_int),
                 ("total_iters", C.c_longlong), ("n_unknowns", C.c_longlong),
-                ("used_mode", C.c_int), ("used_precision", C.c_int)]
+                ("used_mode", C.c_int), ("used_precision", C.c_int),
+                ("gemm_tiles_used", C.c_int), ("graph_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

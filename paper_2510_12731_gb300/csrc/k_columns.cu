@@ -10,7 +10,7 @@ namespace {
 // One block per column c = f * P + p: dipole, polarisability and per-polarisation
 // absorption (Sec. "Observables").
 __global__ void k_observables(int N, int model, int F, int P, const double* __restrict__ pos,
-                              const double2* __restrict__ x, double e0,
+                              const int* __restrict__ perm, const double2* __restrict__ x, double e0,
                               const double* __restrict__ omega_ev, const double* __restrict__ pol,
                               double2* alpha, double2* qout, double2* muout, double* sigma_pol) {
   const int c = blockIdx.x;
@@ -23,13 +23,14 @@ __global__ void k_observables(int N, int model, int F, int P, const double* __re
       d[2 * k] += q.x * pos[3 * i + k];
       d[2 * k + 1] += q.y * pos[3 * i + k];
     }
-    if (qout) qout[(size_t)c * N + i] = q;
+    const int io = perm[i];   // per-atom outputs in the caller's atom order
+    if (qout) qout[(size_t)c * N + io] = q;
     if (model == 1) {
       for (int k = 0; k < 3; ++k) {
         double2 mu = x[(size_t)(N + 3 * i + k) * B + c];
         d[2 * k] += mu.x;
         d[2 * k + 1] += mu.y;
-        if (muout) muout[((size_t)c * N + i) * 3 + k] = mu;
+        if (muout) muout[((size_t)c * N + io) * 3 + k] = mu;
       }
     }
   }
@@ -143,10 +144,10 @@ __global__ void k_relres(const double* rnorm, const double* bnorm, int B, int P,
 }  // namespace
 
 cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
-                               const double2* x, double e0, const double* omega_ev,
+                               const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
                                double* sigma_pol, double* sigma, cudaStream_t s, long long* nl) {
-  k_observables<<<F * P, 256, 0, s>>>(N, model, F, P, pos, x, e0, omega_ev, pol, alpha, qout,
+  k_observables<<<F * P, 256, 0, s>>>(N, model, F, P, pos, perm, x, e0, omega_ev, pol, alpha, qout,
                                       muout, sigma_pol);
   ++*nl;
   if (sigma && sigma_pol && P == 3) {

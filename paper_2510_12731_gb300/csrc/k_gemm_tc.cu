@@ -7,14 +7,17 @@
 //   lo = RN_fp16((v' - hi) 2^11), so that every part stays in fp16's normal range;
 //   D1 = T_hi X_hi and D2 = T_hi X_lo + T_lo X_hi in two TMEM accumulators,
 //   Y = (D1 + 2^-11 D2) 2^-20  (~22 significant bits per product; FP32 accumulation).
-// One CTA computes a 128 x 256 tile of Y:
+// One CTA computes a 128 x BN tile of Y (BN = 256 with a 2-stage ring, or BN = 128
+// with a 3-stage ring; launch_tc_gemm's autotuner picks one per shape):
 //   warp 0   TMA producer: per 64-wide K step, loads T_hi, T_lo (128 x 64) and
-//            X_hi, X_lo (256 x 64, from the transposed operand Xt[c][k]) into a
-//            2-stage ring of 128B-swizzled shared-memory tiles;
-//   warp 1   one elected thread issues 4 x 3 tcgen05.mma (M = 128, N = 256, K = 16)
-//            per K step into one TMEM accumulator and releases the stage with
+//            X_hi, X_lo (BN x 64, from the transposed operand Xt[c][k]) into a
+//            ring of 128B-swizzled shared-memory tiles;
+//   warp 1   one elected thread issues 4 x 3 tcgen05.mma (M = 128, N = BN, K = 16)
+//            per K step into the TMEM accumulator(s) and releases the stage with
 //            tcgen05.commit;
-//   warps 4-7 epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, row-major store.
+//   warps 4-7 epilogue: tcgen05.ld of the 128 x BN FP32 accumulator, row-major store.
+// Every output element accumulates its K products in the same order for either tile
+// shape, so the variants give bit-identical Y.
 // Every mbarrier wait is bounded by a clock64 limit; on time-out the kernel sets an
 // error flag, stops issuing work, waits (bounded) for its accumulator, frees its
 // TMEM and returns.
@@ -24,17 +27,29 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+
 namespace px {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 2;
+constexpr int TC_BM = 128, TC_BK = 64;
 constexpr int A_TILE = TC_BM * TC_BK * 2;                  // 16 KB
-constexpr int B_TILE = TC_BN * TC_BK * 2;                  // 32 KB
-constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;             // 96 KB
-constexpr int TC_SMEM = TC_STAGES * STAGE + 1024 + 256;    // tiles + alignment slack + barriers
-constexpr int TC_TMEM_COLS = 512;   // two 128 x 256 FP32 accumulators (the BF16 mode uses one)
 constexpr long long kWaitCycles = 4000000000LL;            // ~2 s at 2 GHz
+
+// Tile configuration: BN operand columns per CTA, STAGES-deep ring.
+template <int BN, int STAGES>
+struct TcCfg {
+  static constexpr int B_TILE = BN * TC_BK * 2;                     // 32 / 16 KB
+  static constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;              // 96 / 64 KB
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;           // + alignment, barriers
+  static constexpr int TMEM_COLS = 2 * BN;   // two 128 x BN FP32 accumulators (BF16 uses one)
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -95,10 +110,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (format 1) or F16 (format 0),
-// both K-major, M = 128, N = 256.
-constexpr uint32_t kIdescBase = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-constexpr uint32_t kIdescBF16 = kIdescBase | (1u << 7) | (1u << 10);
-constexpr uint32_t kIdescF16 = kIdescBase;
+// both K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc(bool f16) {
+  return (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24) |
+         (f16 ? 0u : ((1u << 7) | (1u << 10)));
+}
 
 __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                         uint32_t acc) {
@@ -126,11 +143,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         "=r"(v[31])                                                                              \
       : "r"(taddr))
 
-template <int F16>
+template <int F16, int TC_BN, int TC_STAGES>
 __global__ void __launch_bounds__(256, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
           const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
           float* __restrict__ Y, int ldy, int K, int* err) {
+  using Cfg = TcCfg<TC_BN, TC_STAGES>;
+  constexpr int B_TILE = Cfg::B_TILE, STAGE = Cfg::STAGE, TC_TMEM_COLS = Cfg::TMEM_COLS;
+  constexpr uint32_t kIdescF16 = idesc<TC_BN>(true), kIdescBF16 = idesc<TC_BN>(false);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -336,32 +356,130 @@ cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t
   return cudaGetLastError();
 }
 
+namespace {
+
+template <int F16, int BN, int ST>
+cudaError_t launch_variant(const CUtensorMap& mTh, const CUtensorMap& mTl, const CUtensorMap& mXh,
+                           const CUtensorMap& mXl, int np, int ncols, float* Y, int ldy, int* err,
+                           cudaStream_t s) {
+  dim3 grd(ncols / BN, np / TC_BM);
+  k_tc_gemm<F16, BN, ST><<<grd, 256, TcCfg<BN, ST>::SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
+  return cudaGetLastError();
+}
+
+template <int F16>
+cudaError_t set_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F16, 256, 2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcCfg<256, 2>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_gemm<F16, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcCfg<128, 3>::SMEM);
+  return e;
+}
+
+// Tile variants: 0 = 128 x 256 tiles, 2-stage ring; 1 = 128 x 128 tiles, 3-stage ring.
+constexpr int kTcVariants = 2;
+constexpr int kTcBN[kTcVariants] = {256, 128};
+
+cudaError_t launch_tc_variant(int v, bool f16, const CUtensorMap* m, int np, int ncols, float* Y,
+                              int ldy, int* err, cudaStream_t s) {
+  if (f16)
+    return v == 0 ? launch_variant<1, 256, 2>(m[0], m[1], m[2], m[3], np, ncols, Y, ldy, err, s)
+                  : launch_variant<1, 128, 3>(m[0], m[1], m[2], m[3], np, ncols, Y, ldy, err, s);
+  return v == 0 ? launch_variant<0, 256, 2>(m[0], m[1], m[2], m[3], np, ncols, Y, ldy, err, s)
+                : launch_variant<0, 128, 3>(m[0], m[1], m[2], m[3], np, ncols, Y, ldy, err, s);
+}
+
+// Autotuner cache: (device, np, ncols, f16) -> fastest variant, measured once per
+// process on the first matvec of that shape.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+}  // namespace
+
 cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
                            const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
-                           cudaStream_t s, long long* nl) {
+                           cudaStream_t s, long long* nl, int variant) {
   // shape contract: M and K tiles of 128 / 64 rows of T, N tiles of 256 operand columns,
   // 16-byte aligned rows; every TMA x coordinate is a multiple of 64 elements (128 bytes).
-  if (np % TC_BM || ncols % TC_BN || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
+  if (np % TC_BM || ncols % 256 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(Th) | reinterpret_cast<uintptr_t>(Tl) |
        reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
     return cudaErrorMisalignedAddress;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  if (variant < -1 || variant >= kTcVariants) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    static std::mutex attr_mu;
+    static std::set<int> attr_done;
+    std::lock_guard<std::mutex> lock(attr_mu);
+    if (!attr_done.count(dev)) {
+      e = set_attrs<0>();
+      if (e == cudaSuccess) e = set_attrs<1>();
+      if (e != cudaSuccess) return e;
+      attr_done.insert(dev);
+    }
   }
-  CUtensorMap mTh, mTl, mXh, mXl;
-  if (!make_map(&mTh, Th, np, np, TC_BM, f16) || !make_map(&mTl, Tl, np, np, TC_BM, f16) ||
-      !make_map(&mXh, Xh, ncols, np, TC_BN, f16) || !make_map(&mXl, Xl, ncols, np, TC_BN, f16))
-    return cudaErrorInvalidValue;
-  dim3 grd(ncols / TC_BN, np / TC_BM);
-  if (f16) k_tc_gemm<1><<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
-  else k_tc_gemm<0><<<grd, 256, TC_SMEM, s>>>(mTh, mTl, mXh, mXl, Y, ldy, np, err);
+  CUtensorMap maps[4];
+  auto encode = [&](int bn) {
+    return make_map(&maps[0], Th, np, np, TC_BM, f16) && make_map(&maps[1], Tl, np, np, TC_BM, f16) &&
+           make_map(&maps[2], Xh, ncols, np, bn, f16) && make_map(&maps[3], Xl, ncols, np, bn, f16);
+  };
+  if (variant < 0) {
+    const auto key = std::make_tuple(dev, np, ncols, f16 ? 1 : 0);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) variant = it->second;
+    }
+    if (variant < 0) {
+      // time every variant on these operands (each writes the same Y), twice each,
+      // keep the faster; the stream is synchronised once per new shape
+      cudaEvent_t ev[2 * kTcVariants + 1];
+      for (auto& x : ev) {
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return e;
+      }
+      for (int v = 0; v < kTcVariants && e == cudaSuccess; ++v) {
+        if (!encode(kTcBN[v])) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) e = launch_tc_variant(v, f16, maps, np, ncols, Y, ldy, err, s);   // warm
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * v], s);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+          e = launch_tc_variant(v, f16, maps, np, ncols, Y, ldy, err, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * v + 1], s);
+        *nl += 3;
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[2 * kTcVariants - 1]);
+      float best_ms = 0.f;
+      variant = 0;
+      for (int v = 0; v < kTcVariants && e == cudaSuccess; ++v) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[2 * v], ev[2 * v + 1]);
+        if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+          best_ms = ms;
+          variant = v;
+        }
+      }
+      for (auto& x : ev) cudaEventDestroy(x);
+      if (e != cudaSuccess) return e;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = variant;
+    }
+  }
+  if (!encode(kTcBN[variant])) return cudaErrorInvalidValue;
+  e = launch_tc_variant(variant, f16, maps, np, ncols, Y, ldy, err, s);
   ++*nl;
-  return cudaGetLastError();
+  return e;
+}
+
+int tc_tuned_variant(int np, int ncols, bool f16) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(dev, np, ncols, f16 ? 1 : 0));
+  return it == g_tune.end() ? -1 : it->second;
 }
 
 }  // namespace px

@@ -6,11 +6,12 @@
 // kernel maps a warp onto 32 consecutive columns of one row (512 contiguous
 // bytes of 16-byte complex elements).
 //
-// Element types: double2 (FP64 complex) for PX_FP64, float4 (double-FP32 complex:
-// re_hi, im_hi, re_lo, im_lo) for the low-precision modes.  Double-FP32 products
-// and sums use the error-free transformations TwoSum (Knuth) and TwoProduct via
-// FMA, so each product a*b of two double-FP32 numbers carries ~48 significant
-// bits (the lo*lo term, below 2^-48 relative, is dropped).
+// Element types of the basis: double2 (FP64 complex), float4 (double-FP32 complex:
+// re_hi, im_hi, re_lo, im_lo) or float2 (FP32 complex).  Double-FP32 products and
+// sums use the error-free transformations TwoSum (Knuth) and TwoProduct via FMA, so
+// each product a*b of two double-FP32 numbers carries ~48 significant bits (the
+// lo*lo term, below 2^-48 relative, is dropped).  FP32 sums run over at most a few
+// dozen rows per thread before the partial sums continue in FP64.
 #include "px_internal.cuh"
 
 namespace px {
@@ -47,6 +48,7 @@ __device__ __forceinline__ double join_f(float h, float l) { return (double)h + 
 // ------------------------------------------------------------ element traits
 struct AccD { double re, im; };
 struct AccF { float rh, rl, ih, il; };
+struct AccS { float re, im; };
 
 template <class E> struct Tr;
 
@@ -161,6 +163,44 @@ template <> struct Tr<float4> {
   }
 };
 
+template <> struct Tr<float2> {
+  using Acc = AccS;
+  using Coef = float2;
+  static __device__ __forceinline__ Acc zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ Coef coef(double2 h) {
+    return make_float2(__double2float_rn(h.x), __double2float_rn(h.y));
+  }
+  static __device__ __forceinline__ void conj_mac(Acc& a, float2 v, float2 w) {
+    a.re = fmaf(v.x, w.x, fmaf(v.y, w.y, a.re));
+    a.im = fmaf(v.x, w.y, fmaf(-v.y, w.x, a.im));
+  }
+  static __device__ __forceinline__ void mac(Acc& a, float2 v, Coef h) {
+    a.re = fmaf(v.x, h.x, fmaf(-v.y, h.y, a.re));
+    a.im = fmaf(v.x, h.y, fmaf(v.y, h.x, a.im));
+  }
+  static __device__ __forceinline__ void norm_mac(Acc& a, float2 w) {
+    a.re = fmaf(w.x, w.x, fmaf(w.y, w.y, a.re));
+  }
+  static __device__ __forceinline__ double2 to_d2(const Acc& a) { return make_double2(a.re, a.im); }
+  static __device__ __forceinline__ double norm_d(const Acc& a) { return a.re; }
+  static __device__ __forceinline__ float2 sub(float2 w, const Acc& a) {
+    return make_float2(w.x - a.re, w.y - a.im);
+  }
+  static __device__ __forceinline__ float2 scale(float2 w, double s) {
+    const float f = __double2float_rn(s);
+    return make_float2(w.x * f, w.y * f);
+  }
+  static __device__ __forceinline__ float2 from_d2(double2 v) {
+    return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  }
+  static __device__ __forceinline__ double2 to_c(float2 v) { return make_double2(v.x, v.y); }
+  static __device__ __forceinline__ float2 hi(float2 v) { return v; }
+  static __device__ __forceinline__ float2 axpy_shift(double yr, double yi, float2 z, float2 x) {
+    return make_float2(fmaf(-z.x, x.x, fmaf(z.y, x.y, (float)yr)),
+                       fmaf(-z.x, x.y, fmaf(-z.y, x.x, (float)yi)));
+  }
+};
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -191,7 +231,7 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
   const int col = blockIdx.x * 32 + tx;
   if (col >= a.Bact) return;
   if (a.jconv && a.jconv[col] > 0) return;   // column stopped at an earlier step
-  const E* X = static_cast<const E*>(a.X);
+  const E* X = static_cast<const E*>(a.X) + (a.jdev ? (size_t)*a.jdev * a.nu * a.Bact : 0);
   E* W = static_cast<E*>(a.W);
   const auto zq = TT::coef(a.zq[col]);
   for (int i = blockIdx.y * 8 + ty; i < a.nu; i += 8 * gridDim.y) {
@@ -320,6 +360,7 @@ __global__ void k_rhs(int nu, int N, const int* __restrict__ rowptr, const int* 
 template <class E>
 __global__ void __launch_bounds__(256) k_dots(KrylovArgs a, int j) {
   using TT = Tr<E>;
+  if (a.jdev) j = *a.jdev;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int col = blockIdx.x * 32 + tx;
   const bool valid = col < a.Bact && a.jconv[col] == 0;   // skip columns that stopped
@@ -368,6 +409,7 @@ __global__ void __launch_bounds__(256) k_dots(KrylovArgs a, int j) {
 
 // h[pass][k][a] = sum_blk part[blk][k][a]
 __global__ void k_dots_reduce(KrylovArgs a, int j, int pass) {
+  if (a.jdev) j = *a.jdev;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (j + 1) * a.Bact) return;
   int k = idx / a.Bact, col = idx % a.Bact;
@@ -381,19 +423,20 @@ __global__ void k_dots_reduce(KrylovArgs a, int j, int pass) {
 }
 
 // W[i][a] -= sum_k V_k[i][a] h[pass][k][a]; with `last`, also |W|^2 partials.
+// The coefficients are staged in shared memory kUpdChunk at a time; a step with more
+// basis vectors sweeps W once per chunk (fixed shared memory for any restart length).
+constexpr int kUpdChunk = 64;
+
 template <class E>
 __global__ void __launch_bounds__(256) k_update(KrylovArgs a, int j, int pass, int last) {
   using TT = Tr<E>;
   using C = typename TT::Coef;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* shh = reinterpret_cast<C*>(smem_raw);   // [(j+1)][32]
+  if (a.jdev) j = *a.jdev;
+  __shared__ __align__(16) C shh[kUpdChunk * 32];
+  __shared__ double shn[8 * 32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int col = blockIdx.x * 32 + tx;
   const bool valid = col < a.Bact && a.jconv[col] == 0;   // skip columns that stopped
-  for (int k = ty; k <= j; k += 8)
-    shh[k * 32 + tx] = TT::coef(valid ? a.h[((size_t)pass * (a.m + 1) + k) * a.Bact + col]
-                                      : make_double2(0.0, 0.0));
-  __syncthreads();
   const E* V = static_cast<const E*>(a.V);
   E* W = static_cast<E*>(a.W);
   typename TT::Acc nacc = TT::zero();
@@ -401,28 +444,35 @@ __global__ void __launch_bounds__(256) k_update(KrylovArgs a, int j, int pass, i
   const int rows_per_blk = (a.nu + gridDim.y - 1) / gridDim.y;
   const int r0 = blockIdx.y * rows_per_blk;
   const int r1 = min(a.nu, r0 + rows_per_blk);
-  if (valid) {
-    for (int i = r0 + ty; i < r1; i += 8) {
-      const size_t off = (size_t)i * a.Bact + col;
-      const E w0 = W[off];
-      typename TT::Acc acc = TT::zero();
-      int k = 0;
-      for (; k + 8 <= j + 1; k += 8) {
-        E v[8];
+  for (int k0 = 0; k0 <= j; k0 += kUpdChunk) {
+    const int kend = min(j + 1, k0 + kUpdChunk);   // uniform over the block
+    const bool final_chunk = kend == j + 1;
+    if (k0 > 0) __syncthreads();                   // previous chunk's coefficients consumed
+    for (int k = k0 + ty; k < kend; k += 8)
+      shh[(k - k0) * 32 + tx] = TT::coef(valid ? a.h[((size_t)pass * (a.m + 1) + k) * a.Bact + col]
+                                               : make_double2(0.0, 0.0));
+    __syncthreads();
+    if (valid) {
+      for (int i = r0 + ty; i < r1; i += 8) {
+        const size_t off = (size_t)i * a.Bact + col;
+        const E w0 = W[off];
+        typename TT::Acc acc = TT::zero();
+        int k = k0;
+        for (; k + 8 <= kend; k += 8) {
+          E v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(k + q) * vstride + off];
+          for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(k + q) * vstride + off];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) TT::mac(acc, v[q], shh[(k + q) * 32 + tx]);
+          for (int q = 0; q < 8; ++q) TT::mac(acc, v[q], shh[(k - k0 + q) * 32 + tx]);
+        }
+        for (; k < kend; ++k) TT::mac(acc, V[(size_t)k * vstride + off], shh[(k - k0) * 32 + tx]);
+        const E w = TT::sub(w0, acc);
+        W[off] = w;
+        if (last && final_chunk) TT::norm_mac(nacc, w);
       }
-      for (; k <= j; ++k) TT::mac(acc, V[(size_t)k * vstride + off], shh[k * 32 + tx]);
-      const E w = TT::sub(w0, acc);
-      W[off] = w;
-      if (last) TT::norm_mac(nacc, w);
     }
   }
   if (last) {
-    __syncthreads();
-    double* shn = reinterpret_cast<double*>(smem_raw);
     shn[ty * 32 + tx] = TT::norm_d(nacc);
     __syncthreads();
     if (ty == 0 && valid) {
@@ -436,6 +486,7 @@ __global__ void __launch_bounds__(256) k_update(KrylovArgs a, int j, int pass, i
 // One thread per column: new Hessenberg column, previous rotations, new rotation,
 // residual estimate |g_{j+1}|, stop test.
 __global__ void k_givens(KrylovArgs a, int j, int passes) {
+  if (a.jdev) j = *a.jdev;
   int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= a.Bact) return;
   const int B = a.Bact, m1 = a.m + 1;
@@ -507,6 +558,7 @@ template <class E>
 __global__ void __launch_bounds__(256) k_normalize(KrylovArgs a, int j, float* X32, double* X64,
                                                    int ldx) {
   using TT = Tr<E>;
+  if (a.jdev) j = *a.jdev;
   const int col = blockIdx.x * 32 + threadIdx.x;
   if (col >= a.Bact) return;
   const int jc = a.jconv[col];
@@ -629,6 +681,18 @@ __global__ void __launch_bounds__(256) k_gather_x(const double2* x, int B, const
     *reinterpret_cast<double2*>(X64 + (size_t)i * ldx + 2 * col) = x[(size_t)i * B + gc];
 }
 
+// End of one Krylov step inside a captured restart cycle: advance the device step
+// index and tell the enclosing while-loop node whether to run another step (some
+// column still iterating and the basis not full).  The index grows by one per step, so
+// the loop ends after at most m steps whatever the data.
+__global__ void k_step_advance(int* jdev, const int* active_count, int m,
+                               cudaGraphConditionalHandle loop) {
+  const int j = *jdev;
+  const bool more = j + 1 < m && active_count[j] > 0;
+  *jdev = j + 1;
+  cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
 __global__ void k_norm_finish(const double* normpart, int nblk, int Bact, const int* act, int P,
                               const double* bnorm, double inner_tol, double tol_abs_frac,
                               double* rnorm, double* beta, double* target_all) {
@@ -645,9 +709,12 @@ __global__ void k_norm_finish(const double* normpart, int nblk, int Bact, const 
 
 inline dim3 col_grid(int Bact, int nblk) { return dim3((Bact + 31) / 32, nblk); }
 
-template <class K>
-cudaError_t set_smem(K kernel, int bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// Calls f with a value of the basis element type selected by `basis`.
+template <class F>
+void with_basis(int basis, F&& f) {
+  if (basis == kBasisFF) f(float4{});
+  else if (basis == kBasisF32) f(float2{});
+  else f(double2{});
 }
 
 }  // namespace
@@ -661,13 +728,11 @@ int reduction_blocks(int nu) {
 
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl) {
   dim3 grd = col_grid(a.Bact, a.nblk), blk(32, 8);
-  if (a.ff) {
-    if (a.y_is_f32) k_shift<float4, true><<<grd, blk, 0, s>>>(a);
-    else k_shift<float4, false><<<grd, blk, 0, s>>>(a);
-  } else {
-    if (a.y_is_f32) k_shift<double2, true><<<grd, blk, 0, s>>>(a);
-    else k_shift<double2, false><<<grd, blk, 0, s>>>(a);
-  }
+  with_basis(a.basis, [&](auto e) {
+    using E = decltype(e);
+    if (a.y_is_f32) k_shift<E, true><<<grd, blk, 0, s>>>(a);
+    else k_shift<E, false><<<grd, blk, 0, s>>>(a);
+  });
   ++*nl;
   return cudaGetLastError();
 }
@@ -689,9 +754,11 @@ cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* c
 }
 
 cudaError_t launch_dots(const KrylovArgs& a, int j, int pass, cudaStream_t s, long long* nl) {
-  if (a.ff) k_dots<float4><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j);
-  else k_dots<double2><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j);
-  int n = (j + 1) * a.Bact;
+  with_basis(a.basis, [&](auto e) {
+    k_dots<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j);
+  });
+  // with a device step index the reduction grid covers the longest step of the cycle
+  int n = ((a.jdev ? a.m : j) + 1) * a.Bact;
   k_dots_reduce<<<(n + 255) / 256, 256, 0, s>>>(a, j, pass);
   *nl += 2;
   return cudaGetLastError();
@@ -699,18 +766,16 @@ cudaError_t launch_dots(const KrylovArgs& a, int j, int pass, cudaStream_t s, lo
 
 cudaError_t launch_update(const KrylovArgs& a, int j, int pass, bool last, cudaStream_t s,
                           long long* nl) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const int bytes = kMaxRestart * 32 * 16;
-    cudaError_t e = set_smem(k_update<float4>, bytes);
-    if (e == cudaSuccess) e = set_smem(k_update<double2>, bytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  size_t smem = (size_t)(j + 1) * 32 * 16;
-  if (smem < 8 * 32 * sizeof(double)) smem = 8 * 32 * sizeof(double);
-  if (a.ff) k_update<float4><<<col_grid(a.Bact, a.nblk), dim3(32, 8), smem, s>>>(a, j, pass, last);
-  else k_update<double2><<<col_grid(a.Bact, a.nblk), dim3(32, 8), smem, s>>>(a, j, pass, last);
+  with_basis(a.basis, [&](auto e) {
+    k_update<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j, pass, last);
+  });
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_advance(int* jdev, const int* active_count, int m,
+                                cudaGraphConditionalHandle loop, cudaStream_t s, long long* nl) {
+  k_step_advance<<<1, 1, 0, s>>>(jdev, active_count, m, loop);
   ++*nl;
   return cudaGetLastError();
 }
@@ -723,8 +788,9 @@ cudaError_t launch_givens(const KrylovArgs& a, int j, int passes, cudaStream_t s
 
 cudaError_t launch_normalize(const KrylovArgs& a, int j, float* X32, double* X64, int ldx,
                              cudaStream_t s, long long* nl) {
-  if (a.ff) k_normalize<float4><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j, X32, X64, ldx);
-  else k_normalize<double2><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j, X32, X64, ldx);
+  with_basis(a.basis, [&](auto e) {
+    k_normalize<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j, X32, X64, ldx);
+  });
   ++*nl;
   return cudaGetLastError();
 }
@@ -732,12 +798,10 @@ cudaError_t launch_normalize(const KrylovArgs& a, int j, float* X32, double* X64
 cudaError_t launch_cycle_start(const KrylovArgs& a, const int* act, const double2* r, int B,
                                const double* beta, const double* target_all, float* X32,
                                double* X64, int ldx, cudaStream_t s, long long* nl) {
-  if (a.ff)
-    k_cycle_start<float4><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, r, B, beta,
-                                                                           target_all, X32, X64, ldx);
-  else
-    k_cycle_start<double2><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, r, B, beta,
-                                                                            target_all, X32, X64, ldx);
+  with_basis(a.basis, [&](auto e) {
+    k_cycle_start<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(
+        a, act, r, B, beta, target_all, X32, X64, ldx);
+  });
   ++*nl;
   return cudaGetLastError();
 }
@@ -746,8 +810,9 @@ cudaError_t launch_cycle_end(const KrylovArgs& a, int jend, const int* act, doub
                              double2* r, int B, double* beta, int* iters, cudaStream_t s,
                              long long* nl) {
   k_backsolve<<<(a.Bact + 127) / 128, 128, 0, s>>>(a, jend, act, beta, iters);
-  if (a.ff) k_xupdate<float4><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, x, r, B);
-  else k_xupdate<double2><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, x, r, B);
+  with_basis(a.basis, [&](auto e) {
+    k_xupdate<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, x, r, B);
+  });
   *nl += 2;
   return cudaGetLastError();
 }

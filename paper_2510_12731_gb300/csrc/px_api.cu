@@ -50,6 +50,18 @@ struct PxError {
   std::string msg;
 };
 
+// One restart cycle captured as a graph: a while-loop node whose body is one Krylov
+// step.  key lists every value the captured launches depend on (sizes, buffers, the
+// structure generation); body_kernels counts the kernels of one step.
+struct CycleGraph {
+  std::vector<uint64_t> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long body_kernels = 0;
+};
+constexpr size_t kMaxCachedGraphs = 64;
+constexpr int kAutoF32MaxRestart = 128;   // longest restart run with an automatic FP32 basis
+
 }  // namespace
 
 struct px_handle {
@@ -63,6 +75,8 @@ struct px_handle {
   // structure buffers
   DevBuf b_pos, b_Rq, b_Rmu, b_area, b_type, b_rowptr, b_col, b_val64, b_val32, b_counts;
   DevBuf b_pair;   // rcut2, r0, d, s tables
+  DevBuf b_perm;   // [N] caller index of internal atom i
+  DevBuf b_stage;  // staging inputs (caller order) and sort scratch
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
@@ -75,14 +89,26 @@ struct px_handle {
   std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_iter[2] = {nullptr, nullptr};
   long long nl = 0;
+  int* d_jstep = nullptr;       // device step index of a captured cycle (in d_active's block)
+  int* h_jstep = nullptr;       // pinned host copy (in h_active's block)
+  cudaStream_t cap_stream = nullptr;   // stream used only to capture cycle graphs
+  std::vector<CycleGraph> graphs;      // instantiated cycle graphs, reused by equal keys
   double drude_n = 0.0, tau = 0.0;   // shared n, tau of the loaded structure (Eq. 6)
   bool verbose = false;              // PX_VERBOSE=1: one stderr line per restart cycle
 };
 
 namespace {
 
+void drop_graphs(px_handle* h) {
+  for (CycleGraph& c : h->graphs) {
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+  }
+  h->graphs.clear();
+}
+
 void free_all(px_handle* h) {
-  DevBuf* bufs[] = {&h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
+  DevBuf* bufs[] = {&h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
                     &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
@@ -100,6 +126,14 @@ px_status validate_options(const px_options* o, std::string* msg) {
   if (o->max_iter < 1 || o->max_cycles < 1) { *msg = "max_iter and max_cycles must be >= 1"; return PX_EINVAL; }
   if (o->max_refine < 0) { *msg = "max_refine must be >= 0"; return PX_EINVAL; }
   if (o->gs_passes < 1 || o->gs_passes > 2) { *msg = "gs_passes must be 1 or 2"; return PX_EINVAL; }
+  if (o->basis < PX_BASIS_AUTO || o->basis > PX_BASIS_FP32) { *msg = "bad basis"; return PX_EINVAL; }
+  if (o->gemm_tiles < 0 || o->gemm_tiles > 2) { *msg = "gemm_tiles must be 0, 1 or 2"; return PX_EINVAL; }
+  if (o->cycle_graphs < 0 || o->cycle_graphs > 1) { *msg = "cycle_graphs must be 0 or 1"; return PX_EINVAL; }
+  if (o->sort_atoms < 0 || o->sort_atoms > 1) { *msg = "sort_atoms must be 0 or 1"; return PX_EINVAL; }
+  if (o->precision == PX_FP64 && o->basis != PX_BASIS_AUTO && o->basis != PX_BASIS_FP64) {
+    *msg = "PX_FP64 needs an FP64 Krylov basis (PX_BASIS_AUTO or PX_BASIS_FP64)";
+    return PX_EINVAL;
+  }
   if (!(o->tol_rel > 0.0) || !(o->tol_rel < 1.0)) { *msg = "tol_rel must be in (0, 1)"; return PX_EINVAL; }
   if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) { *msg = "inner_tol must be in (0, 1)"; return PX_EINVAL; }
   if (!(o->kcut_eps >= 0.0) || !(o->kcut_eps < 0.5)) { *msg = "kcut_eps must be in [0, 0.5)"; return PX_EINVAL; }
@@ -172,14 +206,10 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     for (int t = 0; t < ntypes; ++t)
       if (types[t].Rq_bohr < 0.5 || types[t].Rmu_bohr < 0.5)
         throw PxError{PX_EINVAL, "fp16split needs Gaussian widths >= 0.5 bohr (fp16 range of 4096 T)"};
-  std::vector<double> pos(3 * (size_t)N);
   for (int i = 0; i < N; ++i) {
     if (tidx[i] < 0 || tidx[i] >= ntypes) throw PxError{PX_EINVAL, "type index out of range"};
-    for (int k = 0; k < 3; ++k) {
-      double x = xyz[3 * (size_t)i + k];
-      if (!std::isfinite(x)) throw PxError{PX_EINVAL, "non-finite coordinate"};
-      pos[3 * (size_t)i + k] = x / kBohrAng;
-    }
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(xyz[3 * (size_t)i + k])) throw PxError{PX_EINVAL, "non-finite coordinate"};
   }
   // duplicate atoms: sort by x, compare within a 1e-6 Angstrom window
   {
@@ -196,13 +226,6 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
         if (dx * dx + dy * dy + dz * dz < eps * eps) throw PxError{PX_EINVAL, "two atoms closer than 1e-6 Angstrom"};
       }
     }
-  }
-  std::vector<double> Rq(N), Rmu(N), area(N);
-  for (int i = 0; i < N; ++i) {
-    const px_atom_type& a = types[tidx[i]];
-    Rq[i] = a.Rq_bohr;
-    Rmu[i] = a.Rmu_bohr;
-    area[i] = a.area_bohr2;
   }
   // pair tables: arithmetic means of the two types' r0, d, s; squared cutoff radius
   // where 1 - f(r) = kcut_eps (infinite when kcut_eps == 0).
@@ -244,17 +267,31 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   CU(h->b_rowptr.ensure(sizeof(int) * (N + 1)));
   CU(h->b_counts.ensure(sizeof(int) * N));
   CU(h->b_pair.ensure(sizeof(double) * pair.size()));
+  CU(h->b_perm.ensure(sizeof(int) * N));
   d.pos64 = h->b_pos.as<double>();
   d.Rq = h->b_Rq.as<double>();
   d.Rmu = h->b_Rmu.as<double>();
   d.area = h->b_area.as<double>();
   d.type = h->b_type.as<int>();
   d.rowptr = h->b_rowptr.as<int>();
-  CU(cudaMemcpyAsync(d.pos64, pos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(d.Rq, Rq.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(d.Rmu, Rmu.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(d.area, area.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(d.type, tidx, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  d.perm = h->b_perm.as<int>();
+  // ---- staging (Angstrom -> bohr, Morton order, per-atom parameters) on the device
+  {
+    const size_t in_bytes = round_up(sizeof(double) * 3 * N, 256) + round_up(sizeof(int) * N, 256) +
+                            round_up(sizeof(px_atom_type) * ntypes, 256);
+    const size_t tmp_bytes = h->opt.sort_atoms ? px::stage_scratch_bytes(N) : 0;
+    CU(h->b_stage.ensure(in_bytes + tmp_bytes));
+    unsigned char* sp = h->b_stage.as<unsigned char>();
+    double* d_xyz = reinterpret_cast<double*>(sp);
+    int* d_tidx = reinterpret_cast<int*>(sp + round_up(sizeof(double) * 3 * N, 256));
+    px_atom_type* d_types = reinterpret_cast<px_atom_type*>(
+        sp + round_up(sizeof(double) * 3 * N, 256) + round_up(sizeof(int) * N, 256));
+    CU(cudaMemcpyAsync(d_xyz, xyz, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_tidx, tidx, sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d_types, types, sizeof(px_atom_type) * ntypes, cudaMemcpyHostToDevice, s));
+    CU(px::launch_stage_atoms(d_xyz, d_tidx, d_types, N, h->opt.sort_atoms != 0, sp + in_bytes,
+                              tmp_bytes, d.perm, d.pos64, d.type, d.Rq, d.Rmu, d.area, s, &h->nl));
+  }
   CU(cudaMemcpyAsync(h->b_pair.p, pair.data(), sizeof(double) * pair.size(), cudaMemcpyHostToDevice, s));
   const double* dpair = h->b_pair.as<double>();
   const double* d_rcut2 = dpair;
@@ -397,9 +434,11 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const int B = F * P;
   const int nu = d.nu, np = d.np, N = d.N, ntypes = d.ntypes;
   const px_options& o = h->opt;
-  // restart length: explicit, or automatic (0): wFQ converges about as fast with short
-  // restarts, whose Gram-Schmidt traffic is lower; wFQFmu needs longer ones
-  const int m_req = o.restart_m > 0 ? o.restart_m : (model == PX_WFQ ? 60 : 100);
+  // restart length: explicit, or automatic (0): a low-precision wFQ solve converges about
+  // as fast with short restarts, whose Gram-Schmidt traffic is lower; wFQFmu, and FP64
+  // solves (whose cost is the FP64 matvec, not the orthogonalisation), take longer ones
+  const int m_req = o.restart_m > 0 ? o.restart_m
+                                    : (model == PX_WFQ && o.precision != PX_FP64 ? 60 : 100);
   const int m = std::min(m_req, o.max_iter);
   const int passes = o.gs_passes;
   const bool lowp = o.precision != PX_FP64;
@@ -412,6 +451,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const double inner_tol = lowp ? o.inner_tol : 0.0;
   const double tol_abs_frac = (lowp ? 0.1 : 0.5) * o.tol_rel;
   const int max_inner = 50;   // inner cycles per refinement round
+  // restart cycles as graph launches, unless every matvec is timed with events
+  const bool use_graphs = o.cycle_graphs != 0 && !o.profile;
   const int nblk = px::reduction_blocks(nu);
   long long& nl = h->nl;
   nl = 0;
@@ -422,6 +463,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   st.cycles = 0;
   st.total_iters = 0;
   st.used_precision = o.precision;
+  st.gemm_tiles_used = 0;
+  st.graph_launches = 0;
   CU(cudaEventRecord(h->ev_a, s));
 
   // ---- inputs, shifts (Eq. 6, Eq. 8) and right-hand sides
@@ -457,14 +500,20 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   CU(px::launch_init_residual(b, nu, P, B, bnorm, inner_tol, tol_abs_frac, r, rnorm, beta,
                               target_all, s, &nl));
 
-  // ---- Krylov workspace for up to B active columns (16-byte complex elements)
+  // ---- Krylov workspace for up to B active columns
   px::KrylovArgs A{};
   A.nu = nu;
   A.m = m;
   A.nblk = nblk;
-  A.ff = lowp ? 1 : 0;
-  void* V = grow<double2>(h->b_V, (size_t)(m + 1) * nu * B);
-  void* W = grow<double2>(h->b_W, (size_t)nu * B);
+  // basis element: fixed by the options, or (automatic, low precision) chosen per cycle:
+  // FP32 for restarts up to kAutoF32MaxRestart vectors, double-FP32 for the longer
+  // restarts of shrunken active sets, where classical Gram-Schmidt in FP32 loses
+  // orthogonality
+  const bool basis_auto = lowp && o.basis == PX_BASIS_AUTO;
+  A.basis = px::basis_kind(o.precision, o.basis);
+  const size_t esz_max = basis_auto ? 16 : px::basis_bytes(A.basis);
+  void* V = grow<unsigned char>(h->b_V, (size_t)(m + 1) * nu * B * esz_max);
+  void* W = grow<unsigned char>(h->b_W, (size_t)nu * B * esz_max);
   double2* hh = grow<double2>(h->b_h, 2 * (size_t)(m + 1) * B);
   double2* part = grow<double2>(h->b_part, (size_t)nblk * (m + 1) * B);
   double* normpart = grow<double>(h->b_normpart, (size_t)nblk * B);
@@ -531,6 +580,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       const int mc = std::max(m, (int)std::min<long long>(px::kMaxRestart,
                                                           (long long)(m + 1) * B / Bact - 1));
       A.m = mc;
+      if (basis_auto) A.basis = mc <= kAutoF32MaxRestart ? px::kBasisF32 : px::kBasisFF;
+      const size_t esz = px::basis_bytes(A.basis);
       A.y = yv;
       A.u = yv + (size_t)mc * Bact;
       const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
@@ -541,7 +592,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       CU(px::launch_cycle_start(A, act, r, B, beta, target_all, lowp ? X32 : nullptr,
                                 lowp ? nullptr : X64, ldxa, s, &nl));
       px::ShiftArgs sa{};
-      sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.nblk = nblk; sa.ff = A.ff;
+      sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.nblk = nblk; sa.basis = A.basis;
       sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = d.type;
       sa.zq = zq_act; sa.zmu = zmu_act;
       sa.Y = lowp ? (const void*)Y32 : (const void*)Y64;
@@ -550,55 +601,150 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       sa.jconv = jconv;
       sa.precond_mu = amu_act ? 1 : 0;
       sa.W = W;
-      int jend = 0;
-      for (int j = 0; j < mc; ++j) {
+      // one Krylov step: j >= 0 eagerly (host-side step index, per-step poll), or
+      // j < 0 under capture (kernels read the step index from the device)
+      auto enqueue_step = [&](int j, cudaStream_t q, long long* cnt) {
+        const bool cap = j < 0;
+        px::KrylovArgs Aj = A;
+        Aj.jdev = cap ? h->d_jstep : nullptr;
+        const int jj = cap ? 0 : j;
         // ---- block matvec Y = T X (the dominant kernel)
         cudaEvent_t e0v = nullptr, e1v = nullptr;
-        if (o.profile) {
+        if (o.profile && !cap) {
           e0v = pool_event(h, prof_k++);
           e1v = pool_event(h, prof_k++);
-          CU(cudaEventRecord(e0v, s));
+          CU(cudaEventRecord(e0v, q));
         }
         if (d.matfree) {
-          if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
-          else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+          if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
+          else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
         } else if (tc) {
-          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
-          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
-                                &nl));
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt));
+          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, q,
+                                cnt, o.gemm_tiles - 1));
+          if (st.gemm_tiles_used == 0)
+            st.gemm_tiles_used = o.gemm_tiles ? o.gemm_tiles
+                                              : px::tc_tuned_variant(np, ldxa, tc_f16) + 1;
         } else if (lowp) {
-          CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, s, &nl));
+          CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
         } else if (2 * Bact <= 8) {
-          CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
+          CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, q, cnt));
         } else {
-          CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+          CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
         }
-        if (o.profile) {
-          CU(cudaEventRecord(e1v, s));
+        if (o.profile && !cap) {
+          CU(cudaEventRecord(e1v, q));
           mv_events.push_back({e0v, e1v});
         }
-        st.matvec_launches++;
-        st.matvec_flops += 4.0 * (double)nu * nu * Bact;
-        st.matvec_bytes += (double)nu * nu * (lowp ? 4.0 : 8.0) + 2.0 * nu * 2.0 * Bact * (lowp ? 4.0 : 8.0);
         // ---- conductance + shift: W = Kbar Y - z V_j
-        sa.X = static_cast<const char*>(V) + (size_t)j * nu * Bact * 16;
-        CU(px::launch_shift(sa, s, &nl));
+        px::ShiftArgs sj = sa;
+        sj.jdev = Aj.jdev;
+        sj.X = cap ? V : static_cast<const char*>(V) + (size_t)j * nu * Bact * esz;
+        CU(px::launch_shift(sj, q, cnt));
         // ---- classical Gram-Schmidt, Givens, next basis vector
         for (int pass = 0; pass < passes; ++pass) {
-          CU(px::launch_dots(A, j, pass, s, &nl));
-          CU(px::launch_update(A, j, pass, pass == passes - 1, s, &nl));
+          CU(px::launch_dots(Aj, jj, pass, q, cnt));
+          CU(px::launch_update(Aj, jj, pass, pass == passes - 1, q, cnt));
         }
-        CU(px::launch_givens(A, j, passes, s, &nl));
-        CU(cudaMemcpyAsync(h->h_active + j, h->d_active + j, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CU(px::launch_normalize(A, j, lowp ? X32 : nullptr, lowp ? nullptr : X64, ldxa, s, &nl));
-        CU(cudaEventRecord(h->ev_iter[j & 1], s));
-        jend = j + 1;
-        // lagged poll: wait for step j-1 and stop once every column has stopped
-        if (j >= 1) {
-          wait_event(h, h->ev_iter[(j - 1) & 1]);
-          if (reinterpret_cast<volatile int*>(h->h_active)[j - 1] == 0) break;
+        CU(px::launch_givens(Aj, jj, passes, q, cnt));
+        if (!cap)
+          CU(cudaMemcpyAsync(h->h_active + j, h->d_active + j, sizeof(int), cudaMemcpyDeviceToHost, q));
+        CU(px::launch_normalize(Aj, jj, lowp ? X32 : nullptr, lowp ? nullptr : X64, ldxa, q, cnt));
+      };
+      int jend = 0;
+      if (use_graphs) {
+        // the whole restart cycle is one graph launch: a device-side while loop runs
+        // Krylov steps until every column stopped or the basis is full
+        if (tc && o.gemm_tiles == 0 && px::tc_tuned_variant(np, ldxa, tc_f16) < 0) {
+          // tune the tensor-core tile shape on this cycle's operands before capture
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
+          CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
+                                &nl, -1));
+        }
+        const std::vector<uint64_t> key = {
+            (uint64_t)Bact, (uint64_t)mc, (uint64_t)ldxa, (uint64_t)passes, (uint64_t)A.basis,
+            (uint64_t)o.precision, (uint64_t)d.matfree, (uint64_t)o.gemm_tiles,
+            (uint64_t)(uintptr_t)V, (uint64_t)(uintptr_t)W, (uint64_t)(uintptr_t)hh,
+            (uint64_t)(uintptr_t)part, (uint64_t)(uintptr_t)Rm, (uint64_t)(uintptr_t)yv,
+            (uint64_t)(uintptr_t)X32, (uint64_t)(uintptr_t)Y32, (uint64_t)(uintptr_t)X64,
+            (uint64_t)(uintptr_t)Y64, (uint64_t)(uintptr_t)Xth, (uint64_t)(uintptr_t)zq_act,
+            (uint64_t)(uintptr_t)zmu_act, (uint64_t)(uintptr_t)jconv, (uint64_t)(uintptr_t)normpart,
+            (uint64_t)(uintptr_t)g, (uint64_t)(uintptr_t)cs, (uint64_t)(uintptr_t)sn,
+            (uint64_t)(uintptr_t)target, (uint64_t)(uintptr_t)invh, (uint64_t)(uintptr_t)amu_act,
+            (uint64_t)(uintptr_t)Xtl, (uint64_t)(uintptr_t)h->d_err,
+            // the structure's operators: a graph stays valid for a new structure that
+            // reuses the same buffers and sizes (it captured addresses, not contents)
+            (uint64_t)model, (uint64_t)N, (uint64_t)nu, (uint64_t)np, (uint64_t)nblk,
+            (uint64_t)(uintptr_t)d.T64, (uint64_t)(uintptr_t)d.T32, (uint64_t)(uintptr_t)d.Thi,
+            (uint64_t)(uintptr_t)d.Tlo, (uint64_t)(uintptr_t)d.rowptr, (uint64_t)(uintptr_t)d.col,
+            (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
+            (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d};
+        CycleGraph* cg = nullptr;
+        for (size_t k = 0; k < h->graphs.size(); ++k) {
+          if (h->graphs[k].key != key) continue;
+          if (h->graphs[k].exec) {
+            cg = &h->graphs[k];
+          } else {   // left over from a capture that failed
+            if (h->graphs[k].graph) cudaGraphDestroy(h->graphs[k].graph);
+            h->graphs.erase(h->graphs.begin() + k);
+          }
+          break;
+        }
+        if (!cg) {
+          if (h->graphs.size() >= kMaxCachedGraphs) drop_graphs(h);
+          CycleGraph c;
+          c.key = key;
+          CU(cudaGraphCreate(&c.graph, 0));
+          h->graphs.push_back(c);   // owned by the handle from here on (freed on error too)
+          cg = &h->graphs.back();
+          cudaGraphConditionalHandle loop;
+          CU(cudaGraphConditionalHandleCreate(&loop, cg->graph, 1, cudaGraphCondAssignDefault));
+          cudaGraphNodeParams cp = {};
+          cp.type = cudaGraphNodeTypeConditional;
+          cp.conditional.handle = loop;
+          cp.conditional.type = cudaGraphCondTypeWhile;
+          cp.conditional.size = 1;
+          cudaGraphNode_t wn;
+          CU(cudaGraphAddNode(&wn, cg->graph, nullptr, nullptr, 0, &cp));
+          cudaGraph_t body = cp.conditional.phGraph_out[0];
+          long long body_nl = 0;
+          CU(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+          try {
+            enqueue_step(-1, h->cap_stream, &body_nl);
+            CU(px::launch_step_advance(h->d_jstep, h->d_active, mc, loop, h->cap_stream, &body_nl));
+          } catch (...) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(h->cap_stream, &dummy);
+            throw;
+          }
+          CU(cudaStreamEndCapture(h->cap_stream, &body));
+          CU(cudaGraphInstantiate(&cg->exec, cg->graph, 0));
+          cg->body_kernels = body_nl;
+        }
+        CU(cudaMemsetAsync(h->d_jstep, 0, sizeof(int), s));
+        CU(cudaGraphLaunch(cg->exec, s));
+        CU(cudaMemcpyAsync(h->h_jstep, h->d_jstep, sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync_stream(h, s);
+        jend = *h->h_jstep;
+        if (jend < 1 || jend > mc) throw PxError{PX_ECUDA, "captured restart cycle ran no steps"};
+        nl += cg->body_kernels * jend;
+        st.graph_launches++;
+      } else {
+        for (int j = 0; j < mc; ++j) {
+          enqueue_step(j, s, &nl);
+          CU(cudaEventRecord(h->ev_iter[j & 1], s));
+          jend = j + 1;
+          // lagged poll: wait for step j-1 and stop once every column has stopped
+          if (j >= 1) {
+            wait_event(h, h->ev_iter[(j - 1) & 1]);
+            if (reinterpret_cast<volatile int*>(h->h_active)[j - 1] == 0) break;
+          }
         }
       }
+      st.matvec_launches += jend;
+      st.matvec_flops += 4.0 * (double)nu * nu * Bact * jend;
+      st.matvec_bytes += ((double)nu * nu * (lowp ? 4.0 : 8.0) + 2.0 * nu * 2.0 * Bact * (lowp ? 4.0 : 8.0)) * jend;
       st.total_iters += jend;
       if (h->verbose)
         std::fprintf(stderr, "px: round %d inner %d columns %d steps %d (restart %d)\n", round, inner,
@@ -661,17 +807,22 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
     sync_stream(h, s);
     int nb = 0;
+    double worst = 0.0;
     for (int k = 0; k < Bout; ++k) {
       const int c = h_outer[k];
       if (!std::isfinite(h_col[c])) throw PxError{PX_ECUDA, "non-finite residual"};
+      worst = std::max(worst, h_col[c] / h_bnorm[c % P]);
       if (h_col[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
     }
+    if (h->verbose)
+      std::fprintf(stderr, "px: round %d true residual: max rel %.3e over %d columns, %d left\n",
+                   round, worst, Bout, nb);
     Bout = nb;
   }
   st.cycles = total_cycles;
 
   // ---- observables (Sec. "Observables")
-  CU(px::launch_observables(N, model, F, P, d.pos64, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
+  CU(px::launch_observables(N, model, F, P, d.pos64, d.perm, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
                             so->d_mu, so->d_sigma_pol, so->d_sigma, s, &nl));
   if (so->d_relres) CU(px::launch_relres(rnorm, bnorm, B, P, so->d_relres, s, &nl));
   std::vector<double> h_rnorm(B);
@@ -719,6 +870,10 @@ void default_options(px_options* o) {
   o->max_cycles = 200;
   o->max_refine = 20;
   o->gs_passes = 1;
+  o->basis = PX_BASIS_AUTO;
+  o->gemm_tiles = 0;
+  o->cycle_graphs = 1;
+  o->sort_atoms = 1;
   o->tol_rel = 1e-7;
   o->inner_tol = 1e-3;
   o->kcut_eps = 1e-6;
@@ -765,8 +920,11 @@ px_status px_create(px_handle** out, const px_options* opt) {
     CU(cudaEventCreate(&h->ev_b));
     CU(cudaEventCreateWithFlags(&h->ev_iter[0], cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&h->ev_iter[1], cudaEventDisableTiming));
-    CU(cudaHostAlloc((void**)&h->h_active, sizeof(int) * px::kMaxRestart, cudaHostAllocDefault));
-    CU(cudaMalloc((void**)&h->d_active, sizeof(int) * px::kMaxRestart));
+    CU(cudaHostAlloc((void**)&h->h_active, sizeof(int) * (px::kMaxRestart + 1), cudaHostAllocDefault));
+    CU(cudaMalloc((void**)&h->d_active, sizeof(int) * (px::kMaxRestart + 1)));
+    h->h_jstep = h->h_active + px::kMaxRestart;
+    h->d_jstep = h->d_active + px::kMaxRestart;
+    CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CU(cudaMalloc((void**)&h->d_err, sizeof(int)));
   } catch (const PxError& e) {
     g_create_error = e.msg;
@@ -784,7 +942,8 @@ px_status px_set_options(px_handle* h, const px_options* opt) {
   if (vs != PX_OK) return fail(h, vs, msg);
   bool rebuild = h->have_structure && (opt->precision != h->opt.precision || opt->mode != h->opt.mode ||
                                        opt->kcut_eps != h->opt.kcut_eps ||
-                                       opt->mu_self_term != h->opt.mu_self_term);
+                                       opt->mu_self_term != h->opt.mu_self_term ||
+                                       opt->sort_atoms != h->opt.sort_atoms);
   h->opt = *opt;
   if (rebuild) {
     h->have_structure = false;
@@ -875,6 +1034,8 @@ px_status px_get_stats(const px_handle* h, px_stats* st) {
 
 px_status px_destroy(px_handle* h) {
   if (!h) return PX_OK;
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   free_all(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ev_a) cudaEventDestroy(h->ev_a);

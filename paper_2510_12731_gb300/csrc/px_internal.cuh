@@ -19,6 +19,8 @@
 #include <cstdint>
 #include <cstddef>
 
+#include "px.h"
+
 namespace px {
 
 constexpr int kTile = 128;   // padding granularity of T and of the matvec operands
@@ -50,6 +52,7 @@ struct DevStructure {
   float4* pos4f = nullptr;     // matrix-free: x, y, z, R_q^2 (FP32)
   double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
   bool matfree = false;
+  int* perm = nullptr;         // [N] caller's index of internal (Morton-sorted) atom i
   uint16_t* Thi = nullptr;     // hi part of T: bf16, or fp16 of 2^12 T
   uint16_t* Tlo = nullptr;     // lo part of T: bf16, or fp16 of (2^12 T - hi) 2^11
   bool t_f16 = false;
@@ -58,6 +61,16 @@ struct DevStructure {
 // ---------------------------------------------------------------- launch wrappers
 // Every wrapper enqueues its kernels on `s` and adds the number of kernel
 // launches to *nl.  They never synchronise.
+
+// Structure staging: xyz_ang [N][3] (Angstrom), tidx [N] and types [ntypes] on the
+// device, in the caller's order -> pos (bohr), type, Rq, Rmu, area in internal order
+// and perm[i] = caller index of internal atom i.  sort: Morton order (needs
+// stage_scratch_bytes(N) of scratch), else the caller's order (perm = identity).
+size_t stage_scratch_bytes(int N);
+cudaError_t launch_stage_atoms(const double* xyz_ang, const int* tidx, const px_atom_type* types,
+                               int N, bool sort, void* scratch, size_t scratch_bytes, int* perm,
+                               double* pos, int* type, double* Rq, double* Rmu, double* area,
+                               cudaStream_t s, long long* nl);
 
 // Neighbour list + CSR of K.  rcut2 / r0 / dd / ss are [ntypes][ntypes] pair tables.
 cudaError_t launch_neigh_count(const double* pos, int N, const int* type, int ntypes,
@@ -102,23 +115,41 @@ cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, doub
 // Tensor-core split-precision matvec Y = T X from hi/lo 16-bit parts of T and X
 // (bf16, or scaled fp16 when f16).  Xh / Xl are the transposed operand [ncols][np]
 // (K-major); np % 128 == 0, ncols % 256 == 0.  *err is set to 1 if a pipeline wait
-// ran out of time.
+// ran out of time.  variant: 0 = 128 x 256 tiles (2-stage ring), 1 = 128 x 128 tiles
+// (3-stage ring), -1 = autotuned: the first call of a (np, ncols, f16) shape times every
+// variant on its operands (synchronising the stream once) and caches the fastest.
 cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
                            const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
-                           cudaStream_t s, long long* nl);
+                           cudaStream_t s, long long* nl, int variant);
+// The autotuner's cached variant for a shape on the current device, or -1.
+int tc_tuned_variant(int np, int ncols, bool f16);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
 cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
                             uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);
 
 // ---------------------------------------------------------------- Krylov workspace
-// The Krylov basis V and the work vector W hold complex numbers either in FP64
-// (double2, used by PX_FP64) or in double-FP32 form (float4 = re_hi, im_hi, re_lo,
-// im_lo: value = hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits), used by
-// the low-precision modes so that the Gram-Schmidt arithmetic runs on the FP32 pipe
-// with error-free transformations (GB300's FP64 pipe is 1/64 of its FP32 rate).
+// The Krylov basis V and the work vector W hold complex numbers in one of three
+// element types (kBasis*): FP64 (double2); double-FP32 (float4 = re_hi, im_hi, re_lo,
+// im_lo: value = hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, whose
+// arithmetic runs on the FP32 pipe with error-free transformations -- GB300's FP64
+// pipe is 1/64 of its FP32 rate); or FP32 (float2, half the bytes of the other two,
+// for low-precision inner iterations whose refinement rounds each need only a modest
+// residual reduction).  The Gram-Schmidt sweeps are bound by HBM bandwidth, so the
+// element size sets their cost.
+constexpr int kBasisF64 = 0, kBasisFF = 1, kBasisF32 = 2;
+inline size_t basis_bytes(int basis) { return basis == kBasisF32 ? 8 : 16; }
+// Element type for the options' precision and px_basis choice (validated): FP64 solves
+// keep an FP64 basis; low-precision solves default to FP32 (the solve driver moves an
+// automatic basis to double-FP32 for restart cycles longer than 128 vectors).
+inline int basis_kind(int precision, int basis) {
+  if (precision == PX_FP64 || basis == PX_BASIS_FP64) return kBasisF64;
+  if (basis == PX_BASIS_FF32) return kBasisFF;
+  return kBasisF32;   // PX_BASIS_FP32 or automatic
+}
+
 struct KrylovArgs {
   int nu, Bact, m, nblk;
-  int ff;              // 1: V, W are float4 double-FP32; 0: double2 FP64
+  int basis;           // kBasisF64 (double2), kBasisFF (float4) or kBasisF32 (float2)
   void* V;             // [m+1][nu][Bact]
   void* W;             // [nu][Bact]
   double2* h;          // [2][m+1][Bact] projections of each Gram-Schmidt pass
@@ -140,6 +171,9 @@ struct KrylovArgs {
   int N;               // atoms (dipole rows start at N)
   const int* type;     // [N] atom types
   const double2* amu;  // [ntypes][Bact] alpha^IB = -1 / z_mu of each active column
+  // Step index: kernels take j as an argument, or, when jdev is set (a restart cycle
+  // captured as one graph with a device-side loop), read it from *jdev.
+  const int* jdev;
 };
 
 // Conductance + shift apply of one Krylov step (Eq. 1 / Eq. 7 on a block):
@@ -147,16 +181,17 @@ struct KrylovArgs {
 //   W[i][a] = Y_i - z_mu(type) X[i][a]         dipole rows (wFQFmu)
 // with X = V_j and Y = T X from the matvec ([np][ldy] real, re/im in columns 2a, 2a+1).
 struct ShiftArgs {
-  int nu, N, model, Bact, nblk, ff;
+  int nu, N, model, Bact, nblk, basis;
   const int* rowptr; const int* col; const double* val64; const float* val32;
   const int* type;
   const void* Y; int ldy; bool y_is_f32;
-  const void* X;                                // V_j (float4 or double2), stride Bact
+  const void* X;                                // V_j (basis element type), stride Bact
   const double2* zq;                            // [Bact]
   const double2* zmu;                           // [ntypes][Bact] (wFQFmu)
   const int* jconv;                             // columns with jconv > 0 are skipped
   int precond_mu;                               // 1: dipole rows use the right preconditioner
   void* W;
+  const int* jdev;                              // set: X is V_0 and the step is *jdev
 };
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl);
 
@@ -181,6 +216,10 @@ cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* c
 cudaError_t launch_dots(const KrylovArgs& a, int j, int pass, cudaStream_t s, long long* nl);
 cudaError_t launch_update(const KrylovArgs& a, int j, int pass, bool last, cudaStream_t s,
                           long long* nl);
+// End of a Krylov step inside a captured cycle: ++*jdev and set the while-loop
+// condition to (another step fits in m) && (some column still iterates).
+cudaError_t launch_step_advance(int* jdev, const int* active_count, int m,
+                                cudaGraphConditionalHandle loop, cudaStream_t s, long long* nl);
 cudaError_t launch_givens(const KrylovArgs& a, int j, int passes, cudaStream_t s,
                           long long* nl);
 // V[j+1] = W * inv_h; also writes the matvec operand of V[j+1] (X32 hi parts, or X64).
@@ -234,7 +273,7 @@ cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P
 // sigma_pol[f][p] = 4 pi w / c Im(e_p . alpha e_p); sigma[f] = 4 pi w/(3c) sum_p Im alpha_pp
 // (written when P == 3); q / mu copied out as [F][P][N] / [F][P][N][3].
 cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
-                               const double2* x, double e0, const double* omega_ev,
+                               const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
                                double* sigma_pol, double* sigma, cudaStream_t s, long long* nl);
 

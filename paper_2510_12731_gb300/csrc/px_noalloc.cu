@@ -54,18 +54,20 @@ cudaError_t scratch_for_current_device(void** out) {
 
 // Solution layout of px_solve_device -> the FP64 residual layouts: the column-major
 // block x[i][c] (complex) and the real matvec operand X[i][2c], X[i][2c+1].
-__global__ void k_pack_solution(int N, int model, int B, const double2* __restrict__ q,
-                                const double2* __restrict__ mu, double2* x, double* X, int ldx) {
+__global__ void k_pack_solution(int N, int model, int B, const int* __restrict__ perm,
+                                const double2* __restrict__ q, const double2* __restrict__ mu,
+                                double2* x, double* X, int ldx) {
   const int c = blockIdx.x * 32 + threadIdx.x;
   if (c >= B) return;
   const int nu = model == 1 ? 4 * N : N;
   for (int i = blockIdx.y * 8 + threadIdx.y; i < nu; i += 8 * gridDim.y) {
     double2 v;
+    // the caller's buffers are in the caller's atom order; internal atom a is perm[a]
     if (i < N) {
-      v = q[(size_t)c * N + i];
+      v = q[(size_t)c * N + perm[i]];
     } else {
       const int a = (i - N) / 3, k = (i - N) % 3;
-      v = mu[((size_t)c * N + a) * 3 + k];
+      v = mu[((size_t)c * N + perm[a]) * 3 + k];
     }
     x[(size_t)i * B + c] = v;
     X[(size_t)i * ldx + 2 * c] = v.x;
@@ -186,7 +188,7 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
   // the matvec operand's padding rows and columns must be zero
   NA_CU(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)np * ldx, s));
   k_pack_solution<<<dim3((B + 31) / 32, nblk), dim3(32, 8), 0, s>>>(
-      N, model, B, reinterpret_cast<const double2*>(d_q), reinterpret_cast<const double2*>(d_mu), x,
+      N, model, B, d.perm, reinterpret_cast<const double2*>(d_q), reinterpret_cast<const double2*>(d_mu), x,
       X, ldx);
   NA_CU(cudaGetLastError());
   if (d.matfree) NA_CU(px::launch_dgemm_mf(d.pos4d, N, np, X, ldx, Y, ldx, ldx, s, &nl));

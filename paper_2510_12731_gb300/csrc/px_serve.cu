@@ -4,6 +4,7 @@
 // the slot's own handle and stream.  Admission keeps the sum of the admitted requests'
 // device footprints (and of the memory idle slots still hold) inside the budget.
 #include "px_serve.h"
+#include "px_internal.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -72,7 +73,8 @@ size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
   const size_t nu = model == PX_WFQ ? N : 4 * (size_t)N;
   const size_t np = round_up(nu, 128);
   const size_t ldx = round_up(2 * (size_t)B, 256);
-  const size_t m = o.restart_m > 0 ? o.restart_m : (model == PX_WFQ ? 60 : 100);
+  const size_t m = o.restart_m > 0 ? o.restart_m
+                                   : (model == PX_WFQ && o.precision != PX_FP64 ? 60 : 100);
   size_t t = 0;
   if (mat) {
     t += np * np * 8;
@@ -80,8 +82,11 @@ size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
     if (o.precision == PX_FP32) t += np * np * 4;
     if (o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT) t += np * np * 4;
   }
-  t += (m + 1) * nu * B * 16;          // Krylov basis
-  t += 3 * nu * B * 16;                // W, x, r
+  // automatic low-precision bases switch to 16-byte elements for long restarts
+  const size_t esz = (o.precision != PX_FP64 && o.basis == PX_BASIS_AUTO)
+                         ? 16 : px::basis_bytes(px::basis_kind(o.precision, o.basis));
+  t += (m + 1) * nu * B * esz;         // Krylov basis
+  t += nu * B * esz + 2 * nu * B * 16; // W, x, r
   t += np * ldx * (8 + 8 + 4 + 4 + 4); // X64, Y64, X32, Y32, split operand
   t += 2 * (m + 1) * B * 16 * 4;       // projections, Hessenberg, partials (bound)
   t += (size_t)128 * (m + 1) * B * 16; // partial projections

@@ -67,6 +67,7 @@ def test_defaults_and_version_without_gpu(libpath):
     o = L.Options()
     assert lib.px_options_default(C.byref(o)) == L.PX_OK
     assert o.restart_m == 0 and o.gs_passes == 1 and o.tol_rel == 1e-7
+    assert o.basis == L.PX_BASIS_AUTO and o.gemm_tiles == 0 and o.cycle_graphs == 1
     assert lib.px_options_default(None) == L.PX_EINVAL
     assert lib.px_destroy(None) == L.PX_OK
 
@@ -80,6 +81,22 @@ def test_create_rejects_bad_options(libpath):
     assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
     assert b"restart_m" in lib.px_last_error(None)
     assert lib.px_create(None, C.byref(o)) == L.PX_EINVAL
+    lib.px_options_default(C.byref(o))
+    o.basis = 4
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    assert b"basis" in lib.px_last_error(None)
+    # an FP64 solve keeps an FP64 basis
+    o.basis = L.PX_BASIS_FP32
+    o.precision = L.PX_FP64
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    assert b"FP64" in lib.px_last_error(None)
+    lib.px_options_default(C.byref(o))
+    o.gemm_tiles = 3
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    lib.px_options_default(C.byref(o))
+    o.cycle_graphs = 2
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    assert b"cycle_graphs" in lib.px_last_error(None)
 
 
 def test_calls_on_null_handle_fail_cleanly(libpath):

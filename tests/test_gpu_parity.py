@@ -190,7 +190,7 @@ def test_bf16split_before_refinement_within_1e3(model):
     w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=12, wmin=2.0, wmax=5.5)
     ref, _ = _oracle(w)
     out, _ = _run(w, precision="bf16split", tol_rel=1e-9, inner_tol=1e-8, max_refine=0,
-                  restart_m=200)
+                  restart_m=200, basis="ff32")
     assert _alpha_err(out, ref) <= 1e-3
 
 
@@ -226,11 +226,124 @@ def test_fp16split_before_refinement_beats_bf16split(model):
     5x closer to the oracle, and within 1e-4."""
     w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=12, wmin=2.0, wmax=5.5)
     ref, _ = _oracle(w)
-    kw = dict(tol_rel=1e-9, inner_tol=1e-8, max_refine=0, restart_m=200)
+    kw = dict(tol_rel=1e-9, inner_tol=1e-8, max_refine=0, restart_m=200, basis="ff32")
     e16 = _alpha_err(_run(w, precision="fp16split", **kw)[0], ref)
     ebf = _alpha_err(_run(w, precision="bf16split", **kw)[0], ref)
     assert e16 <= 1e-4
     assert e16 <= ebf / 5
+
+
+# ------------------------------------------------------------------ tensor-core tile variants
+
+@pytest.mark.parametrize("precision", ["bf16split", "fp16split"])
+def test_gemm_tile_variants_are_bit_identical(precision):
+    """128 x 256 and 128 x 128 tiles accumulate every output's K products in the same
+    order, so the whole solve (deterministic reductions) gives bit-identical results;
+    the autotuned default picks one of them."""
+    # Na sphere r = 20 A: N = 893 (7 row tiles, ragged); 50 w x 3 pols = 150 columns ->
+    # 300 real operand columns padded to 512: 2 column tiles of 256 or 4 of 128
+    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=50, wmin=2.0, wmax=4.0)
+    outs = []
+    for tiles in (1, 2, 0):
+        out, stats = _run(w, precision=precision, tol_rel=1e-8, gemm_tiles=tiles)
+        assert out["ok"]
+        assert stats["gemm_tiles_used"] in ((tiles,) if tiles else (1, 2))
+        outs.append(out)
+    for o in outs[1:]:
+        assert np.array_equal(o["alpha"], outs[0]["alpha"])
+        assert np.array_equal(o["iters"], outs[0]["iters"])
+
+
+# ------------------------------------------------------------------ restart cycles as graphs
+
+@pytest.mark.parametrize("model,precision", [("wfq", "fp64"), ("wfq", "fp32"),
+                                             ("wfq", "bf16split"), ("wfqfmu", "fp16split")])
+def test_cycle_graphs_match_eager_launches(model, precision):
+    """A restart cycle run as one graph launch (device-side loop over the Krylov steps)
+    executes the same kernels on the same data as the eager per-step launches, so the
+    results are bit-identical; the eager path runs at most one idle step more."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=20, wmin=2.0, wmax=5.5)
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    eager, st_e = _run(w, precision=precision, tol_rel=tol, cycle_graphs=0)
+    graph, st_g = _run(w, precision=precision, tol_rel=tol, cycle_graphs=1)
+    prof, st_p = _run(w, precision=precision, tol_rel=tol, cycle_graphs=1, profile=1)
+    assert eager["ok"] and graph["ok"]
+    assert st_e["graph_launches"] == 0 and st_p["graph_launches"] == 0
+    assert st_g["graph_launches"] == st_g["cycles"] > 0
+    for k in ("alpha", "q", "rel_residual", "iters"):
+        assert np.array_equal(graph[k], eager[k]), k
+        assert np.array_equal(prof[k], eager[k]), k
+    assert st_g["total_iters"] <= st_e["total_iters"]
+
+
+def test_cycle_graph_cache_survives_repeated_solves_and_new_structures():
+    """Repeated solves reuse the handle's instantiated graphs; a new structure drops
+    them; results stay those of fresh handles."""
+    from paper_2510_12731_gb300 import Solver
+    w1 = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=10, wmin=2.0, wmax=5.5)
+    w2 = S.small_cluster(element="Na", radius=12.0, model="wfq", nfreq=10, wmin=2.0, wmax=4.0)
+    ref1, _ = _run(w1, precision="fp32", tol_rel=1e-9)
+    ref2, _ = _run(w2, precision="fp32", tol_rel=1e-9)
+    with Solver(precision="fp32", tol_rel=1e-9) as s:
+        for w, ref in ((w1, ref1), (w1, ref1), (w2, ref2), (w1, ref1)):
+            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+            for _ in range(2):
+                out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib)
+                assert np.array_equal(out["alpha"], ref["alpha"])
+
+
+# ------------------------------------------------------------------ structure staging order
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_morton_order_is_invisible_to_the_caller(model):
+    """Internal Morton order vs the caller's order, and a shuffled input: alpha agrees to
+    rounding and per-atom outputs come back in the caller's order."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=6, wmin=2.0, wmax=5.5)
+    ref, _ = _run(w, precision="fp64", tol_rel=1e-11, sort_atoms=0)
+    srt, _ = _run(w, precision="fp64", tol_rel=1e-11, sort_atoms=1)
+    rng = np.random.default_rng(7)
+    perm = rng.permutation(w.natoms)
+    ws = S.Workload(**{**w.__dict__, "xyz_ang": w.xyz_ang[perm], "type_idx": w.type_idx[perm]})
+    shf, _ = _run(ws, precision="fp64", tol_rel=1e-11, sort_atoms=1)
+    scale = np.abs(ref["alpha"]).max()
+    assert np.abs(srt["alpha"] - ref["alpha"]).max() <= 1e-9 * scale
+    assert np.abs(shf["alpha"] - ref["alpha"]).max() <= 1e-9 * scale
+    qs = np.abs(ref["q"]).max()
+    assert np.abs(srt["q"] - ref["q"]).max() <= 1e-8 * qs
+    assert np.abs(shf["q"] - ref["q"][..., perm]).max() <= 1e-8 * qs
+    if model == "wfqfmu":
+        ms = np.abs(ref["mu"]).max()
+        assert np.abs(shf["mu"] - ref["mu"][:, :, perm]).max() <= 1e-8 * ms
+
+
+# ------------------------------------------------------------------ Krylov basis storage
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
+@pytest.mark.parametrize("basis", ["fp64", "ff32", "fp32"])
+def test_every_basis_reaches_the_fp64_tolerance(model, precision, basis):
+    """The basis element type changes only the inner iteration: with the FP64 true
+    residual and refinement every choice meets the same per-column tolerance and alpha
+    agrees with the oracle."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=30, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision=precision, tol_rel=1e-9, basis=basis)
+    assert out["ok"], out["rel_residual"].max()
+    assert np.all(out["rel_residual"] <= 1e-9)
+    assert _alpha_err(out, ref) <= 1e-6
+
+
+def test_fp32_basis_single_round_is_limited_by_fp32_not_by_the_matvec():
+    """One round with the FP32 basis and an FP32 matvec, asked for 1e-8: the implicit
+    residual no longer follows the true one below a few FP32 ulps, so the unrefined
+    alpha is accurate to ~1e-5 but not to 1e-8; refinement rounds close the gap."""
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=12, wmin=2.0, wmax=5.5)
+    ref, _ = _oracle(w)
+    out1, _ = _run(w, precision="fp32", tol_rel=1e-9, inner_tol=1e-8, max_refine=0,
+                   restart_m=200, basis="fp32")
+    assert _alpha_err(out1, ref) <= 1e-4
+    out2, _ = _run(w, precision="fp32", tol_rel=1e-9, basis="fp32")
+    assert out2["ok"] and _alpha_err(out2, ref) <= 1e-7
 
 
 # ------------------------------------------------------------------ matrix-free (on the fly)
