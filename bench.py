@@ -52,13 +52,20 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches):
+def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches, n_u=None):
     """Roofline entry of the block matvec (the dominant kernel) for the precision used."""
     achieved = flops_per_launch / avg_launch_s / 1e12
     if prec in ("bf16split", "fp16split"):
         peaks, src = _measured_peaks()
         peak = float(peaks["bf16_tflops_sustained"])
-        traffic, _ = _profile_traffic("k_gemm_tc.cu", f"k_tc_gemm_{prec}.md")
+        traffic = None
+        ratio = _profile_ratio("k_gemm_tc.cu", "k_tc_gemm_fp16split.md")
+        if ratio is not None and n_u:
+            # algorithmic bytes of the average launch: T hi + lo once, the hi/lo operand
+            # and the FP32 result for its 2 B real columns
+            np_ = -(-n_u // 128) * 128
+            b_avg = flops_per_launch / (4.0 * n_u * n_u)
+            traffic = ratio * (4.0 * np_ * np_ + 16.0 * np_ * b_avg)
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"k_tc_gemm (tcgen05 {prec} block matvec, 3 MMAs per product)",
@@ -154,9 +161,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline traffic
+# Device code of a kernel source: the text before its first host-side launcher helper
+# (the host code below that line does not change what the kernel executes).
+DEVICE_PART_END = {"k_gemm_tc.cu": b"PFN_cuTensorMapEncodeTiled_v12000 encode_fn()"}
+
+
+def kernel_source_sha(kernel_file):
+    """sha256 of the device part of a kernel source (the whole file where no end marker
+    is listed)."""
+    src = os.path.join(ROOT, "paper_2510_12731_gb300", "csrc", kernel_file)
+    data = open(src, "rb").read()
+    end = DEVICE_PART_END.get(kernel_file)
+    if end is not None and end in data:
+        data = data[:data.index(end)]
+    return hashlib.sha256(data).hexdigest()
+
+
 def _profile_traffic(kernel_file, profile_file):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current source of the kernel (the summary records the source's sha256)."""
+    current device code of the kernel (the summary records its sha256)."""
     path = os.path.join(ROOT, "profiles", profile_file)
     src = os.path.join(ROOT, "paper_2510_12731_gb300", "csrc", kernel_file)
     if not (os.path.exists(path) and os.path.exists(src)):
@@ -164,10 +187,24 @@ def _profile_traffic(kernel_file, profile_file):
     text = open(path).read()
     m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_tr = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = kernel_source_sha(kernel_file)
     if not (m_sha and m_tr) or m_sha.group(1) != sha:
         return None, sha
     return float(m_tr.group(1)), sha
+
+
+def _profile_ratio(kernel_file, profile_file):
+    """Measured DRAM bytes / algorithmic bytes of one captured launch, from a committed
+    ncu summary taken on the current device code (None otherwise)."""
+    path = os.path.join(ROOT, "profiles", profile_file)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_r = re.search(r"dram_over_algorithmic:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_r) or m_sha.group(1) != kernel_source_sha(kernel_file):
+        return None
+    return float(m_r.group(1))
 
 
 # ---------------------------------------------------------------- multi-rank helpers
@@ -212,8 +249,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     wl = _workload(args.workload)
+    # one full-size sample is ~100 s of CPU work (a dense LU of the whole system), so the
+    # untimed warm-up steps run the same code on the 791-atom Ag sphere (BLAS thread pool
+    # and allocator warm-up) and the run stays within a few minutes
+    warm_wl = _workload("ag_sphere")
     for _ in range(args.warmup):
-        _oracle_sample(wl, args.cpu_freqs)
+        _oracle_sample(warm_wl, 1)
     times = []
     pts = 0
     for _ in range(args.steps):
@@ -231,6 +272,7 @@ def run_reference(args, rank, world):
             "config": {"workload": wl.name, "natoms": wl.natoms, "columns": wl.ncols},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                              "sample": sample},
+            "warmup_sample": "dense LU of the 791-atom Ag sphere, 1 frequency",
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -359,7 +401,8 @@ def run_ours(args, rank, world, local_rank):
     graph_launches = st["graph_launches"]
     avg_launch_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
     flops_per_launch = mv_flops / mv_n if mv_n else float("nan")
-    roofline = _roofline(prec, opts["mode"], flops_per_launch, avg_launch_s, mv_n)
+    roofline = _roofline(prec, opts["mode"], flops_per_launch, avg_launch_s, mv_n,
+                         n_u=N if wl.model == "wfq" else 4 * N)
 
     # ---- plain FP64 GPU solve (P0): one (frequency, polarisation) column at a time, FP64
     # matvec (GEMV on the FP64 T) and FP64 GMRES, same tolerance; timed on a sample of

@@ -125,8 +125,9 @@ typedef struct {
                                AUTO and PX_BASIS_FP64 */
   int gemm_tiles;           /* tile shape of the tensor-core matvec: 0 (default) = autotuned
                                per (rows, columns) shape on first use, cached per process;
-                               1 = 128 x 256 tiles, 2-stage ring; 2 = 128 x 128 tiles,
-                               3-stage ring.  Every choice gives bit-identical results */
+                               1 = 128 x 256 tiles, 2-stage ring (where the padded operand
+                               column count is a multiple of 256, else 2 runs); 2 = 128 x 128
+                               tiles, 3-stage ring.  Every choice gives bit-identical results */
   int cycle_graphs;         /* 1 (default): each restart cycle is one CUDA graph launch whose
                                device-side while loop runs the Krylov steps (matvec, shift,
                                Gram-Schmidt, Givens, normalisation) until every column stopped

@@ -400,14 +400,18 @@ std::map<std::tuple<int, int, int, int>, int> g_tune;
 
 cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
                            const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
-                           cudaStream_t s, long long* nl, int variant) {
-  // shape contract: M and K tiles of 128 / 64 rows of T, N tiles of 256 operand columns,
-  // 16-byte aligned rows; every TMA x coordinate is a multiple of 64 elements (128 bytes).
-  if (np % TC_BM || ncols % 256 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
+                           cudaStream_t s, long long* nl, int variant, int* used) {
+  // shape contract: M and K tiles of 128 / 64 rows of T, N tiles of 128 or 256 operand
+  // columns, 16-byte aligned rows; every TMA x coordinate is a multiple of 64 elements
+  // (128 bytes).  The 256-column tiles need ncols % 256 == 0; other column counts run
+  // the 128-column tiles.
+  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(Th) | reinterpret_cast<uintptr_t>(Tl) |
        reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
     return cudaErrorMisalignedAddress;
   if (variant < -1 || variant >= kTcVariants) return cudaErrorInvalidValue;
+  auto fits = [&](int v) { return ncols % kTcBN[v] == 0; };
+  if (variant >= 0 && !fits(variant)) variant = 1;   // 128-column tiles fit every shape
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -443,6 +447,7 @@ cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const
         if (e != cudaSuccess) return e;
       }
       for (int v = 0; v < kTcVariants && e == cudaSuccess; ++v) {
+        if (!fits(v)) continue;
         if (!encode(kTcBN[v])) e = cudaErrorInvalidValue;
         if (e == cudaSuccess) e = launch_tc_variant(v, f16, maps, np, ncols, Y, ldy, err, s);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * v], s);
@@ -453,11 +458,12 @@ cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const
       }
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[2 * kTcVariants - 1]);
       float best_ms = 0.f;
-      variant = 0;
+      variant = -1;
       for (int v = 0; v < kTcVariants && e == cudaSuccess; ++v) {
+        if (!fits(v)) continue;
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, ev[2 * v], ev[2 * v + 1]);
-        if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+        if (e == cudaSuccess && (variant < 0 || ms < best_ms)) {
           best_ms = ms;
           variant = v;
         }
@@ -471,6 +477,7 @@ cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const
   if (!encode(kTcBN[variant])) return cudaErrorInvalidValue;
   e = launch_tc_variant(variant, f16, maps, np, ncols, Y, ldy, err, s);
   ++*nl;
+  if (used) *used = variant;
   return e;
 }
 

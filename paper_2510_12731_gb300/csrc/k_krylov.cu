@@ -636,40 +636,108 @@ __global__ void k_backsolve(KrylovArgs a, int jend, const int* act, double* beta
   iters[gc] += jc;
 }
 
-// x[., act[a]] += sum_{k<jc} V_k y_k ;  r[., act[a]] = sum_{k<=jc} V_k u_k  (FP64 sums)
+// x[., act[a]] += sum_{k<jc} V_k y_k ;  r[., act[a]] = sum_{k<=jc} V_k u_k  (FP64 sums;
+// r is required).  Each thread keeps four rows' sums in registers per sweep over a chunk
+// of 32 basis vectors whose y, u coefficients are staged in shared memory, so four loads
+// of V are in flight per thread.  Per-row-block partial sums of |r|^2 go to
+// normpart[blk][a]: the norm of the implicit residual V u equals |gamma| only while the
+// basis is orthonormal, and the next cycle is normalised by the measured norm, so a
+// basis that lost orthogonality (FP32 classical Gram-Schmidt on a slowly converging
+// column) cannot mis-scale it.
 template <class E>
 __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, double2* x,
                                                  double2* r, int B) {
   using TT = Tr<E>;
-  const int col = blockIdx.x * 32 + threadIdx.x;
-  if (col >= a.Bact) return;
-  const int gc = act[col];
-  const int jc = a.jconv[col];
+  constexpr int kXChunk = 32, kRows = 4;
+  __shared__ double2 shy[kXChunk][32], shu[kXChunk][32];
+  __shared__ double sh[8][32];
+  __shared__ int sh_jmax;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int col = blockIdx.x * 32 + tx;
+  const bool valid = col < a.Bact;
+  const int jc = valid ? a.jconv[col] : 0;
+  // basis vectors the block reads: the largest jc of its 32 columns (every warp of the
+  // block holds the same columns)
+  int jmax = jc;
+  for (int o = 16; o > 0; o >>= 1) jmax = max(jmax, __shfl_xor_sync(0xffffffffu, jmax, o));
+  if (tx == 0 && ty == 0) sh_jmax = jmax;
+  __syncthreads();
+  jmax = sh_jmax;
   const size_t vstride = (size_t)a.nu * a.Bact;
   const E* V = static_cast<const E*>(a.V);
-  for (int i = blockIdx.y * 8 + threadIdx.y; i < a.nu; i += 8 * gridDim.y) {
-    const size_t off = (size_t)i * a.Bact + col;
-    double2 dx = make_double2(0.0, 0.0);
-    double2 ar = make_double2(0.0, 0.0);
-    for (int k = 0; k <= jc; ++k) {
-      const double2 v = TT::to_c(V[(size_t)k * vstride + off]);
-      const double2 pu = cmul(v, a.u[(size_t)k * a.Bact + col]);
-      ar.x += pu.x;
-      ar.y += pu.y;
-      if (k < jc) {
-        const double2 py = cmul(v, a.y[(size_t)k * a.Bact + col]);
-        dx.x += py.x;
-        dx.y += py.y;
+  const int rows_per_blk = (a.nu + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per_blk;
+  const int r1 = min(a.nu, r0 + rows_per_blk);
+  const int nrows = max(0, (r1 - r0 - ty + 7) / 8);   // rows r0 + ty + 8 q of this thread
+  const int gc = valid ? act[col] : 0;
+  double nrm = 0.0;
+  for (int k0 = 0; k0 <= jmax; k0 += kXChunk) {
+    const int kend = min(jmax + 1, k0 + kXChunk);   // uniform over the block
+    if (k0 > 0) __syncthreads();                    // previous chunk consumed
+    for (int k = k0 + ty; k < kend; k += 8) {
+      shy[k - k0][tx] = (valid && k < jc) ? a.y[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0);
+      shu[k - k0][tx] = (valid && k <= jc) ? a.u[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (!valid) continue;
+    const bool first = k0 == 0, last = kend == jmax + 1;
+    for (int rb = 0; rb < nrows; rb += kRows) {
+      double2 dx[kRows], ar[kRows];
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) dx[q] = ar[q] = make_double2(0.0, 0.0);
+      for (int k = k0; k < kend; ++k) {
+        const double2 yk = shy[k - k0][tx], uk = shu[k - k0][tx];
+        E v[kRows];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q)
+          if (rb + q < nrows)
+            v[q] = V[(size_t)k * vstride + (size_t)(r0 + ty + 8 * (rb + q)) * a.Bact + col];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+          if (rb + q >= nrows) continue;
+          const double2 vc = TT::to_c(v[q]);
+          const double2 pu = cmul(vc, uk), py = cmul(vc, yk);
+          ar[q].x += pu.x;
+          ar[q].y += pu.y;
+          dx[q].x += py.x;
+          dx[q].y += py.y;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        if (rb + q >= nrows) continue;
+        const int i = r0 + ty + 8 * (rb + q);
+        // x += M V y with M = alpha^IB on the dipole rows (right preconditioner)
+        double2 d = dx[q];
+        if (a.amu && i >= a.N) d = cmul(a.amu[(size_t)a.type[(i - a.N) / 3] * a.Bact + col], d);
+        double2 ax = x[(size_t)i * B + gc];
+        ax.x += d.x;
+        ax.y += d.y;
+        x[(size_t)i * B + gc] = ax;
+        double2 rv = first ? make_double2(0.0, 0.0) : r[(size_t)i * B + gc];
+        rv.x += ar[q].x;
+        rv.y += ar[q].y;
+        r[(size_t)i * B + gc] = rv;
+        if (last) nrm += rv.x * rv.x + rv.y * rv.y;
       }
     }
-    // x += M V y with M = alpha^IB on the dipole rows (right preconditioner)
-    if (a.amu && i >= a.N) dx = cmul(a.amu[(size_t)a.type[(i - a.N) / 3] * a.Bact + col], dx);
-    double2 ax = x[(size_t)i * B + gc];
-    ax.x += dx.x;
-    ax.y += dx.y;
-    x[(size_t)i * B + gc] = ax;
-    if (r) r[(size_t)i * B + gc] = ar;
   }
+  sh[ty][tx] = nrm;
+  __syncthreads();
+  if (ty == 0 && valid) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k][tx];
+    a.normpart[(size_t)blockIdx.y * a.Bact + col] = t;
+  }
+}
+
+// beta[act[a]] = || V u ||, the measured norm of the implicit residual
+__global__ void k_beta_measured(KrylovArgs a, const int* act, double* beta) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= a.Bact) return;
+  double t = 0.0;
+  for (int b = 0; b < a.nblk; ++b) t += a.normpart[(size_t)b * a.Bact + col];
+  beta[act[col]] = sqrt(t);
 }
 
 __global__ void __launch_bounds__(256) k_gather_x(const double2* x, int B, const int* act,
@@ -813,7 +881,8 @@ cudaError_t launch_cycle_end(const KrylovArgs& a, int jend, const int* act, doub
   with_basis(a.basis, [&](auto e) {
     k_xupdate<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, act, x, r, B);
   });
-  *nl += 2;
+  k_beta_measured<<<(a.Bact + 127) / 128, 128, 0, s>>>(a, act, beta);
+  *nl += 3;
   return cudaGetLastError();
 }
 

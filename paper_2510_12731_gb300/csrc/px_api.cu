@@ -445,7 +445,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const bool tc = o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT;
   const bool tc_f16 = o.precision == PX_FP16SPLIT;
   if (tc && d.Thi == nullptr) throw PxError{PX_EINVAL, "precision changed since px_set_structure"};
-  const size_t colpad = tc ? 256 : px::kTile;   // operand column padding of the matvec kernel
+  const size_t colpad = px::kTile;   // operand column padding of every matvec kernel
   // stopping targets of the inner (low-precision) iteration:
   //   max(inner_tol * ||r_outer||, tol_frac * tol * ||b||)
   const double inner_tol = lowp ? o.inner_tol : 0.0;
@@ -620,11 +620,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
         } else if (tc) {
           CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt));
+          int used = -1;
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, q,
-                                cnt, o.gemm_tiles - 1));
-          if (st.gemm_tiles_used == 0)
-            st.gemm_tiles_used = o.gemm_tiles ? o.gemm_tiles
-                                              : px::tc_tuned_variant(np, ldxa, tc_f16) + 1;
+                                cnt, o.gemm_tiles - 1, &used));
+          if (st.gemm_tiles_used == 0) st.gemm_tiles_used = used + 1;
         } else if (lowp) {
           CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
         } else if (2 * Bact <= 8) {
@@ -659,7 +658,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           // tune the tensor-core tile shape on this cycle's operands before capture
           CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
-                                &nl, -1));
+                                &nl, -1, nullptr));
         }
         const std::vector<uint64_t> key = {
             (uint64_t)Bact, (uint64_t)mc, (uint64_t)ldxa, (uint64_t)passes, (uint64_t)A.basis,

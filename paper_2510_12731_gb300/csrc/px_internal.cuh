@@ -114,13 +114,15 @@ cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, doub
                          int nc, cudaStream_t s, long long* nl);
 // Tensor-core split-precision matvec Y = T X from hi/lo 16-bit parts of T and X
 // (bf16, or scaled fp16 when f16).  Xh / Xl are the transposed operand [ncols][np]
-// (K-major); np % 128 == 0, ncols % 256 == 0.  *err is set to 1 if a pipeline wait
-// ran out of time.  variant: 0 = 128 x 256 tiles (2-stage ring), 1 = 128 x 128 tiles
-// (3-stage ring), -1 = autotuned: the first call of a (np, ncols, f16) shape times every
-// variant on its operands (synchronising the stream once) and caches the fastest.
+// (K-major); np % 128 == 0, ncols % 128 == 0.  *err is set to 1 if a pipeline wait
+// ran out of time.  variant: 0 = 128 x 256 tiles (2-stage ring; only when ncols % 256
+// == 0, else variant 1 runs), 1 = 128 x 128 tiles (3-stage ring), -1 = autotuned: the
+// first call of a (np, ncols, f16) shape times every variant that fits on its operands
+// (synchronising the stream once) and caches the fastest.  *used (may be NULL) receives
+// the variant launched.
 cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const uint16_t* Xh,
                            const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int* err,
-                           cudaStream_t s, long long* nl, int variant);
+                           cudaStream_t s, long long* nl, int variant, int* used);
 // The autotuner's cached variant for a shape on the current device, or -1.
 int tc_tuned_variant(int np, int ncols, bool f16);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
@@ -231,8 +233,9 @@ cudaError_t launch_cycle_start(const KrylovArgs& a, const int* act, const double
                                const double* beta, const double* target_all, float* X32,
                                double* X64, int ldx, cudaStream_t s, long long* nl);
 // Cycle end: y = R^-1 g, u = Omega^H (0..0, gamma) per column; x[., act[a]] += V y,
-// r[., act[a]] = V u (the residual of the inner iteration), beta[act[a]] = |gamma|,
-// iters[act[a]] += basis size used.
+// r[., act[a]] = V u (the residual of the inner iteration; r must not be NULL),
+// beta[act[a]] = ||V u|| (measured, not |gamma|, so a basis that lost orthogonality
+// cannot mis-scale the next cycle), iters[act[a]] += basis size used.
 cudaError_t launch_cycle_end(const KrylovArgs& a, int jend, const int* act, double2* x,
                              double2* r, int B, double* beta, int* iters, cudaStream_t s,
                              long long* nl);

@@ -240,9 +240,10 @@ def test_gemm_tile_variants_are_bit_identical(precision):
     """128 x 256 and 128 x 128 tiles accumulate every output's K products in the same
     order, so the whole solve (deterministic reductions) gives bit-identical results;
     the autotuned default picks one of them."""
-    # Na sphere r = 20 A: N = 893 (7 row tiles, ragged); 50 w x 3 pols = 150 columns ->
-    # 300 real operand columns padded to 512: 2 column tiles of 256 or 4 of 128
-    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=50, wmin=2.0, wmax=4.0)
+    # Na sphere r = 20 A: N = 893 (7 row tiles, ragged); 64 w x 2 pols = 128 columns ->
+    # 256 real operand columns in the first cycle: 1 column tile of 256 or 2 of 128
+    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=64, wmin=2.0, wmax=4.0)
+    w.pol_dirs = w.pol_dirs[:2]
     outs = []
     for tiles in (1, 2, 0):
         out, stats = _run(w, precision=precision, tol_rel=1e-8, gemm_tiles=tiles)
@@ -252,6 +253,17 @@ def test_gemm_tile_variants_are_bit_identical(precision):
     for o in outs[1:]:
         assert np.array_equal(o["alpha"], outs[0]["alpha"])
         assert np.array_equal(o["iters"], outs[0]["iters"])
+
+
+def test_gemm_tiles_fall_back_to_128_columns_when_256_do_not_fit():
+    """64 w x 3 pols = 192 columns -> 384 real operand columns, not a multiple of 256:
+    asking for 128 x 256 tiles runs 128 x 128 tiles, with results identical to asking
+    for those directly."""
+    w = S.small_cluster(element="Na", radius=20.0, model="wfq", nfreq=64, wmin=2.0, wmax=4.0)
+    a, st_a = _run(w, precision="fp16split", tol_rel=1e-8, gemm_tiles=1)
+    b, st_b = _run(w, precision="fp16split", tol_rel=1e-8, gemm_tiles=2)
+    assert st_a["gemm_tiles_used"] == 2 and st_b["gemm_tiles_used"] == 2
+    assert a["ok"] and np.array_equal(a["alpha"], b["alpha"])
 
 
 # ------------------------------------------------------------------ restart cycles as graphs
