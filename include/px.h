@@ -78,9 +78,7 @@ typedef enum {
 /* Storage and arithmetic of the Krylov basis V and the Gram-Schmidt sweeps over it
  * (the sweeps are bound by HBM bandwidth, so the element size sets their cost). */
 typedef enum {
-  PX_BASIS_AUTO = 0,  /* PX_FP64: FP64; low-precision matvecs: FP32 for restart cycles of
-                         up to 128 vectors, double-FP32 for longer ones (shrunken active
-                         sets), where classical Gram-Schmidt in FP32 loses orthogonality */
+  PX_BASIS_AUTO = 0,  /* PX_FP64: FP64; low-precision matvecs: FP32 */
   PX_BASIS_FP64 = 1,  /* FP64 complex, 16 bytes per entry */
   PX_BASIS_FF32 = 2,  /* double-FP32 complex (hi + lo pairs, ~48 bits), 16 bytes per
                          entry; arithmetic on the FP32 pipe with error-free transforms */

@@ -239,7 +239,18 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
     const E xv = X[off];
     double yr, yi;
     auto zz = zq;
-    if (i < a.N) {
+    if (i < a.N && a.kbar_in_y) {
+      // the matvec applied M = diag(Kbar, I) T: no conductance gather
+      if (F32Y) {
+        const float* Y = static_cast<const float*>(a.Y);
+        yr = Y[(size_t)i * a.ldy + 2 * col] * a.yscale;
+        yi = Y[(size_t)i * a.ldy + 2 * col + 1] * a.yscale;
+      } else {
+        const double* Y = static_cast<const double*>(a.Y);
+        yr = Y[(size_t)i * a.ldy + 2 * col] * (double)a.yscale;
+        yi = Y[(size_t)i * a.ldy + 2 * col + 1] * (double)a.yscale;
+      }
+    } else if (i < a.N) {
       if (F32Y) {
         const float* Y = static_cast<const float*>(a.Y);
         const float y0r = Y[(size_t)i * a.ldy + 2 * col], y0i = Y[(size_t)i * a.ldy + 2 * col + 1];
@@ -271,14 +282,15 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
       // -z_mu alpha^IB v = +v: the shift term becomes +v
       zz = a.precond_mu ? TT::coef(make_double2(-1.0, 0.0))
                         : TT::coef(a.zmu[(size_t)a.type[atom] * a.Bact + col]);
+      const float ys = a.kbar_in_y ? a.yscale : 1.0f;
       if (F32Y) {
         const float* Y = static_cast<const float*>(a.Y);
-        yr = Y[(size_t)i * a.ldy + 2 * col];
-        yi = Y[(size_t)i * a.ldy + 2 * col + 1];
+        yr = Y[(size_t)i * a.ldy + 2 * col] * ys;
+        yi = Y[(size_t)i * a.ldy + 2 * col + 1] * ys;
       } else {
         const double* Y = static_cast<const double*>(a.Y);
-        yr = Y[(size_t)i * a.ldy + 2 * col];
-        yi = Y[(size_t)i * a.ldy + 2 * col + 1];
+        yr = Y[(size_t)i * a.ldy + 2 * col] * (double)ys;
+        yi = Y[(size_t)i * a.ldy + 2 * col + 1] * (double)ys;
       }
     }
     W[off] = TT::axpy_shift(yr, yi, zz, xv);

@@ -219,6 +219,64 @@ __global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32
   }
 }
 
+// One block per row i of M = diag(Kbar, I) T: charge rows apply the CSR of K (Eq. 2,
+// Laplacian form) to the rows of T in FP64; other rows copy T.  Block max |M| goes to
+// *absmax_bits with an integer atomicMax on the bits of the (non-negative) double.
+__global__ void __launch_bounds__(256) k_build_M(const double* __restrict__ T, int np, int N,
+                                                 const int* __restrict__ rowptr,
+                                                 const int* __restrict__ col,
+                                                 const double* __restrict__ val, double* M,
+                                                 unsigned long long* absmax_bits) {
+  const int i = blockIdx.x;
+  const double* Ti = T + (size_t)i * np;
+  double* Mi = M + (size_t)i * np;
+  double amax = 0.0;
+  if (i < N) {
+    const int e0 = rowptr[i], e1 = rowptr[i + 1];
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+      const double ti = Ti[k];
+      double acc = 0.0;
+      for (int e = e0; e < e1; ++e) acc = fma(val[e], T[(size_t)col[e] * np + k] - ti, acc);
+      Mi[k] = acc;
+      amax = fmax(amax, fabs(acc));
+    }
+  } else {
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+      const double v = Ti[k];
+      Mi[k] = v;
+      amax = fmax(amax, fabs(v));
+    }
+  }
+  __shared__ double sh[8];
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    atomicMax(absmax_bits, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// hi/lo 16-bit split of an FP64 operator (see launch_split_op)
+__global__ void k_split_op(const double* __restrict__ A, size_t n, uint16_t* hi, uint16_t* lo,
+                           int f16, double scale) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double v = A[k];
+    if (f16) {
+      const double vs = v * scale;
+      const __half h = __float2half_rn((float)vs);
+      hi[k] = __half_as_ushort(h);
+      lo[k] = __half_as_ushort(__float2half_rn((float)((vs - (double)__half2float(h)) * 2048.0)));
+    } else {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      hi[k] = __bfloat16_as_ushort(h);
+      lo[k] = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(h)));
+    }
+  }
+}
+
 __global__ void k_stage_pos4(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
                              float4* p4f, double* p4d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,6 +346,20 @@ cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaSt
   int blocks = 152 * 16;
   k_convert_T<<<blocks, threads, 0, s>>>(d.T64, n, f32 ? d.T32 : nullptr, split ? d.Thi : nullptr,
                                          split ? d.Tlo : nullptr, d.t_f16 ? 1 : 0);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_M64(const DevStructure& d, double* M64,
+                             unsigned long long* absmax_bits, cudaStream_t s, long long* nl) {
+  k_build_M<<<d.np, 256, 0, s>>>(d.T64, d.np, d.N, d.rowptr, d.col, d.val64, M64, absmax_bits);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_op(const double* A, size_t n, uint16_t* hi, uint16_t* lo, bool f16,
+                            int scale_exp, cudaStream_t s, long long* nl) {
+  k_split_op<<<152 * 16, 256, 0, s>>>(A, n, hi, lo, f16 ? 1 : 0, ldexp(1.0, scale_exp));
   ++*nl;
   return cudaGetLastError();
 }

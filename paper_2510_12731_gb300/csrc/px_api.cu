@@ -60,7 +60,6 @@ struct CycleGraph {
   long long body_kernels = 0;
 };
 constexpr size_t kMaxCachedGraphs = 64;
-constexpr int kAutoF32MaxRestart = 128;   // longest restart run with an automatic FP32 basis
 
 }  // namespace
 
@@ -78,6 +77,7 @@ struct px_handle {
   DevBuf b_perm;   // [N] caller index of internal atom i
   DevBuf b_stage;  // staging inputs (caller order) and sort scratch
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
+  DevBuf b_M64;    // FP64 M = diag(Kbar, I) T while its split planes are built
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
   DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
@@ -108,7 +108,7 @@ void drop_graphs(px_handle* h) {
 }
 
 void free_all(px_handle* h) {
-  DevBuf* bufs[] = {&h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
+  DevBuf* bufs[] = {&h->b_M64, &h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
                     &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
@@ -202,10 +202,6 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     if (a.drude_n_au != types[0].drude_n_au || a.tau_au != types[0].tau_au)
       throw PxError{PX_EINVAL, "all atom types must share drude_n_au and tau_au (Eq. 1 has one z_q)"};
   }
-  if (h->opt.precision == PX_FP16SPLIT)
-    for (int t = 0; t < ntypes; ++t)
-      if (types[t].Rq_bohr < 0.5 || types[t].Rmu_bohr < 0.5)
-        throw PxError{PX_EINVAL, "fp16split needs Gaussian widths >= 0.5 bohr (fp16 range of 4096 T)"};
   for (int i = 0; i < N; ++i) {
     if (tidx[i] < 0 || tidx[i] >= ntypes) throw PxError{PX_EINVAL, "type index out of range"};
     for (int k = 0; k < 3; ++k)
@@ -323,7 +319,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   size_t need = np2 * sizeof(double);
   if (prec != PX_FP64) need += 2 * np2 * sizeof(float);   // double-FP32 planes (residual)
   if (prec == PX_FP32) need += np2 * sizeof(float);
-  if (split) need += 2 * np2 * sizeof(uint16_t);
+  if (split) need += 2 * np2 * sizeof(uint16_t) + np2 * sizeof(double);   // + transient FP64 M
   size_t budget = h->opt.hbm_budget_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
@@ -340,6 +336,8 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.T32 = nullptr;
   d.Thi = d.Tlo = nullptr;
   d.Tffh = d.Tffl = nullptr;
+  d.op_has_kbar = false;
+  d.op_scale_exp = 12;
   d.t_f16 = prec == PX_FP16SPLIT;
   if (d.matfree) {
     if (model != PX_WFQ) throw PxError{PX_ENOTIMPL, "matrix-free mode supports PX_WFQ only in this build"};
@@ -363,7 +361,30 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
       d.Tlo = h->b_Tlo.as<uint16_t>();
     }
     CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
-    if (d.T32 || d.Thi) CU(px::launch_convert_T(d, d.T32 != nullptr, d.Thi != nullptr, s, &h->nl));
+    if (d.T32) CU(px::launch_convert_T(d, true, false, s, &h->nl));
+    if (d.Thi) {
+      // tensor-core operator M = diag(Kbar, I) T: the conductance gather leaves the
+      // Krylov step and Kbar's differences are taken in FP64.  The fp16 parts are scaled
+      // by 2^e with 2^e max|M| <= 2^14 (the shift kernel undoes the scale).
+      CU(h->b_M64.ensure(np2 * sizeof(double) + 256));
+      double* M64 = h->b_M64.as<double>();
+      unsigned long long* d_amax = reinterpret_cast<unsigned long long*>(M64 + np2);
+      CU(cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s));
+      CU(px::launch_build_M64(d, M64, d_amax, s, &h->nl));
+      unsigned long long amax_bits = 0;
+      CU(cudaMemcpyAsync(&amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      double amax = 0.0;
+      std::memcpy(&amax, &amax_bits, sizeof(amax));
+      if (!std::isfinite(amax)) throw PxError{PX_EINVAL, "non-finite operator entries"};
+      int e = 12;
+      if (amax > 0.0) e = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / amax))));
+      d.op_scale_exp = e;
+      d.op_has_kbar = true;
+      CU(px::launch_split_op(M64, np2, d.Thi, d.Tlo, d.t_f16, e, s, &h->nl));
+      CU(cudaStreamSynchronize(s));
+      h->b_M64.release();   // only the split planes stay resident
+    }
     if (prec != PX_FP64) {
       CU(h->b_Tffh.ensure(np2 * sizeof(float)));
       CU(h->b_Tffl.ensure(np2 * sizeof(float)));
@@ -505,13 +526,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   A.nu = nu;
   A.m = m;
   A.nblk = nblk;
-  // basis element: fixed by the options, or (automatic, low precision) chosen per cycle:
-  // FP32 for restarts up to kAutoF32MaxRestart vectors, double-FP32 for the longer
-  // restarts of shrunken active sets, where classical Gram-Schmidt in FP32 loses
-  // orthogonality
-  const bool basis_auto = lowp && o.basis == PX_BASIS_AUTO;
+  // basis element: FP64 for FP64 solves; FP32 (automatic) or as the options say for the
+  // low-precision ones
   A.basis = px::basis_kind(o.precision, o.basis);
-  const size_t esz_max = basis_auto ? 16 : px::basis_bytes(A.basis);
+  const size_t esz_max = px::basis_bytes(A.basis);
   void* V = grow<unsigned char>(h->b_V, (size_t)(m + 1) * nu * B * esz_max);
   void* W = grow<unsigned char>(h->b_W, (size_t)nu * B * esz_max);
   double2* hh = grow<double2>(h->b_h, 2 * (size_t)(m + 1) * B);
@@ -580,7 +598,6 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       const int mc = std::max(m, (int)std::min<long long>(px::kMaxRestart,
                                                           (long long)(m + 1) * B / Bact - 1));
       A.m = mc;
-      if (basis_auto) A.basis = mc <= kAutoF32MaxRestart ? px::kBasisF32 : px::kBasisFF;
       const size_t esz = px::basis_bytes(A.basis);
       A.y = yv;
       A.u = yv + (size_t)mc * Bact;
@@ -600,6 +617,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       sa.y_is_f32 = lowp;
       sa.jconv = jconv;
       sa.precond_mu = amu_act ? 1 : 0;
+      // the tensor-core planes hold M = diag(Kbar, I) T, fp16 parts scaled by 2^e (the
+      // epilogue undoes 2^12)
+      sa.kbar_in_y = tc && d.op_has_kbar ? 1 : 0;
+      sa.yscale = tc_f16 && d.op_has_kbar ? std::ldexp(1.0f, 12 - d.op_scale_exp) : 1.0f;
       sa.W = W;
       // one Krylov step: j >= 0 eagerly (host-side step index, per-step poll), or
       // j < 0 under capture (kernels read the step index from the device)
@@ -677,7 +698,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
             (uint64_t)(uintptr_t)d.T64, (uint64_t)(uintptr_t)d.T32, (uint64_t)(uintptr_t)d.Thi,
             (uint64_t)(uintptr_t)d.Tlo, (uint64_t)(uintptr_t)d.rowptr, (uint64_t)(uintptr_t)d.col,
             (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
-            (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d};
+            (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d,
+            (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp};
         CycleGraph* cg = nullptr;
         for (size_t k = 0; k < h->graphs.size(); ++k) {
           if (h->graphs[k].key != key) continue;

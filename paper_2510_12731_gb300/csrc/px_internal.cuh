@@ -53,6 +53,11 @@ struct DevStructure {
   double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
   bool matfree = false;
   int* perm = nullptr;         // [N] caller's index of internal (Morton-sorted) atom i
+  // tensor-core planes Thi / Tlo hold M = diag(Kbar, I) T (split-precision modes), fp16
+  // parts scaled by 2^op_scale_exp; the FP64 T, the FP32 T and the double-FP32 planes
+  // stay T
+  bool op_has_kbar = false;
+  int op_scale_exp = 12;
   uint16_t* Thi = nullptr;     // hi part of T: bf16, or fp16 of 2^12 T
   uint16_t* Tlo = nullptr;     // lo part of T: bf16, or fp16 of (2^12 T - hi) 2^11
   bool t_f16 = false;
@@ -84,10 +89,19 @@ cudaError_t launch_neigh_fill(const double* pos, int N, const int* type, int nty
 // Dense T in FP64 (Eq. 5; wFQFmu adds the 4x4 blocks of Sec. 2.2).
 cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream_t s,
                              long long* nl);
-// T32 = float(T64) when f32; Thi / Tlo split of T64 (bf16, or scaled fp16 when d.t_f16)
-// when split.
+// T32 = float(T64) when f32; Thi / Tlo split of T64 (bf16, or fp16 of 2^12 T when
+// d.t_f16) when split.
 cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaStream_t s,
                              long long* nl);
+// M = diag(Kbar, I) T in FP64 (charge rows: M_ik = sum_j K_ij (T_jk - T_ik), Eq. 2 applied
+// to T; dipole and padding rows copy T), and *absmax_bits = bits of max |M| (a
+// non-negative double, so its bit pattern orders like its value; zero it first).
+cudaError_t launch_build_M64(const DevStructure& d, double* M64,
+                             unsigned long long* absmax_bits, cudaStream_t s, long long* nl);
+// Thi / Tlo split of an FP64 operator A [np][np]: bf16 hi/lo, or (f16) fp16 hi of
+// 2^scale_exp A and fp16 lo of the remainder times 2^11.
+cudaError_t launch_split_op(const double* A, size_t n, uint16_t* hi, uint16_t* lo, bool f16,
+                            int scale_exp, cudaStream_t s, long long* nl);
 
 // Matvec Y[np][ldy] = T[np][np] X[np][ldx], columns ncols (multiple of kTile).
 cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float* Y, int ldy,
@@ -141,8 +155,7 @@ cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t
 constexpr int kBasisF64 = 0, kBasisFF = 1, kBasisF32 = 2;
 inline size_t basis_bytes(int basis) { return basis == kBasisF32 ? 8 : 16; }
 // Element type for the options' precision and px_basis choice (validated): FP64 solves
-// keep an FP64 basis; low-precision solves default to FP32 (the solve driver moves an
-// automatic basis to double-FP32 for restart cycles longer than 128 vectors).
+// keep an FP64 basis; low-precision solves default to FP32.
 inline int basis_kind(int precision, int basis) {
   if (precision == PX_FP64 || basis == PX_BASIS_FP64) return kBasisF64;
   if (basis == PX_BASIS_FF32) return kBasisFF;
@@ -182,6 +195,8 @@ struct KrylovArgs {
 //   W[i][a] = (Kbar Y)_i - z_q X[i][a]         charge rows (i < N)
 //   W[i][a] = Y_i - z_mu(type) X[i][a]         dipole rows (wFQFmu)
 // with X = V_j and Y = T X from the matvec ([np][ldy] real, re/im in columns 2a, 2a+1).
+// When the matvec applied M = diag(Kbar, I) T instead (kbar_in_y), every row is
+// W = yscale Y - z X (yscale undoes a power-of-two operator scaling).
 struct ShiftArgs {
   int nu, N, model, Bact, nblk, basis;
   const int* rowptr; const int* col; const double* val64; const float* val32;
@@ -194,6 +209,8 @@ struct ShiftArgs {
   int precond_mu;                               // 1: dipole rows use the right preconditioner
   void* W;
   const int* jdev;                              // set: X is V_0 and the step is *jdev
+  int kbar_in_y;                                // 1: Y = M X already holds Kbar T X
+  float yscale;                                 // power of two applied to Y (kbar_in_y)
 };
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl);
 

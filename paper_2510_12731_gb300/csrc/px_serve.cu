@@ -80,11 +80,10 @@ size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
     t += np * np * 8;
     if (o.precision != PX_FP64) t += np * np * 8;   // double-FP32 planes of T
     if (o.precision == PX_FP32) t += np * np * 4;
-    if (o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT) t += np * np * 4;
+    // split planes, plus the FP64 M = diag(Kbar, I) T they are cut from (transient)
+    if (o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT) t += np * np * (4 + 8);
   }
-  // automatic low-precision bases switch to 16-byte elements for long restarts
-  const size_t esz = (o.precision != PX_FP64 && o.basis == PX_BASIS_AUTO)
-                         ? 16 : px::basis_bytes(px::basis_kind(o.precision, o.basis));
+  const size_t esz = px::basis_bytes(px::basis_kind(o.precision, o.basis));
   t += (m + 1) * nu * B * esz;         // Krylov basis
   t += nu * B * esz + 2 * nu * B * 16; // W, x, r
   t += np * ldx * (8 + 8 + 4 + 4 + 4); // X64, Y64, X32, Y32, split operand

@@ -220,6 +220,19 @@ def test_fp16split_parity(model):
 
 
 @pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_fp16split_narrow_gaussians(model):
+    """The tensor-core operator M = diag(Kbar, I) T gets its fp16 scale from max |M|, so
+    narrow Gaussian widths (large T entries, R_q = R_mu = 0.4 bohr) still meet the
+    parity bar after refinement."""
+    w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=12, wmin=2.0, wmax=5.5)
+    w.types = [{**t, "Rq_bohr": 0.4, "Rmu_bohr": 0.4} for t in w.types]
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp16split", tol_rel=1e-9)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
 def test_fp16split_before_refinement_beats_bf16split(model):
     """One low-precision round (no FP64 refinement): the scaled FP16 split keeps ~22
     bits per product against the BF16 split's ~16, so its unrefined alpha is at least
