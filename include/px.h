@@ -244,9 +244,10 @@ px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
                           void* cuda_stream);
 
 /* No-allocation residual check.  The paper has no counterpart: this is a service for
- * callers that cannot allocate device memory at the point of the call (code running
- * while a stream is captured into a CUDA graph, callers whose memory pool owns all free
- * device memory, latency-bound loops that must not enter the allocator).  It computes,
+ * callers that cannot allocate device memory at the point of the call (callers whose
+ * memory pool -- a framework's caching allocator, another library's arena -- owns all
+ * free device memory, and latency-bound loops that must not enter the driver's
+ * allocator, which can synchronise the device).  It computes,
  * exactly as px_solve_device does for its own solution, the FP64 relative residual
  * ||b - A x|| / ||b|| of every (frequency, polarisation) column for a solution the
  * caller holds in device memory:

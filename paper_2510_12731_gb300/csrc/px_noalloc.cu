@@ -3,11 +3,12 @@
 // array that is part of the library image -- the call allocates no device memory.
 //
 // Who needs this: callers that cannot allocate device memory at the point of the
-// call -- code that runs while a CUDA stream is being captured into a graph (an
-// allocation there breaks or invalidates the capture), callers whose memory pool
-// owns all free device memory (a framework caching allocator, another library's
-// arena), and latency-bound loops that must never enter the driver's allocator.
-// They keep their solutions in their own buffers and only need the residual norm.
+// call -- callers whose memory pool owns all free device memory (a framework caching
+// allocator, another library's arena), and latency-bound loops that must never enter
+// the driver's allocator (an allocation can synchronise the device).  They keep their
+// solutions in their own buffers and only need the residual norm.  The first call on
+// a device looks up the scratch array's device address; make it before any stream
+// capture.
 //
 // The scratch is one file-scope device array of kNoAllocScratchBytes.  Every GPU
 // that loads the library holds it until the process exits.  Every call shares it

@@ -1,8 +1,8 @@
 """The no-allocation residual check (px_relres_device_noalloc) against px_solve_device.
 
 px_relres_device_noalloc serves callers that cannot allocate device memory where they
-call it (inside a CUDA-graph stream capture, under a memory pool that owns the free
-device memory, in loops that must not enter the allocator): it recomputes the FP64
+call it (under a memory pool that owns all free device memory, in latency-bound loops
+that must not enter the driver's allocator): it recomputes the FP64
 relative residual of a device-resident solution using only a fixed scratch array in
 the library.  Here the solution comes from px_solve_device, whose own relative
 residuals are the expected values; the check runs twice in a row to show that the
