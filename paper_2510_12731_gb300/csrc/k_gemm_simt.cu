@@ -8,6 +8,8 @@
 // the kernels need no bounds checks.
 #include "px_internal.cuh"
 
+#include <algorithm>
+
 namespace px {
 
 namespace {
@@ -89,11 +91,13 @@ k_sgemm(const float* __restrict__ T, int ldt, const float* __restrict__ X, int l
 }
 
 // FP64: BM = BN = 64, BK = 16, 256 threads, 4 x 4 outputs per thread at rows
-// {ty*2 + r, 32 + ty*2 + r} and columns {tx*2 + c, 32 + tx*2 + c}.
+// {ty*2 + r, 32 + ty*2 + r} and columns {tx*2 + c, 32 + tx*2 + c}.  Split K: block z of
+// gridDim.z sums K tiles [z nk / nz, (z+1) nk / nz) into Y + z zstride (nz = 1: all K).
 __global__ void __launch_bounds__(256)
 k_dgemm(const double* __restrict__ T, int ldt, const double* __restrict__ X, int ldx,
-        double* __restrict__ Y, int ldy, int K) {
+        double* __restrict__ Y, int ldy, int K, size_t zstride) {
   constexpr int BM = 64, BN = 64, BK = 16;
+  Y += blockIdx.z * zstride;
   __shared__ __align__(16) double As[2][BK][BM];
   __shared__ __align__(16) double Bs[2][BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -115,17 +119,19 @@ k_dgemm(const double* __restrict__ T, int ldt, const double* __restrict__ X, int
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-  const int nk = K / BK;
-  load(0, 0);
-  for (int kt = 0; kt < nk; ++kt) {
-    if (kt + 1 < nk) {
-      load((kt + 1) & 1, (kt + 1) * BK);
+  const int nk_all = K / BK;
+  const int kt0 = (int)(((long long)blockIdx.z * nk_all) / gridDim.z);
+  const int kt1 = (int)(((long long)(blockIdx.z + 1) * nk_all) / gridDim.z);
+  if (kt1 > kt0) load(0, kt0 * BK);
+  for (int kt = kt0; kt < kt1; ++kt) {
+    if (kt + 1 < kt1) {
+      load((kt + 1 - kt0) & 1, (kt + 1) * BK);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int st = kt & 1;
+    const int st = (kt - kt0) & 1;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       double2 a0 = *reinterpret_cast<const double2*>(&As[st][kk][ty * 2]);
@@ -201,8 +207,44 @@ cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float*
 cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl) {
   dim3 grd(ncols / 64, np / 64);
-  k_dgemm<<<grd, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np);
+  k_dgemm<<<grd, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, 0);
   ++*nl;
+  return cudaGetLastError();
+}
+
+namespace {
+// Y[i][c] = sum_z P[z][i][c], z in order (deterministic), c < ncols
+__global__ void k_sum_parts(const double* __restrict__ P, int nz, size_t zstride, int np,
+                            int ncols, int ldp, double* __restrict__ Y, int ldy) {
+  const size_t n = (size_t)np * ncols;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / ncols), c = (int)(t % ncols);
+    double v = 0.0;
+    for (int z = 0; z < nz; ++z) v += P[z * zstride + (size_t)i * ldp + c];
+    Y[(size_t)i * ldy + c] = v;
+  }
+}
+}  // namespace
+
+int dgemm_splits(int np, int ncols) {
+  const int tiles = (ncols / 64) * (np / 64);
+  const int nk = np / 16;
+  int nz = (2 * 152 + tiles - 1) / tiles;   // about two waves of blocks
+  return std::max(1, std::min(std::min(nz, 16), nk));
+}
+
+cudaError_t launch_dgemm_splitk(const double* T, int np, const double* X, int ldx, double* Y,
+                                int ldy, int ncols, double* part, size_t part_elems, cudaStream_t s,
+                                long long* nl) {
+  const int nz = dgemm_splits(np, ncols);
+  const size_t zstride = (size_t)np * ncols;
+  if (nz == 1 || part == nullptr || part_elems < nz * zstride)
+    return launch_dgemm(T, np, X, ldx, Y, ldy, ncols, s, nl);
+  dim3 grd(ncols / 64, np / 64, nz);
+  k_dgemm<<<grd, 256, 0, s>>>(T, np, X, ldx, part, ncols, np, zstride);
+  k_sum_parts<<<152 * 8, 256, 0, s>>>(part, nz, zstride, np, ncols, ncols, Y, ldy);
+  *nl += 2;
   return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct px_handle {
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
   DevBuf b_V, b_W, b_h, b_part, b_normpart, b_R, b_g, b_cs, b_sn, b_target, b_jconv, b_invh, b_y;
   DevBuf b_X32, b_Y32, b_X64, b_Y64, b_Xth, b_Xtl;
+  DevBuf b_dpart;  // split-K partial products of the FP64 GEMM
   int* d_err = nullptr;         // device flag: a bounded pipeline wait ran out of time
   DevBuf b_alpha, b_q, b_mu;
   int* h_active = nullptr;      // pinned host copy of d_active [kMaxRestart]
@@ -114,7 +115,7 @@ void free_all(px_handle* h) {
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
-                    &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl,
+                    &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl, &h->b_dpart,
                     &h->b_alpha, &h->b_q, &h->b_mu};
   for (DevBuf* b : bufs) b->release();
 }
@@ -560,6 +561,16 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   CU(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   double* X64 = grow<double>(h->b_X64, (size_t)np * ldx);
   double* Y64 = grow<double>(h->b_Y64, (size_t)np * ldx);
+  // split-K partial products of the FP64 GEMM (small N, FP64 solves): sized here for
+  // every operand width a cycle can have, so no allocation happens inside a cycle
+  double* dpart = nullptr;
+  size_t dpart_elems = 0;
+  if (!lowp && !d.matfree) {
+    for (size_t w = colpad; w <= (size_t)ldx; w += colpad)
+      dpart_elems = std::max(dpart_elems, (size_t)px::dgemm_splits(np, (int)w) * np * w);
+    if (dpart_elems > (size_t)np * ldx) dpart = grow<double>(h->b_dpart, dpart_elems);
+    else dpart_elems = 0;
+  }
   A.V = V; A.W = W; A.h = hh; A.part = part; A.normpart = normpart; A.R = Rm; A.g = g;
   A.cs = cs; A.sn = sn; A.target = target; A.jconv = jconv; A.inv_h = invh;
   A.y = yv; A.u = yv + (size_t)m * B;
@@ -650,7 +661,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
         } else if (2 * Bact <= 8) {
           CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, q, cnt));
         } else {
-          CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
+          CU(px::launch_dgemm_splitk(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, dpart, dpart_elems, q,
+                                     cnt));
         }
         if (o.profile && !cap) {
           CU(cudaEventRecord(e1v, q));
@@ -699,7 +711,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
             (uint64_t)(uintptr_t)d.Tlo, (uint64_t)(uintptr_t)d.rowptr, (uint64_t)(uintptr_t)d.col,
             (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
             (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d,
-            (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp};
+            (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp,
+            (uint64_t)(uintptr_t)dpart, (uint64_t)dpart_elems};
         CycleGraph* cg = nullptr;
         for (size_t k = 0; k < h->graphs.size(); ++k) {
           if (h->graphs[k].key != key) continue;
@@ -807,7 +820,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       CU(px::launch_split_ff(X64, (size_t)np * ldxa, X32, Y32, s, &nl));
       CU(px::launch_ffgemm(d.Tffh, d.Tffl, np, X32, Y32, ldxa, Y64, ldxa, ldxa, s, &nl));
     } else {
-      CU(px::launch_dgemm(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+      CU(px::launch_dgemm_splitk(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, dpart, dpart_elems, s,
+                                 &nl));
     }
     if (o.profile) {
       CU(cudaEventRecord(r1e, s));

@@ -108,6 +108,14 @@ cudaError_t launch_sgemm(const float* T, int np, const float* X, int ldx, float*
                          int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int ncols, cudaStream_t s, long long* nl);
+// The same product with K split over blocks when the output has fewer than ~2 waves
+// of tiles (small N): partial products in part [nz][np][ncols] (part_elems doubles;
+// nz = dgemm_splits(np, ncols)), summed in a fixed order into Y.  Falls back to
+// launch_dgemm when nz == 1 or part is too small.
+int dgemm_splits(int np, int ncols);
+cudaError_t launch_dgemm_splitk(const double* T, int np, const double* X, int ldx, double* Y,
+                                int ldy, int ncols, double* part, size_t part_elems, cudaStream_t s,
+                                long long* nl);
 // FP64-class matvec Y = (Th + Tl)(Xh + Xl) in double-FP32 arithmetic (FP64 result);
 // np % 64 == 0, ncols % 64 == 0.
 cudaError_t launch_ffgemm(const float* Th, const float* Tl, int np, const float* Xh,
