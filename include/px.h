@@ -181,6 +181,8 @@ typedef struct {
   int gemm_tiles_used;     /* tensor-core matvec tile shape of the first (widest) cycle:
                               1 or 2 as in px_options.gemm_tiles; 0 without that matvec */
   long long graph_launches; /* restart cycles run as one graph launch each */
+  long long graphs_built;   /* of those, cycles whose graph was captured and instantiated
+                               (the others reused a cached graph) */
 } px_stats;
 
 typedef struct px_handle px_handle;

@@ -62,7 +62,8 @@ class Stats(C.Structure):
                 ("cycles", C.c_int),
                 ("total_iters", C.c_longlong), ("n_unknowns", C.c_longlong),
                 ("used_mode", C.c_int), ("used_precision", C.c_int),
-                ("gemm_tiles_used", C.c_int), ("graph_launches", C.c_longlong)]
+                ("gemm_tiles_used", C.c_int), ("graph_launches", C.c_longlong),
+                ("graphs_built", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -487,6 +487,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   st.used_precision = o.precision;
   st.gemm_tiles_used = 0;
   st.graph_launches = 0;
+  st.graphs_built = 0;
   CU(cudaEventRecord(h->ev_a, s));
 
   // ---- inputs, shifts (Eq. 6, Eq. 8) and right-hand sides
@@ -755,6 +756,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           CU(cudaStreamEndCapture(h->cap_stream, &body));
           CU(cudaGraphInstantiate(&cg->exec, cg->graph, 0));
           cg->body_kernels = body_nl;
+          st.graphs_built++;
         }
         CU(cudaMemsetAsync(h->d_jstep, 0, sizeof(int), s));
         CU(cudaGraphLaunch(cg->exec, s));

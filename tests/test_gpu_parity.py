@@ -303,8 +303,9 @@ def test_cycle_graphs_match_eager_launches(model, precision):
 
 
 def test_cycle_graph_cache_survives_repeated_solves_and_new_structures():
-    """Repeated solves reuse the handle's instantiated graphs; a new structure drops
-    them; results stay those of fresh handles."""
+    """Repeated solves reuse the handle's instantiated graphs (a second identical solve
+    captures none); a structure of another size gets its own graphs; results stay those
+    of fresh handles."""
     from paper_2510_12731_gb300 import Solver
     w1 = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=10, wmin=2.0, wmax=5.5)
     w2 = S.small_cluster(element="Na", radius=12.0, model="wfq", nfreq=10, wmin=2.0, wmax=4.0)
@@ -313,9 +314,13 @@ def test_cycle_graph_cache_survives_repeated_solves_and_new_structures():
     with Solver(precision="fp32", tol_rel=1e-9) as s:
         for w, ref in ((w1, ref1), (w1, ref1), (w2, ref2), (w1, ref1)):
             s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
-            for _ in range(2):
+            for k in range(2):
                 out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib)
                 assert np.array_equal(out["alpha"], ref["alpha"])
+                st = s.stats()
+                assert 0 <= st["graphs_built"] <= st["graph_launches"]
+                if k == 1:
+                    assert st["graphs_built"] == 0
 
 
 # ------------------------------------------------------------------ structure staging order
