@@ -175,7 +175,7 @@ def test_not_converged_is_reported():
 @pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
 def test_bf16split_parity_after_refinement(model):
     # N = 225 (2 row tiles of 128, ragged); 50 w x 3 pols = 150 columns -> 300 real
-    # operand columns -> 2 column tiles of 256 (ragged)
+    # operand columns, padded to 384 -> 3 column tiles of 128 (ragged)
     w = S.small_cluster(element="Ag", radius=9.0, model=model, nfreq=50, wmin=2.0, wmax=5.5)
     ref, _ = _oracle(w)
     out, stats = _run(w, precision="bf16split", tol_rel=1e-9)
