@@ -195,28 +195,11 @@ __global__ void k_build_T4(const double* __restrict__ pos, const double* __restr
   }
 }
 
-__global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32, uint16_t* Thi,
-                            uint16_t* Tlo, int f16) {
-  size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; k < n; k += stride) {
-    double v = T64[k];
-    if (T32) T32[k] = (float)v;
-    if (Thi) {
-      if (f16) {
-        // fp16 split of 2^12 T: both parts stay in the normal fp16 range
-        const float vs = (float)(v * 4096.0);
-        const __half hi = __float2half_rn(vs);
-        const double rem = v * 4096.0 - (double)__half2float(hi);
-        Thi[k] = __half_as_ushort(hi);
-        Tlo[k] = __half_as_ushort(__float2half_rn((float)(rem * 2048.0)));
-      } else {
-        const __nv_bfloat16 hi = __double2bfloat16(v);
-        Thi[k] = __bfloat16_as_ushort(hi);
-        Tlo[k] = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hi)));
-      }
-    }
-  }
+// T32 = float(T64)
+__global__ void k_convert_T(const double* __restrict__ T64, size_t n, float* T32) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    T32[k] = (float)T64[k];
 }
 
 // One block per row i of M = diag(Kbar, I) T: charge rows apply the CSR of K (Eq. 2,
@@ -339,13 +322,9 @@ cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaStream_t s,
-                             long long* nl) {
-  size_t n = (size_t)d.np * d.np;
-  int threads = 256;
-  int blocks = 152 * 16;
-  k_convert_T<<<blocks, threads, 0, s>>>(d.T64, n, f32 ? d.T32 : nullptr, split ? d.Thi : nullptr,
-                                         split ? d.Tlo : nullptr, d.t_f16 ? 1 : 0);
+cudaError_t launch_convert_T(const DevStructure& d, cudaStream_t s, long long* nl) {
+  const size_t n = (size_t)d.np * d.np;
+  k_convert_T<<<152 * 16, 256, 0, s>>>(d.T64, n, d.T32);
   ++*nl;
   return cudaGetLastError();
 }

@@ -362,7 +362,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
       d.Tlo = h->b_Tlo.as<uint16_t>();
     }
     CU(px::launch_build_T64(d, h->opt.mu_self_term, s, &h->nl));
-    if (d.T32) CU(px::launch_convert_T(d, true, false, s, &h->nl));
+    if (d.T32) CU(px::launch_convert_T(d, s, &h->nl));
     if (d.Thi) {
       // tensor-core operator M = diag(Kbar, I) T: the conductance gather leaves the
       // Krylov step and Kbar's differences are taken in FP64.  The fp16 parts are scaled

@@ -58,9 +58,9 @@ struct DevStructure {
   // stay T
   bool op_has_kbar = false;
   int op_scale_exp = 12;
-  uint16_t* Thi = nullptr;     // hi part of T: bf16, or fp16 of 2^12 T
-  uint16_t* Tlo = nullptr;     // lo part of T: bf16, or fp16 of (2^12 T - hi) 2^11
-  bool t_f16 = false;
+  uint16_t* Thi = nullptr;     // hi part of M: bf16, or fp16 of 2^e M (e = op_scale_exp)
+  uint16_t* Tlo = nullptr;     // lo part of M: bf16, or fp16 of (2^e M - hi) 2^11
+  bool t_f16 = false;          // the split planes are fp16 (else bf16)
 };
 
 // ---------------------------------------------------------------- launch wrappers
@@ -89,10 +89,8 @@ cudaError_t launch_neigh_fill(const double* pos, int N, const int* type, int nty
 // Dense T in FP64 (Eq. 5; wFQFmu adds the 4x4 blocks of Sec. 2.2).
 cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream_t s,
                              long long* nl);
-// T32 = float(T64) when f32; Thi / Tlo split of T64 (bf16, or fp16 of 2^12 T when
-// d.t_f16) when split.
-cudaError_t launch_convert_T(const DevStructure& d, bool f32, bool split, cudaStream_t s,
-                             long long* nl);
+// T32 = float(T64) (the FP32 CUDA-core matvec's operator).
+cudaError_t launch_convert_T(const DevStructure& d, cudaStream_t s, long long* nl);
 // M = diag(Kbar, I) T in FP64 (charge rows: M_ik = sum_j K_ij (T_jk - T_ik), Eq. 2 applied
 // to T; dipole and padding rows copy T), and *absmax_bits = bits of max |M| (a
 // non-negative double, so its bit pattern orders like its value; zero it first).
