@@ -180,6 +180,101 @@ def test_three_atom_wfq_cramer():
     assert np.allclose(res.q[0, 0], q, rtol=1e-12, atol=1e-14 * max(abs(x) for x in q))
 
 
+def _gauss_solve_longdouble(A, b):
+    """Gaussian elimination with partial pivoting in extended precision (no LAPACK)."""
+    n = len(b)
+    M_ = [[np.clongdouble(A[i][j]) for j in range(n)] + [np.clongdouble(b[i])] for i in range(n)]
+    for c in range(n):
+        p = max(range(c, n), key=lambda r: abs(M_[r][c]))
+        M_[c], M_[p] = M_[p], M_[c]
+        for r in range(c + 1, n):
+            f = M_[r][c] / M_[c][c]
+            for k in range(c, n + 1):
+                M_[r][k] -= f * M_[c][k]
+    x = [np.clongdouble(0)] * n
+    for r in range(n - 1, -1, -1):
+        x[r] = (M_[r][n] - sum(M_[r][k] * x[k] for k in range(r + 1, n))) / M_[r][r]
+    return [complex(v) for v in x]
+
+
+def test_three_atom_wfqfmu_brute_force():
+    """Eq. 7 for three atoms in general position, assembled entry by entry: the dipole
+    kernels as 4th-order finite differences of the scalar potential erf(r/R)/r (a
+    dipole at r_j is the limit of two charges; the field is minus the gradient), the
+    12 x 12 system solved by long-double Gaussian elimination.  Pins the block layout,
+    every sign and index of Eq. 7, and the observables, against the oracle's LU."""
+    xyz = np.array([[0.0, 0.0, 0.0], [2.9, 0.3, 0.0], [1.2, 2.6, 0.4]])
+    st, el = _st(xyz, Rmu_bohr=0.9 * S.ELEMENTS["Ag"].atom_type()["Rmu_bohr"])
+    w_ev = np.array([2.8, 3.9])
+    aib = el.alpha_ib(w_ev)[None, :]
+    e = np.array([0.6, 0.0, 0.8])
+    res = M.solve(st, "wfqfmu", w_ev, [e], alpha_ib=aib)
+    N = 3
+    pos = [np.array(p) for p in st.pos]
+    Rq, Rmu = list(st.Rq), list(st.Rmu)
+    h = 2e-3
+
+    def pot(ri, rj, R):
+        r = float(np.linalg.norm(ri - rj))
+        return math.erf(r / R) / r
+
+    def d1(f, x, u):   # 4th-order directional derivative of f at x along unit u
+        return (-f(x + 2 * h * u) + 8 * f(x + h * u) - 8 * f(x - h * u) + f(x - 2 * h * u)) / (12 * h)
+
+    E3 = np.eye(3)
+    # potential at i of a unit dipole at j along b: derivative of pot with respect to r_j
+    def t_qmu(i, j, b):
+        R = math.sqrt(Rq[i] ** 2 + Rmu[j] ** 2)
+        return d1(lambda rj: pot(pos[i], rj, R), pos[j], E3[b])
+
+    # minus the field at i (component a) of a unit charge at j: gradient with respect to r_i
+    def t_muq(i, j, a):
+        R = math.sqrt(Rmu[i] ** 2 + Rq[j] ** 2)
+        return d1(lambda ri: pot(ri, pos[j], R), pos[i], E3[a])
+
+    # minus the field at i (component a) of a unit dipole at j along b
+    def t_mumu(i, j, a, b):
+        R = math.sqrt(Rmu[i] ** 2 + Rmu[j] ** 2)
+        g = lambda ri: d1(lambda rj: pot(ri, rj, R), pos[j], E3[b])   # potential of the dipole
+        return d1(g, pos[i], E3[a])   # minus the field = gradient of the potential
+
+    A_, Kb = _brute_matrix_wfq(st, 0.0)
+    n4 = 4 * N
+    T = [[0.0] * n4 for _ in range(n4)]
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                T[i][i] = math.sqrt(2.0 / math.pi) / Rq[i]
+                continue
+            T[i][j] = pot(pos[i], pos[j], math.sqrt(Rq[i] ** 2 + Rq[j] ** 2))
+            for b in range(3):
+                T[i][N + 3 * j + b] = t_qmu(i, j, b)
+            for a in range(3):
+                T[N + 3 * i + a][j] = t_muq(i, j, a)
+                for b in range(3):
+                    T[N + 3 * i + a][N + 3 * j + b] = t_mumu(i, j, a, b)
+    for f in range(w_ev.size):
+        w = w_ev[f] / M.HARTREE_EV
+        zq = -w * (w * st.tau + 1j) / (2.0 * st.n * st.tau)
+        zmu = -1.0 / aib[0, f]
+        A = [[0j] * n4 for _ in range(n4)]
+        for i in range(N):      # charge rows: Kbar applied to the charge rows of T
+            for c in range(n4):
+                A[i][c] = sum(Kb[i][k] * T[k][c] for k in range(N)) - (zq if c == i else 0.0)
+        for r in range(N, n4):  # dipole rows: T itself
+            for c in range(n4):
+                A[r][c] = T[r][c] - (zmu if c == r else 0.0)
+        V = [-(e @ p) for p in pos]
+        b = [-sum(Kb[i][k] * V[k] for k in range(N)) for i in range(N)]
+        b += [e[a] for i in range(N) for a in range(3)]
+        x = _gauss_solve_longdouble(A, b)
+        q, mu = x[:N], x[N:]
+        dip = sum(q[i] * pos[i] for i in range(N)) + sum(
+            np.array(mu[3 * i:3 * i + 3]) for i in range(N))
+        assert np.allclose(res.alpha[f, :, 0], dip, rtol=1e-7, atol=0)
+        assert np.allclose(res.q[f, 0], q, rtol=1e-7, atol=1e-9 * max(abs(v) for v in q))
+
+
 # ------------------------------------------------------------ invariants
 
 @pytest.fixture(scope="module")
