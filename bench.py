@@ -78,9 +78,14 @@ def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches, n_u=None):
                 "kernel": "k_dgemm / k_dgemv (FP64 CUDA-core block matvec)",
                 "peak_source": "GB300 dense FP64 rate, 1.25 TFLOP/s nominal",
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
-    traffic, _ = _profile_traffic("k_gemm_simt.cu", "k_sgemm_fp32.md")
-    if prec == "fp32" and mode == "matfree":
-        traffic, _ = _profile_traffic("k_gemm_mf.cu", "k_sgemm_mf_fp32.md")
+    traffic = None
+    if mode != "matfree":
+        ratio = _profile_ratio("k_gemm_simt.cu", "k_sgemm_fp32.md")
+        if ratio is not None and n_u:
+            np_ = -(-n_u // 128) * 128
+            b_avg = flops_per_launch / (4.0 * n_u * n_u)
+            # T (FP32) once, the FP32 operand and result of the 2 B real columns
+            traffic = ratio * (4.0 * np_ * np_ + 16.0 * np_ * b_avg)
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
             "kernel": "k_sgemm (FP32 CUDA-core block matvec on the materialised T)",
@@ -161,36 +166,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline traffic
-# Device code of a kernel source: the text before its first host-side launcher helper
-# (the host code below that line does not change what the kernel executes).
+# Device code of a profiled kernel: the text before the file's first host-side launcher
+# helper (tensor-core file), or the span from the file's namespace to the next kernel
+# (the FP32 GEMM shares its file with the FP64 kernels).  Code outside it does not change
+# what the profiled kernel executes.
 DEVICE_PART_END = {"k_gemm_tc.cu": b"PFN_cuTensorMapEncodeTiled_v12000 encode_fn()"}
+DEVICE_PART_SPAN = {"k_gemm_simt.cu": (b"namespace px {", b"// FP64: BM = BN = 64, BK = 16")}
 
 
 def kernel_source_sha(kernel_file):
-    """sha256 of the device part of a kernel source (the whole file where no end marker
-    is listed)."""
+    """sha256 of the device part of a kernel source (the whole file where no marker is
+    listed)."""
     src = os.path.join(ROOT, "paper_2510_12731_gb300", "csrc", kernel_file)
     data = open(src, "rb").read()
     end = DEVICE_PART_END.get(kernel_file)
     if end is not None and end in data:
         data = data[:data.index(end)]
+    span = DEVICE_PART_SPAN.get(kernel_file)
+    if span is not None and span[0] in data and span[1] in data:
+        i = data.index(span[0])
+        data = data[i:data.index(span[1], i)]
     return hashlib.sha256(data).hexdigest()
-
-
-def _profile_traffic(kernel_file, profile_file):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current device code of the kernel (the summary records its sha256)."""
-    path = os.path.join(ROOT, "profiles", profile_file)
-    src = os.path.join(ROOT, "paper_2510_12731_gb300", "csrc", kernel_file)
-    if not (os.path.exists(path) and os.path.exists(src)):
-        return None, None
-    text = open(path).read()
-    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    m_tr = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    sha = kernel_source_sha(kernel_file)
-    if not (m_sha and m_tr) or m_sha.group(1) != sha:
-        return None, sha
-    return float(m_tr.group(1)), sha
 
 
 def _profile_ratio(kernel_file, profile_file):

@@ -54,3 +54,14 @@ def test_fp64_and_fp32_rooflines_use_alu_peaks():
     assert r64["bound"] == "alu" and r64["peak"] == bench.FP64_PEAK_TFLOPS
     r32 = bench._roofline("fp32", "materialised", 1e12, 1.0, 1)
     assert r32["bound"] == "alu" and abs(r32["peak"] - 152 * 128 * 2 * 2.070e9 / 1e12) < 1e-9
+
+
+def test_fp32_gemm_profile_matches_and_models_traffic():
+    """The FP32 GEMM summary matches the current code of that kernel (the FP64 kernels
+    sharing its file are outside the hashed span); traffic = ratio x algorithmic bytes."""
+    ratio = bench._profile_ratio("k_gemm_simt.cu", "k_sgemm_fp32.md")
+    assert ratio is not None and 0.9 < ratio < 1.2
+    n_u, b = 22052, 450
+    r = bench._roofline("fp32", "materialised", 4.0 * n_u * n_u * b, 1e-2, 5, n_u=n_u)
+    np_ = 22144
+    assert abs(r["traffic"] - ratio * (4.0 * np_ * np_ + 16.0 * np_ * b)) < 1.0
