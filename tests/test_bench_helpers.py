@@ -65,3 +65,93 @@ def test_fp32_gemm_profile_matches_and_models_traffic():
     r = bench._roofline("fp32", "materialised", 4.0 * n_u * n_u * b, 1e-2, 5, n_u=n_u)
     np_ = 22144
     assert abs(r["traffic"] - ratio * (4.0 * np_ * np_ + 16.0 * np_ * b)) < 1.0
+
+
+class _FakeSolver:
+    """Stands in for paper_2510_12731_gb300.Solver: fixed statistics, every column
+    converged, no device."""
+
+    def __init__(self, **opts):
+        self.opts = opts
+        self.natoms = 0
+        self.model = 0
+
+    def set_structure(self, model, xyz, type_idx, types):
+        self.natoms = len(xyz)
+
+    def solve_device(self, omega_ev, pol_dirs, alpha_ib=None, e0=1.0, d_alpha=None, d_q=None,
+                     d_mu=None, d_relres=None, stream=None):
+        if d_relres is not None:
+            d_relres.zero_()
+        return True
+
+    def alloc_outputs(self, F, P, want_q=True, want_mu=True, empty=None):
+        import numpy as np
+        return {"alpha": np.zeros((F, 3, P), complex), "rel_residual": np.zeros((F, P)),
+                "status": np.zeros((F, P), np.int32)}
+
+    def solve(self, omega_ev, pol_dirs, alpha_ib=None, out=None):
+        return out
+
+    def stats(self):
+        return {"kernel_launches": 100, "setup_launches": 10, "matvec_ms": 5.0,
+                "matvec_launches": 10, "matvec_flops": 4.0 * 7119 ** 2 * 300 * 10,
+                "total_iters": 10, "graph_launches": 0}
+
+    def close(self):
+        pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+def test_gpu_arm_emits_the_contract_line(monkeypatch, capsys):
+    """run_ours end to end on the CPU: torch's CUDA calls and the solver replaced by
+    stand-ins; the JSON line carries every key of the bench contract."""
+    import json
+    import torch
+    import paper_2510_12731_gb300 as pkg
+
+    class _Ev:
+        t = 0.0
+
+        def __init__(self, enable_timing=True):
+            self.at = None
+
+        def record(self):
+            _Ev.t += 1.0
+            self.at = _Ev.t
+
+        def elapsed_time(self, other):
+            return 1000.0 * (other.at - self.at)
+
+    real_empty = torch.empty
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "Event", _Ev)
+    monkeypatch.setattr(torch, "device", lambda *a: "cpu")
+    monkeypatch.setattr(torch, "empty",
+                        lambda *a, **k: real_empty(*a, **{x: y for x, y in k.items()
+                                                          if x not in ("pin_memory",)}))
+    monkeypatch.setattr(pkg, "Solver", _FakeSolver)
+    monkeypatch.setattr(bench.ClockSampler, "start", lambda self: None)
+    args = bench.argparse.Namespace(
+        gpus=1, steps=2, warmup=1, impl="ours", workload="na_sphere40", precision="fp32",
+        mode=None, restart_m=0, gs_passes=1, basis="auto", graphs=False, inner_tol=None,
+        e2e_steps=1, cpu_freqs=1, no_cpu_baseline=True, p0_cols=0, serve_requests=2,
+        serve_nmax=600, serve_slots=1)
+    assert bench.run_ours(args, 0, 1, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "clocks", "e2e", "gpu_launches", "roofline", "cpu_baseline"):
+        assert k in line, k
+    assert line["points_per_step"] == 300          # 100 w x 3 pols, all converged
+    assert line["gpu_launches"] == 2 * 110
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in line["roofline"], k
+    assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert line["config"]["workload"] == "na_sphere_r40A_wfq"
