@@ -155,3 +155,18 @@ def test_gpu_arm_emits_the_contract_line(monkeypatch, capsys):
         assert k in line["roofline"], k
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert line["config"]["workload"] == "na_sphere_r40A_wfq"
+
+
+def test_reference_arm_line(capsys):
+    """The reference arm (the CPU oracle) on the 791-atom workload: one JSON line with
+    impl, cpu_baseline and an e2e entry whose value is the line's own."""
+    import json
+    args = bench.argparse.Namespace(gpus=1, steps=1, warmup=1, workload="ag_sphere",
+                                    cpu_freqs=1)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["e2e"]["value"] == line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert bench.run_reference(args, 1, 2) == 0          # other ranks exit without work
