@@ -20,7 +20,7 @@ spectral  a second exact route for wFQ (Cholesky of T + symmetric eigensolve),
           too slow.
 calibrate the effective-area calibration that the parameter presets use.
 fields    induced density, potential and field of a solved structure at probe points
-          (Sec. "Post-process Analysis" maps), for the next kernel to be checked against.
+          (the maps of Sec. "Post-process Analysis").
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against values
 fixed by the paper and by mathematics (closed forms, limits, brute force,
