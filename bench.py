@@ -93,6 +93,14 @@ def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches, n_u=None):
             "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
 
 
+# Arithmetic the path computes in, per matvec precision: the matvec's operand and
+# accumulation types, then the FP64-class (double-FP32 or FP64) true residual and
+# refinement.
+DTYPES = {"fp16split": "f16-split (3 MMA) / f32 accumulate + f32 basis + f64-class residual",
+          "bf16split": "bf16-split (3 MMA) / f32 accumulate + f32 basis + f64-class residual",
+          "fp32": "f32 + f32 basis + f64-class residual", "fp64": "f64"}
+
+
 def _workload(name):
     from paper_2510_12731_gb300 import structures as S
     table = {
@@ -456,7 +464,8 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES.get(prec, prec),
+            "data": "synthetic",
             "config": {"workload": wl.name, "natoms": N, "n_unknowns": N if wl.model == "wfq" else 4 * N,
                        "n_freq": F, "n_pol": P, "columns": F * P, "tol_rel": wl.tol,
                        "precision": prec, "mode": opts["mode"], "restart_m": args.restart_m,
@@ -521,7 +530,7 @@ def run_serving(args, rank, world, local_rank):
     cols = sum(w.ncols for w in wls)
     line = {"metric": METRIC, "value": pts1 / wall1, "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": wall1 * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPES.get(prec, prec), "data": "synthetic",
             "config": {"workload": "serving_mix", "requests": len(wls), "columns": cols,
                        "natoms_range": [min(w.natoms for w in wls), max(w.natoms for w in wls)],
                        "wfqfmu_requests": sum(w.model == "wfqfmu" for w in wls),

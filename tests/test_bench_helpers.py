@@ -155,6 +155,7 @@ def test_gpu_arm_emits_the_contract_line(monkeypatch, capsys):
         assert k in line["roofline"], k
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert line["config"]["workload"] == "na_sphere_r40A_wfq"
+    assert line["dtype"] == bench.DTYPES["fp32"]
 
 
 def test_reference_arm_line(capsys):
