@@ -21,6 +21,8 @@ spectral  a second exact route for wFQ (Cholesky of T + symmetric eigensolve),
 calibrate the effective-area calibration that the parameter presets use.
 fields    induced density, potential and field of a solved structure at probe points
           (the maps of Sec. "Post-process Analysis").
+hetero    heterogeneous wFQFmu (Eq. 9, the frequency-dependent conductance block, and the
+          per-atom interband polarisability of Eq. 10).
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against values
 fixed by the paper and by mathematics (closed forms, limits, brute force,
