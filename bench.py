@@ -258,12 +258,16 @@ def _cores():
 
 
 def run_reference(args, rank, world):
+    """The FP64 CPU checker on the host cores, on the bench's workload.  One sample is a
+    dense LU of the whole system at one frequency for every polarisation (~100 s at
+    N = 19,931 on 16 cores), so the timed samples stop once the next one would pass a
+    wall-time budget (--ref-budget-s); at least one is always timed, and the line
+    reports how many were."""
     if rank != 0:
         return 0
     wl = _workload(args.workload)
-    # one full-size sample is ~100 s of CPU work (a dense LU of the whole system), so the
-    # untimed warm-up steps run the same code on the 791-atom Ag sphere (BLAS thread pool
-    # and allocator warm-up) and the run stays within a few minutes
+    # the untimed warm-up steps run the same code on the 791-atom Ag sphere (BLAS thread
+    # pool and allocator warm-up), so they cost seconds, not minutes
     warm_wl = _workload("ag_sphere")
     for _ in range(args.warmup):
         _oracle_sample(warm_wl, 1)
@@ -273,18 +277,23 @@ def run_reference(args, rank, world):
         dt, p = _oracle_sample(wl, args.cpu_freqs)
         times.append(dt)
         pts = p
+        if sum(times) + max(times) > args.ref_budget_s:
+            break
     per = sum(times) / len(times)
     value = pts / per
     sample = (f"dense LU (numpy/LAPACK) of the full N={wl.natoms} system for {args.cpu_freqs} "
-              f"frequency x {wl.pol_dirs.shape[0]} polarisations per step")
+              f"frequency x {wl.pol_dirs.shape[0]} polarisations per step; {len(times)} of "
+              f"{args.steps} requested steps timed within a {args.ref_budget_s:.0f} s budget")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps,
+            "warmup": args.warmup,
             "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "natoms": wl.natoms, "columns": wl.ncols},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                              "sample": sample},
             "warmup_sample": "dense LU of the 791-atom Ag sphere, 1 frequency",
+            "step_s": [round(t, 2) for t in times],
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -566,6 +575,8 @@ def main():
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)
+    ap.add_argument("--ref-budget-s", dest="ref_budget_s", type=float, default=240.0,
+                    help="wall-time budget of the reference arm's timed samples")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p0-cols", dest="p0_cols", type=int, default=4)
     ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=40)

@@ -150,7 +150,12 @@ typedef struct {
  * (f, p) is one spectrum point.  Every pointer may be NULL. */
 typedef struct {
   double* alpha;         /* [F][3][P] complex: alpha_kp = d_k / E0 for field along pol p */
-  double* sigma_abs;     /* [F]: 4 pi w/(3c) sum_p Im alpha_pp; only when P == 3 */
+  double* sigma_abs;     /* [F]: 4 pi w/(3c) Tr Im alpha (orientation average); only when
+                            P == 3.  The full alpha tensor is A E^-1 (A = alpha[f] as written
+                            here, E = the 3 x 3 matrix whose columns are the field
+                            directions), so any three linearly independent directions work;
+                            linearly dependent ones (|det E| < 1e-6) with sigma_abs
+                            requested make px_solve return PX_EINVAL */
   double* sigma_abs_pol; /* [F][P]: 4 pi w / c Im(e_p . alpha e_p) */
   double* q;             /* [F][P][N] complex induced charges, caller's atom order */
   double* mu;            /* [F][P][N][3] complex induced dipoles (wFQFmu) */
@@ -259,9 +264,11 @@ px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
  * Host-side inputs are as in px_solve.  All work space comes from one fixed device
  * array of 32 MiB inside the library (held by every GPU that loads it until the
  * process exits); problems that need more return PX_EINVAL with the required size.
- * The call performs no device allocation.  Its first call on a device looks up the
- * array's address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array: calls that overlap
+ * The call performs no device allocation.  Each call made outside a stream capture
+ * looks up the array's address on the current device (cudaGetSymbolAddress); a call
+ * under a capture reuses the address of that device's last uncaptured call, so make
+ * the first call on a device before any stream capture (a captured first call returns
+ * PX_ECUDA).  Inputs are validated as in px_solve.  Every call shares the array: calls that overlap
  * on the GPU (two host threads, or two streams) race.  The call is synchronous.
  * A structure must be loaded with px_set_structure. */
 px_status px_relres_device_noalloc(px_handle* h, int n_freq, const double* omega_ev,

@@ -3,6 +3,8 @@
 // Sec. "Observables" (dipole, polarisability, absorption cross-section).
 #include "px_internal.cuh"
 
+#include <cmath>
+
 namespace px {
 
 namespace {
@@ -55,13 +57,20 @@ __global__ void k_observables(int N, int model, int F, int P, const double* __re
   }
 }
 
-// sigma[f] = (1/3) sum_p sigma_pol[f][p] = 4 pi w / (3c) Tr Im alpha for P = 3 orthonormal fields
-__global__ void k_sigma_total(int F, int P, const double* sigma_pol, double* sigma) {
+// sigma[f] = 4 pi w / (3c) Tr Im alpha_full (Sec. "Observables").  The solve measures
+// A = alpha_full E column by column (E = [e_1 e_2 e_3], one column per field direction),
+// so alpha_full = A E^-1 and Tr alpha_full = sum_kp A_kp (E^-1)_pk for any three linearly
+// independent directions; einv holds E^-1 row-major.
+struct Mat3 { double m[9]; };
+__global__ void k_sigma_total(int F, const double2* alpha, const double* omega_ev, Mat3 einv,
+                              double* sigma) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   double t = 0.0;
-  for (int p = 0; p < P; ++p) t += sigma_pol[(size_t)f * P + p];
-  sigma[f] = t / 3.0;
+  for (int k = 0; k < 3; ++k)
+    for (int p = 0; p < 3; ++p) t += alpha[((size_t)f * 3 + k) * 3 + p].y * einv.m[p * 3 + k];
+  const double w = omega_ev[f] / 27.211386245988;
+  sigma[f] = 4.0 * 3.141592653589793 * w / (3.0 * 137.035999084) * t;
 }
 
 __global__ void k_shifts(int F, int P, int ntypes, int model, const double* omega_ev,
@@ -146,15 +155,34 @@ __global__ void k_relres(const double* rnorm, const double* bnorm, int B, int P,
 cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
                                const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
-                               double* sigma_pol, double* sigma, cudaStream_t s, long long* nl) {
+                               double* sigma_pol, double* sigma, const double* pol_inv,
+                               cudaStream_t s, long long* nl) {
   k_observables<<<F * P, 256, 0, s>>>(N, model, F, P, pos, perm, x, e0, omega_ev, pol, alpha, qout,
                                       muout, sigma_pol);
   ++*nl;
-  if (sigma && sigma_pol && P == 3) {
-    k_sigma_total<<<(F + 127) / 128, 128, 0, s>>>(F, P, sigma_pol, sigma);
+  if (sigma && alpha && pol_inv && P == 3) {
+    Mat3 ei;
+    for (int k = 0; k < 9; ++k) ei.m[k] = pol_inv[k];
+    k_sigma_total<<<(F + 127) / 128, 128, 0, s>>>(F, alpha, omega_ev, ei, sigma);
     ++*nl;
   }
   return cudaGetLastError();
+}
+
+bool pol_triple_inverse(const double* pol, double* inv) {
+  // E[k][p] = pol[3 p + k]: column p is field direction p
+  auto E = [&](int k, int p) { return pol[3 * p + k]; };
+  const double det = E(0, 0) * (E(1, 1) * E(2, 2) - E(1, 2) * E(2, 1)) -
+                     E(0, 1) * (E(1, 0) * E(2, 2) - E(1, 2) * E(2, 0)) +
+                     E(0, 2) * (E(1, 0) * E(2, 1) - E(1, 1) * E(2, 0));
+  if (!(std::fabs(det) >= 1e-6)) return false;
+  // inverse = adjugate / det, row-major
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      const int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+      inv[3 * r + c] = (E(r1, c1) * E(r2, c2) - E(r1, c2) * E(r2, c1)) / det;
+    }
+  return true;
 }
 
 cudaError_t launch_shifts(int F, int P, int ntypes, int model, const double* omega_ev,

@@ -416,6 +416,8 @@ struct SolveOut {
   double* d_relres = nullptr;  // device [F][P]
   double* d_sigma_pol = nullptr;  // device [F][P]
   double* d_sigma = nullptr;      // device [F] (P == 3)
+  bool sigma_required = false;    // the caller asked for sigma_abs (P == 3 needs an
+                                  // invertible triple of field directions)
   std::vector<double> relres;  // [B]
   std::vector<int> iters;      // [B]
   std::vector<int> status;     // [B]
@@ -452,6 +454,12 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     for (size_t k = 0; k < 2 * (size_t)d.ntypes * F; ++k)
       if (!std::isfinite(alpha_ib[k])) throw PxError{PX_EINVAL, "non-finite alpha_ib"};
   if ((long long)F * P > (1LL << 24)) throw PxError{PX_EINVAL, "too many columns"};
+  // sigma_abs = 4 pi w/(3c) Tr Im alpha needs the full alpha tensor, which three linearly
+  // independent field directions determine: alpha = A E^-1
+  double pol_inv[9];
+  const bool have_triple = P == 3 && px::pol_triple_inverse(pol, pol_inv);
+  if (P == 3 && so->sigma_required && !have_triple)
+    throw PxError{PX_EINVAL, "sigma_abs needs three linearly independent field directions"};
 
   const int B = F * P;
   const int nu = d.nu, np = d.np, N = d.N, ntypes = d.ntypes;
@@ -860,7 +868,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
 
   // ---- observables (Sec. "Observables")
   CU(px::launch_observables(N, model, F, P, d.pos64, d.perm, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
-                            so->d_mu, so->d_sigma_pol, so->d_sigma, s, &nl));
+                            so->d_mu, so->d_sigma_pol, so->d_sigma, have_triple ? pol_inv : nullptr,
+                            s, &nl));
   if (so->d_relres) CU(px::launch_relres(rnorm, bnorm, B, P, so->d_relres, s, &nl));
   std::vector<double> h_rnorm(B);
   int h_err = 0;
@@ -1019,6 +1028,7 @@ px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const doubl
     so.d_relres = so.d_sigma + F;
     if (out->q) so.d_q = grow<double2>(h->b_q, B * N);
     if (out->mu && h->ds.model == PX_WFQFMU) so.d_mu = grow<double2>(h->b_mu, B * N * 3);
+    so.sigma_required = out->sigma_abs != nullptr;
     px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s);
     if (out->alpha) CU(cudaMemcpyAsync(out->alpha, so.d_alpha, sizeof(double2) * F * 3 * P, cudaMemcpyDeviceToHost, s));
     if (out->sigma_abs_pol) CU(cudaMemcpyAsync(out->sigma_abs_pol, so.d_sigma_pol, sizeof(double) * F * P, cudaMemcpyDeviceToHost, s));

@@ -296,12 +296,17 @@ cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P
 
 // ---------------------------------------------------------------- observables
 // alpha[f][k][p] = (sum_i q_i r_ik + sum_i mu_ik) / e0 (Sec. "Observables");
-// sigma_pol[f][p] = 4 pi w / c Im(e_p . alpha e_p); sigma[f] = 4 pi w/(3c) sum_p Im alpha_pp
-// (written when P == 3); q / mu copied out as [F][P][N] / [F][P][N][3].
+// sigma_pol[f][p] = 4 pi w / c Im(e_p . alpha e_p); sigma[f] = 4 pi w/(3c) Tr Im alpha_full
+// (written when P == 3 and pol_inv, the host-side row-major inverse of the 3 x 3 matrix whose
+// columns are the field directions, is given); q / mu copied out as [F][P][N] / [F][P][N][3].
 cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
                                const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
-                               double* sigma_pol, double* sigma, cudaStream_t s, long long* nl);
+                               double* sigma_pol, double* sigma, const double* pol_inv,
+                               cudaStream_t s, long long* nl);
+// Row-major inverse of E = [e_0 e_1 e_2] (columns = the three field directions pol[3][3]);
+// false when the directions are not linearly independent (|det E| < 1e-6).
+bool pol_triple_inverse(const double* pol, double* inv);
 
 int reduction_blocks(int nu);
 

@@ -8,7 +8,8 @@
 // the driver's allocator (an allocation can synchronise the device).  They keep their
 // solutions in their own buffers and only need the residual norm.  The first call on
 // a device looks up the scratch array's device address; make it before any stream
-// capture.
+// capture (under a capture the address found by the device's last call outside one is
+// used).
 //
 // The scratch is one file-scope device array of kNoAllocScratchBytes.  Every GPU
 // that loads the library holds it until the process exits.  Every call shares it
@@ -32,22 +33,31 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 
-// Device address of g_scratch, looked up once per device with that device current.
+// Device address of g_scratch on the current device.  Outside a stream capture it is
+// looked up on every call (a cheap host-side query), so a module reloaded at another
+// address (after cudaDeviceReset, say) is never served a stale pointer; under a capture
+// the address of the device's last uncaptured call is reused, because a first lookup
+// may load the module, which a capture does not allow.
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-cudaError_t scratch_for_current_device(void** out) {
+cudaError_t scratch_for_current_device(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = p;
+  } else if (!g_scratch_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -117,6 +127,21 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
   for (int f = 0; f < n_freq; ++f)
     if (!std::isfinite(omega_ev[f]) || !(omega_ev[f] > 0.0))
       return fail_h(h, PX_EINVAL, "frequencies must be finite and > 0");
+  // the same input checks as px_solve_device, before any size is derived from them
+  if ((long long)n_freq * n_pol > (1LL << 24)) return fail_h(h, PX_EINVAL, "too many columns");
+  for (int p = 0; p < n_pol; ++p) {
+    double n2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double v = pol_dir[3 * p + k];
+      if (!std::isfinite(v)) return fail_h(h, PX_EINVAL, "non-finite polarisation");
+      n2 += v * v;
+    }
+    if (std::fabs(std::sqrt(n2) - 1.0) > 1e-6)
+      return fail_h(h, PX_EINVAL, "polarisation directions must be unit vectors");
+  }
+  if (d.model == PX_WFQFMU)
+    for (size_t k = 0; k < 2 * (size_t)d.ntypes * n_freq; ++k)
+      if (!std::isfinite(alpha_ib[k])) return fail_h(h, PX_EINVAL, "non-finite alpha_ib");
   const int F = n_freq, P = n_pol, B = F * P;
   const int N = d.N, nu = d.nu, np = d.np, ntypes = d.ntypes, model = d.model;
   const int ldx = (int)px::round_up(2 * (size_t)B, px::kTile);
@@ -146,11 +171,11 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
                       " bytes of scratch; its fixed scratch array holds " +
                       std::to_string(kNoAllocScratchBytes));
 
-  void* sp = nullptr;
-  cudaError_t e = scratch_for_current_device(&sp);
-  if (e != cudaSuccess)
-    return fail_h(h, PX_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : px_stream(h);
+  void* sp = nullptr;
+  cudaError_t e = scratch_for_current_device(s, &sp);
+  if (e != cudaSuccess)
+    return fail_h(h, PX_ECUDA, std::string("scratch address lookup: ") + cudaGetErrorString(e));
   Carve cv{static_cast<unsigned char*>(sp)};
   double* d_in = cv.take<double>((size_t)F + 3 * P + 2 * (size_t)ntypes * F);
   double* d_omega = d_in;

@@ -7,6 +7,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
+import pytest  # noqa: E402
 
 
 def test_tc_profile_matches_current_device_code():
@@ -163,11 +164,32 @@ def test_reference_arm_line(capsys):
     impl, cpu_baseline and an e2e entry whose value is the line's own."""
     import json
     args = bench.argparse.Namespace(gpus=1, steps=1, warmup=1, workload="ag_sphere",
-                                    cpu_freqs=1)
+                                    cpu_freqs=1, ref_budget_s=240.0)
     assert bench.run_reference(args, 0, 1) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference"
+    assert line["steps"] == 1
     assert line["e2e"]["value"] == line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert bench.run_reference(args, 1, 2) == 0          # other ranks exit without work
+
+
+def test_reference_arm_stops_at_its_budget(capsys, monkeypatch):
+    """With samples slower than the budget allows, the arm times one step (never zero)
+    and reports how many it timed out of those requested."""
+    import json
+    calls = []
+
+    def fake_sample(wl, n_freq=1):
+        calls.append(wl.name)
+        return 50.0, 3
+
+    monkeypatch.setattr(bench, "_oracle_sample", fake_sample)
+    args = bench.argparse.Namespace(gpus=1, steps=20, warmup=5, workload="ag_sphere",
+                                    cpu_freqs=1, ref_budget_s=60.0)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["steps"] == 1 and line["steps_requested"] == 20
+    assert line["value"] == pytest.approx(3 / 50.0)
+    assert len(calls) == 5 + 1                     # warm-up samples, then one timed step

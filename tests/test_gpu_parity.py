@@ -98,6 +98,38 @@ def test_sigma_abs_three_polarisations():
     assert np.allclose(out["sigma_abs"], sig, rtol=1e-8, atol=0)
 
 
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_sigma_abs_rotated_and_skewed_triples(model):
+    """Tr Im alpha from any three linearly independent field directions (alpha = A E^-1):
+    a rotated orthonormal triple and a skewed one give the x, y, z orientation average."""
+    w = S.small_cluster(element="Ag", radius=8.0, model=model, nfreq=4, wmin=2.5, wmax=5.0)
+    ref, st = _oracle(w)
+    sig = M.sigma_abs(w.omega_ev / M.HARTREE_EV, np.einsum("fkk->f", ref.alpha).imag)
+    a, b = 0.7, -0.4
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+    skew = np.array([[1.0, 0.0, 0.0], [0.6, 0.8, 0.0], [0.0, 0.6, 0.8]])
+    for E in ((Rz @ Rx).T, skew):
+        with _solver(precision="fp64", tol_rel=1e-11) as s:
+            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+            out = s.solve(w.omega_ev, E, w.alpha_ib)
+        assert out["ok"]
+        assert np.allclose(out["sigma_abs"], sig, rtol=1e-8, atol=0)
+
+
+def test_sigma_abs_rejects_linearly_dependent_triple():
+    from paper_2510_12731_gb300 import PxError
+    w = S.small_cluster(element="Ag", radius=6.0, model="wfq", nfreq=2, wmin=3.0, wmax=4.0)
+    xxy = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    with _solver(precision="fp64") as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        with pytest.raises(PxError, match="EINVAL.*linearly independent"):
+            s.solve(w.omega_ev, xxy, w.alpha_ib)
+        # without sigma_abs the same directions are a valid request
+        d = s.solve(w.omega_ev, xxy, w.alpha_ib, out={**s.alloc_outputs(2, 3), "sigma_abs": None})
+        assert d["ok"]
+
+
 # ------------------------------------------------------------------ edge cases
 
 def _single(model, xyz, element="Ag", nfreq=3):

@@ -38,10 +38,19 @@ def test_noalloc_residual_matches_solve_device(model, precision):
         assert s.solve_device(w.omega_ev, w.pol_dirs, w.alpha_ib, d_q=d_q,
                               d_mu=d_mu if model == "wfqfmu" else None, d_relres=d_rr)
         expect = d_rr.cpu().numpy()
-        for _ in range(2):
-            got_t = torch.full((F, P), -1.0, dtype=torch.float64, device=dev)
-            s.relres_device_noalloc(w.omega_ev, w.pol_dirs, d_q, got_t, alpha_ib=w.alpha_ib,
+        outs = [torch.full((F, P), -1.0, dtype=torch.float64, device=dev) for _ in range(2)]
+        torch.cuda.synchronize()
+        for k in range(2):
+            free0 = torch.cuda.mem_get_info(dev)[0]
+            s.relres_device_noalloc(w.omega_ev, w.pol_dirs, d_q, outs[k], alpha_ib=w.alpha_ib,
                                     d_mu=d_mu if model == "wfqfmu" else None)
+            free1 = torch.cuda.mem_get_info(dev)[0]
+            # the defining property: the call takes no device memory (the first call of
+            # the process may load the library's module, so only later calls are held
+            # to it)
+            if k == 1:
+                assert free1 == free0
+        for got_t in outs:
             got = got_t.cpu().numpy()
             assert np.all(got >= 0.0)
             # both are FP64-class residual norms of the same solution (px_solve_device
@@ -66,3 +75,25 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
         s.set_structure("wfq", xyz, np.zeros(N, np.int32), [el.atom_type()])
         with pytest.raises(PxError, match="EINVAL.*scratch"):
             s.relres_device_noalloc(w_ev, np.eye(3), d_q, d_rr)
+
+
+def test_noalloc_validates_inputs_like_solve():
+    import torch
+    from paper_2510_12731_gb300 import PxError, Solver
+
+    w = _case("wfqfmu")
+    F, P, N = w.omega_ev.size, w.pol_dirs.shape[0], w.natoms
+    dev = torch.device("cuda", 0)
+    d_q = torch.zeros((F, P, N), dtype=torch.complex128, device=dev)
+    d_mu = torch.zeros((F, P, N, 3), dtype=torch.complex128, device=dev)
+    d_rr = torch.zeros((F, P), dtype=torch.float64, device=dev)
+    with Solver(precision="fp32") as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        bad_pol = w.pol_dirs.copy()
+        bad_pol[1] *= 2.0
+        with pytest.raises(PxError, match="EINVAL.*unit"):
+            s.relres_device_noalloc(w.omega_ev, bad_pol, d_q, d_rr, alpha_ib=w.alpha_ib, d_mu=d_mu)
+        bad_aib = w.alpha_ib.copy()
+        bad_aib[0, 2] = np.nan
+        with pytest.raises(PxError, match="EINVAL.*alpha_ib"):
+            s.relres_device_noalloc(w.omega_ev, w.pol_dirs, d_q, d_rr, alpha_ib=bad_aib, d_mu=d_mu)
