@@ -462,6 +462,12 @@ def run_ours(args, rank, world, local_rank):
               "sample": f"{len(fidx)} columns (w index {fidx.tolist()}, first polarisation), "
                         "each solved alone with FP64 matvec and FP64 GMRES; set-up excluded"}
 
+    shifted = None
+    nsk = args.steps if getattr(args, "shifted_steps", 0) < 0 else getattr(args, "shifted_steps", 0)
+    if nsk > 0 and wl.model == "wfq":
+        shifted = run_shifted_leg(args, wl, nsk, dev, dist, world, d_alpha, d_q, d_rr, pinned,
+                                  value)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, pts = _oracle_sample(wl, args.cpu_freqs)
@@ -487,6 +493,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches, "graph_launches_last_step": graph_launches,
             "roofline": {**roofline, "kernel_timing": kernel_timing}, "cpu_baseline": cpu,
             "p0_fp64_gpu": p0, "vs_p0": (value / world / p0["value"]) if p0 else None,
+            "shifted_krylov": shifted,
             "points_per_step": points_per_step, "iters_per_step": iters / args.steps,
             "wall_s": wall, "step_wall_ms": [round(x, 1) for x in step_wall],
         }
@@ -495,6 +502,95 @@ def run_ours(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_shifted_leg(args, wl, steps, dev, dist, world, d_alpha, d_q, d_rr, pinned, batched_value):
+    """The same workload and step (set-up + solve of every column + observables) with the
+    shifted Krylov solver: one real Arnoldi process per field direction for the whole
+    sweep (Eq. 1 with the scalar shift of Eq. 6), double-FP32 throughout.  A separate mode,
+    reported next to the batched line.  Its dominant kernel, the double-FP32 matvec on the
+    directions' columns, streams T's two FP32 planes once per step: HBM-bound."""
+    import torch
+    from paper_2510_12731_gb300 import Solver
+    F, P, N = wl.omega_ev.size, wl.pol_dirs.shape[0], wl.natoms
+    # profile = 1 events every shifted matvec (two events per Arnoldi step, ~0.1% of it)
+    sk = Solver(solver="shifted", precision="fp32", tol_rel=wl.tol, profile=1)
+
+    def step():
+        sk.set_structure(wl.model, wl.xyz_ang, wl.type_idx, wl.types)
+        return sk.solve_device(wl.omega_ev, wl.pol_dirs, wl.alpha_ib, d_alpha=d_alpha, d_q=d_q,
+                               d_relres=d_rr)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, min(args.warmup, 5))):
+        step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    conv = 0
+    mv_ms = mv_n = mv_bytes = ksteps = launches = 0.0
+    e0.record()
+    for _ in range(steps):
+        ok = step()
+        st = sk.stats()
+        mv_ms += st["shift_matvec_ms"]
+        mv_n += st["shift_matvec_launches"]
+        mv_bytes += st["shift_matvec_bytes"]
+        ksteps += st["shift_steps"]
+        launches += st["kernel_launches"] + st["setup_launches"]
+        conv += F * P if ok else int((d_rr <= wl.tol).sum().item())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    value = whole_job_value(conv / steps, world, ms / steps)
+    # end to end: host buffers through px_solve, copies inside the timed region
+    xyz_p = pinned(wl.xyz_ang.shape, np.float64)
+    xyz_p[...] = wl.xyz_ang
+    tid_p = pinned(wl.type_idx.shape, np.int32)
+    tid_p[...] = wl.type_idx
+    out = sk.alloc_outputs(F, P, want_q=True, want_mu=True, empty=lambda s, dtype: pinned(s, dtype))
+    e2e_steps = max(1, min(steps, args.e2e_steps))
+    sk.set_structure(wl.model, xyz_p, tid_p, wl.types)
+    sk.solve(wl.omega_ev, wl.pol_dirs, wl.alpha_ib, out=out)
+    barrier()
+    e0.record()
+    pts = 0
+    for _ in range(e2e_steps):
+        sk.set_structure(wl.model, xyz_p, tid_p, wl.types)
+        r = sk.solve(wl.omega_ev, wl.pol_dirs, wl.alpha_ib, out=out)
+        pts += int((r["status"] == 0).sum())
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    sk.close()
+    peaks, src = _measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    avg_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
+    achieved = (mv_bytes / mv_n) / avg_s / 1e9 if mv_n else float("nan")
+    h2d = wl.xyz_ang.nbytes + wl.type_idx.nbytes + wl.omega_ev.nbytes + wl.pol_dirs.nbytes + \
+        64 * len(wl.types)
+    d2h = sum(v.nbytes for k, v in out.items() if isinstance(v, np.ndarray)
+              and not (k == "sigma_abs" and P != 3))
+    return {
+        "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+        "points_per_step": conv / steps, "krylov_steps_per_step": ksteps / steps,
+        "gpu_launches": int(launches), "vs_batched": value / batched_value if batched_value else None,
+        "e2e": {"value": whole_job_value(pts / e2e_steps, world, e2e_ms / e2e_steps), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "k_sk_matvec (double-FP32 matvec of T's two FP32 planes on one "
+                               "column per field direction)",
+                     "peak_source": f"STREAM-style copy ({src})",
+                     "algorithmic_bytes_per_launch": mv_bytes / mv_n if mv_n else None,
+                     "avg_launch_ms": avg_s * 1e3, "launches": int(mv_n),
+                     "kernel_timing": "CUDA events around every shifted matvec over the timed region"},
+        "note": "separate mode (Eq. 1: one Krylov space per field direction serves all "
+                "frequencies); not part of the batched-vs-P0 comparison"}
 
 
 # ---------------------------------------------------------------- serving mix
@@ -570,8 +666,12 @@ def main():
     ap.add_argument("--restart-m", dest="restart_m", type=int, default=0)
     ap.add_argument("--gs-passes", dest="gs_passes", type=int, default=1)
     ap.add_argument("--basis", default="auto", choices=["auto", "fp64", "ff32", "fp32"])
-    ap.add_argument("--graphs", action="store_true",
-                    help="run restart cycles as graph launches in the timed region")
+    ap.add_argument("--graphs", action=argparse.BooleanOptionalAction, default=True,
+                    help="run restart cycles as graph launches in the timed region (default; "
+                         "--no-graphs: one launch per kernel, every matvec event-timed)")
+    ap.add_argument("--shifted-steps", dest="shifted_steps", type=int, default=-1,
+                    help="timed steps of the shifted Krylov leg (wFQ workloads; -1 = --steps, "
+                         "0 = skip)")
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=None)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
     ap.add_argument("--cpu-freqs", dest="cpu_freqs", type=int, default=1)

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define PX_ABI_VERSION 1
+#define PX_ABI_VERSION 2
 
 typedef enum {
   PX_OK = 0,
@@ -93,6 +93,21 @@ typedef enum {
   PX_MODE_MATFREE = 1,      /* generate T tiles on the fly inside the matvec ("on the fly") */
   PX_MODE_MATERIALISED = 2  /* store T once per structure ("on memory") */
 } px_mode;
+
+/* How the columns of a sweep are solved. */
+typedef enum {
+  PX_SOLVER_BATCHED = 0,  /* every (frequency, direction) column is its own restarted GMRES;
+                             all columns share one block matvec (both models) */
+  PX_SOLVER_SHIFTED = 1   /* PX_WFQ only: Eq. 1's frequency enters as the scalar shift
+                             z_q(w) I (Eq. 6) and its right-hand side does not depend on w,
+                             so one real Arnoldi process of Kbar T per field direction
+                             serves every frequency (shifted GMRES, unrestarted, in
+                             double-FP32 throughout: matvec on T held as two FP32 planes,
+                             basis, orthogonalisation).  Columns whose FP64-class true
+                             residual misses tol_rel afterwards (basis limit reached) continue
+                             in the batched refinement with the handle's precision.  Needs
+                             the materialised T */
+} px_solver;
 
 /* Per-atom-type parameters (Eqs. 3-6 and the Gaussian widths of Secs. 2.1, 2.2).
  * Pair values of r0, d and s are the arithmetic means of the two atoms' types. */
@@ -144,6 +159,11 @@ typedef struct {
   int profile;              /* 1: time every matvec launch with CUDA events; default 0 */
   size_t hbm_budget_bytes;  /* device memory the handle may use; 0 = 90% of free memory */
   double device_wait_limit_s; /* bound on any host wait for device progress; default 600 */
+  int solver;               /* px_solver; default PX_SOLVER_BATCHED */
+  int shift_krylov_max;     /* PX_SOLVER_SHIFTED: largest basis per field direction; 0 (default)
+                               = automatic, min(n_u, 2500) further limited so that the basis,
+                               the per-shift triangular factors and the products T V fit in
+                               40% of the free device memory */
 } px_options;
 
 /* Host-side results of px_solve.  F = n_freq, P = n_pol, N = n_atoms.  Column
@@ -188,6 +208,12 @@ typedef struct {
   long long graph_launches; /* restart cycles run as one graph launch each */
   long long graphs_built;   /* of those, cycles whose graph was captured and instantiated
                                (the others reused a cached graph) */
+  int solver_used;          /* px_solver of the last px_solve */
+  long long shift_steps;    /* PX_SOLVER_SHIFTED: Arnoldi steps, summed over direction groups */
+  long long shift_matvec_launches;  /* double-FP32 matvecs on <= 4 columns (one per step) */
+  double shift_matvec_ms;   /* their summed CUDA-event durations (only with options.profile) */
+  double shift_matvec_bytes;  /* their algorithmic bytes: T's two FP32 planes once, n_u^2 8 */
+  double shift_ms;          /* device time of the shifted phase, start to true residual */
 } px_stats;
 
 typedef struct px_handle px_handle;
@@ -275,6 +301,28 @@ px_status px_relres_device_noalloc(px_handle* h, int n_freq, const double* omega
                                    const double* alpha_ib, int n_pol, const double* pol_dir,
                                    double e0, const double* d_q, const double* d_mu,
                                    double* d_relres, void* cuda_stream);
+
+/* Induced density, potential and field maps (Sec. "Post-process Analysis") of solved
+ * columns at probe points, for the loaded structure.  The model's charges and dipoles
+ * are Gaussian densities (Secs. 2.1, 2.2): atom i carries q_i g(x; R_q,i) and
+ * -mu_i . grad g(x; R_mu,i), g(x; R) = (pi R^2)^(-3/2) exp(-|x|^2/R^2), x = r - r_i, whose
+ * potential is erf(|x|/R)/|x| (the kernel of Eq. 5).  For every column c and point m:
+ *   rho = sum_i q_i g(x; R_q,i) + (2/R_mu,i^2)(mu_i . x) g(x; R_mu,i)
+ *   phi = sum_i q_i G(x; R_q,i) - mu_i . grad G(x; R_mu,i),   G = erf(|x|/R)/|x|
+ *   E   = -grad phi
+ * (atomic units; points may sit on atom centres, where the limits are used).
+ *   points_ang  host [n_points][3] probe points, Angstrom
+ *   d_q         device [n_cols][N] complex charges, caller's atom order (the layout
+ *               px_solve_device writes: n_cols = F P)
+ *   d_mu        device [n_cols][N][3] complex dipoles (PX_WFQFMU), or NULL (no dipoles)
+ *   d_rho, d_phi  device [n_cols][n_points] complex outputs, d_E device
+ *               [n_cols][n_points][3] complex; each may be NULL (skipped)
+ * Pair terms are evaluated in FP32 and accumulated in FP64 (relative error ~1e-5 of the
+ * largest map value).  Synchronous; allocates the points' device copy for the call.
+ * PX_EINVAL for NULL / non-finite inputs or d_mu with a PX_WFQ structure. */
+px_status px_fields(px_handle* h, int n_points, const double* points_ang, int n_cols,
+                    const double* d_q, const double* d_mu, double* d_rho, double* d_phi,
+                    double* d_E, void* cuda_stream);
 
 /* Counters of the last px_solve / px_set_structure. */
 px_status px_get_stats(const px_handle* h, px_stats* st);

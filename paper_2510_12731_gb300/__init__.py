@@ -27,9 +27,10 @@ def options(**kw) -> L.Options:
     """A px_options record: library defaults, overridden by keyword arguments.
 
     Keywords: precision ("fp64" | "fp32" | "bf16split" | "fp16split"), mode ("auto" |
-    "matfree" | "materialised"), basis ("auto" | "fp64" | "ff32" | "fp32"), restart_m,
-    max_iter, max_cycles, max_refine, gs_passes, tol_rel, inner_tol, kcut_eps,
-    mu_self_term, profile, hbm_budget_bytes, device_wait_limit_s.
+    "matfree" | "materialised"), basis ("auto" | "fp64" | "ff32" | "fp32"), solver
+    ("batched" | "shifted"), restart_m, max_iter, max_cycles, max_refine, gs_passes,
+    gemm_tiles, cycle_graphs, sort_atoms, tol_rel, inner_tol, kcut_eps, mu_self_term,
+    profile, hbm_budget_bytes, device_wait_limit_s, shift_krylov_max.
     """
     o = L.Options()
     L.lib().px_options_default(C.byref(o))
@@ -40,6 +41,8 @@ def options(**kw) -> L.Options:
             v = L.MODES[v] if isinstance(v, str) else int(v)
         elif k == "basis":
             v = L.BASES[v] if isinstance(v, str) else int(v)
+        elif k == "solver":
+            v = L.SOLVERS[v] if isinstance(v, str) else int(v)
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
@@ -177,6 +180,18 @@ class Solver:
             self._h, w.size, L.dptr(w), L.dptr(aib) if aib is not None else None, pol.shape[0],
             L.dptr(pol), float(e0), ptr(d_q), ptr(d_mu), ptr(d_relres),
             C.c_void_p(stream) if stream else None))
+
+    def fields(self, points_ang, d_q, d_mu=None, d_rho=None, d_phi=None, d_E=None, stream=None):
+        """Induced density / potential / field maps of device-resident solved columns at
+        probe points (see px_fields in include/px.h).  d_q: (C, N) complex128 CUDA tensor
+        (C = F P, as px_solve_device writes it); d_mu: (C, N, 3) or None; outputs: (C, M)
+        complex128 for d_rho / d_phi, (C, M, 3) for d_E, each optional."""
+        pts = np.ascontiguousarray(points_ang, dtype=np.float64).reshape(-1, 3)
+        C_ = int(d_q.numel() // max(self.natoms, 1))
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._lib.px_fields(self._h, pts.shape[0], L.dptr(pts), C_, ptr(d_q), ptr(d_mu),
+                                        ptr(d_rho), ptr(d_phi), ptr(d_E),
+                                        C.c_void_p(stream) if stream else None))
 
     def stats(self) -> dict:
         s = L.Stats()

@@ -26,6 +26,8 @@ PRECISIONS = {"fp64": PX_FP64, "fp32": PX_FP32, "bf16split": PX_BF16SPLIT,
               "fp16split": PX_FP16SPLIT}
 MODES = {"auto": PX_MODE_AUTO, "matfree": PX_MODE_MATFREE, "materialised": PX_MODE_MATERIALISED}
 BASES = {"auto": PX_BASIS_AUTO, "fp64": PX_BASIS_FP64, "ff32": PX_BASIS_FF32, "fp32": PX_BASIS_FP32}
+PX_SOLVER_BATCHED, PX_SOLVER_SHIFTED = 0, 1
+SOLVERS = {"batched": PX_SOLVER_BATCHED, "shifted": PX_SOLVER_SHIFTED}
 
 
 class AtomType(C.Structure):
@@ -41,7 +43,8 @@ class Options(C.Structure):
                 ("cycle_graphs", C.c_int), ("sort_atoms", C.c_int),
                 ("tol_rel", C.c_double), ("inner_tol", C.c_double), ("kcut_eps", C.c_double),
                 ("mu_self_term", C.c_int), ("profile", C.c_int),
-                ("hbm_budget_bytes", C.c_size_t), ("device_wait_limit_s", C.c_double)]
+                ("hbm_budget_bytes", C.c_size_t), ("device_wait_limit_s", C.c_double),
+                ("solver", C.c_int), ("shift_krylov_max", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -63,7 +66,10 @@ class Stats(C.Structure):
                 ("total_iters", C.c_longlong), ("n_unknowns", C.c_longlong),
                 ("used_mode", C.c_int), ("used_precision", C.c_int),
                 ("gemm_tiles_used", C.c_int), ("graph_launches", C.c_longlong),
-                ("graphs_built", C.c_longlong)]
+                ("graphs_built", C.c_longlong), ("solver_used", C.c_int),
+                ("shift_steps", C.c_longlong), ("shift_matvec_launches", C.c_longlong),
+                ("shift_matvec_ms", C.c_double), ("shift_matvec_bytes", C.c_double),
+                ("shift_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +108,8 @@ SIGNATURES = {
     "px_relres_device_noalloc": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, C.c_int, _dp,
                                            C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p]),
+    "px_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "px_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "px_destroy": (C.c_int, [C.c_void_p]),
     "px_last_error": (C.c_char_p, [C.c_void_p]),

@@ -156,41 +156,66 @@ k_dgemm(const double* __restrict__ T, int ldt, const double* __restrict__ X, int
   }
 }
 
-// FP64 matvec for a few operand columns (NC real columns, the per-column solve): one
-// warp per row of T, lanes stride along K (coalesced 256-byte row segments), the
-// operand rows come from L1/L2, warp-shuffle reduction.
+// FP64 matvec on nc <= 8 real columns, Y = T X.  GB300's FP64 pipe (~2 FMA per clock per
+// SM) bounds it: at 2 columns it needs 2 FMAs per 8-byte element of T, about 3x the time
+// of streaming T from HBM.  So the kernel keeps every SM's FP64 pipe fed: each warp owns
+// 4 rows and reads 2 consecutive columns per lane per step (16-byte loads, 64 columns per
+// warp step) with 4 x 2 x NC independent FMA chains per lane; blocks of 2 warps (8 rows)
+// give ~16 blocks per SM at N = 20k, so the last round of blocks is a small fraction.
+// X rows are 64 bytes at most and come through L1 / L2.
 template <int NC>
-__global__ void __launch_bounds__(256) k_dgemv(const double* __restrict__ T, int ldt,
-                                               const double* __restrict__ X, int ldx,
-                                               double* __restrict__ Y, int ldy, int nrows, int K) {
+__global__ void __launch_bounds__(64) k_dgemv(const double* __restrict__ T, int ldt,
+                                              const double* __restrict__ X, int ldx,
+                                              double* __restrict__ Y, int ldy, int nrows, int K) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= nrows) return;
-  const double* Tr = T + (size_t)warp * ldt;
-  double acc[NC];
+  const int row0 = warp * 4;
+  if (row0 >= nrows) return;
+  double acc[4][NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-  for (int k = lane; k < K; k += 32) {
-    const double t = Tr[k];
-    const double* xr = X + (size_t)k * ldx;
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = fma(t, xr[c], acc[c]);
+    for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
+  for (int k = 2 * lane; k < K; k += 64) {
+    double2 t[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      t[r] = __ldcs(reinterpret_cast<const double2*>(T + (size_t)(row0 + r) * ldt + k));
+    double x0[NC], x1[NC];
+    const double* xr0 = X + (size_t)k * ldx;
+    const double* xr1 = xr0 + ldx;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      x0[c] = __ldg(xr0 + c);
+      x1[c] = __ldg(xr1 + c);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[r][c] = fma(t[r].y, x1[c], fma(t[r].x, x0[c], acc[r][c]));
   }
 #pragma unroll
-  for (int c = 0; c < NC; ++c)
-    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], o);
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) Y[(size_t)warp * ldy + c] = acc[c];
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Y[(size_t)(row0 + r) * ldy + c] = acc[r][c];
 }
 
 }  // namespace
 
 cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
                          int nc, cudaStream_t s, long long* nl) {
-  const int blocks = (int)(((long long)np * 32 + 255) / 256);
-  if (nc <= 2) k_dgemv<2><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
-  else if (nc <= 4) k_dgemv<4><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
-  else if (nc <= 8) k_dgemv<8><<<blocks, 256, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  // 8 rows per 64-thread block; np is a multiple of 128, K = np is even
+  if (np % 128 || ldx < nc) return cudaErrorInvalidValue;
+  const int blocks = np / 8;
+  if (nc <= 2) k_dgemv<2><<<blocks, 64, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  else if (nc <= 4) k_dgemv<4><<<blocks, 64, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
+  else if (nc <= 8) k_dgemv<8><<<blocks, 64, 0, s>>>(T, np, X, ldx, Y, ldy, np, np);
   else return cudaErrorInvalidValue;
   ++*nl;
   return cudaGetLastError();

@@ -85,6 +85,10 @@ struct px_handle {
   DevBuf b_dpart;  // split-K partial products of the FP64 GEMM
   int* d_err = nullptr;         // device flag: a bounded pipeline wait ran out of time
   DevBuf b_alpha, b_q, b_mu;
+  DevBuf b_sk;                  // shifted Krylov work space (carved per solve)
+  int* h_skact = nullptr;       // pinned host copy of the shifted solve's active counts
+  size_t h_skact_n = 0;
+  cudaEvent_t ev_sk[2] = {nullptr, nullptr};   // start / end of the shifted phase
   int* h_active = nullptr;      // pinned host copy of d_active [kMaxRestart]
   int* d_active = nullptr;      // device: unfrozen columns after each Krylov step
   std::vector<cudaEvent_t> ev_pool;
@@ -116,7 +120,7 @@ void free_all(px_handle* h) {
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
                     &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl, &h->b_dpart,
-                    &h->b_alpha, &h->b_q, &h->b_mu};
+                    &h->b_alpha, &h->b_q, &h->b_mu, &h->b_sk};
   for (DevBuf* b : bufs) b->release();
 }
 
@@ -139,6 +143,8 @@ px_status validate_options(const px_options* o, std::string* msg) {
   if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) { *msg = "inner_tol must be in (0, 1)"; return PX_EINVAL; }
   if (!(o->kcut_eps >= 0.0) || !(o->kcut_eps < 0.5)) { *msg = "kcut_eps must be in [0, 0.5)"; return PX_EINVAL; }
   if (!(o->device_wait_limit_s > 0.0)) { *msg = "device_wait_limit_s must be > 0"; return PX_EINVAL; }
+  if (o->solver < PX_SOLVER_BATCHED || o->solver > PX_SOLVER_SHIFTED) { *msg = "bad solver"; return PX_EINVAL; }
+  if (o->shift_krylov_max < 0) { *msg = "shift_krylov_max must be >= 0"; return PX_EINVAL; }
   return PX_OK;
 }
 
@@ -318,7 +324,8 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
   size_t np2 = (size_t)d.np * d.np;
   size_t need = np2 * sizeof(double);
-  if (prec != PX_FP64) need += 2 * np2 * sizeof(float);   // double-FP32 planes (residual)
+  const bool ff_planes = prec != PX_FP64 || (h->opt.solver == PX_SOLVER_SHIFTED && model == PX_WFQ);
+  if (ff_planes) need += 2 * np2 * sizeof(float);   // double-FP32 planes (residual, shifted)
   if (prec == PX_FP32) need += np2 * sizeof(float);
   if (split) need += 2 * np2 * sizeof(uint16_t) + np2 * sizeof(double);   // + transient FP64 M
   size_t budget = h->opt.hbm_budget_bytes;
@@ -386,7 +393,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
       CU(cudaStreamSynchronize(s));
       h->b_M64.release();   // only the split planes stay resident
     }
-    if (prec != PX_FP64) {
+    if (ff_planes) {
       CU(h->b_Tffh.ensure(np2 * sizeof(float)));
       CU(h->b_Tffl.ensure(np2 * sizeof(float)));
       d.Tffh = h->b_Tffh.as<float>();
@@ -496,6 +503,15 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   st.gemm_tiles_used = 0;
   st.graph_launches = 0;
   st.graphs_built = 0;
+  // the shifted solver applies to Eq. 1 (one scalar shift); wFQFmu solves stay batched
+  const bool shifted = o.solver == PX_SOLVER_SHIFTED && model == PX_WFQ;
+  st.solver_used = shifted ? PX_SOLVER_SHIFTED : PX_SOLVER_BATCHED;
+  st.shift_steps = st.shift_matvec_launches = 0;
+  st.shift_matvec_ms = st.shift_matvec_bytes = st.shift_ms = 0.0;
+  if (shifted && (d.matfree || d.Tffh == nullptr))
+    throw PxError{d.matfree ? PX_ENOTIMPL : PX_EINVAL,
+                  d.matfree ? "the shifted solver needs the materialised T"
+                            : "select the shifted solver before px_set_structure"};
   CU(cudaEventRecord(h->ev_a, s));
 
   // ---- inputs, shifts (Eq. 6, Eq. 8) and right-hand sides
@@ -599,11 +615,177 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     if (h_bnorm[c % P] > 0.0) h_outer[Bout++] = c;
 
   size_t prof_k = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv_events, rs_events;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv_events, rs_events, sk_events;
   int total_cycles = 0;
+  int round0 = 0;
+  if (shifted && Bout > 0) {
+    // ---- shifted Krylov phase (Eq. 1 with the scalar shift of Eq. 6): x of every column
+    // from one real Arnoldi process per field direction, then the FP64-class true
+    // residual of every column; the columns that still miss tol_rel continue in the
+    // refinement rounds below
+    CU(cudaEventRecord(h->ev_sk[0], s));
+    const int NPmax = std::min(P, 4);
+    const size_t BgMax = (size_t)F * NPmax;
+    const px::SkMatvecPlan plan = px::sk_matvec_plan(np);
+    const int nrb = px::sk_row_blocks(nu);
+    const int nnb = (nu + 255) / 256;
+    auto carve_all = [&](size_t m, unsigned char* base, std::vector<void*>* ptrs) {
+      size_t t = 0;
+      const size_t sizes[] = {
+          8 * (m + 1) * nu * NPmax,                          // V
+          8 * m * nu * NPmax,                                // U = T V
+          8 * (size_t)nu * NPmax,                            // W
+          8 * (size_t)plan.S * np * NPmax,                   // matvec partials
+          8 * (size_t)nrb * (m + 1) * NPmax,                 // projection partials
+          8 * 2 * (m + 1) * NPmax,                           // projections
+          8 * (size_t)px::sk_update_chunks((int)m) * nu * NPmax,  // update partials
+          8 * (size_t)nnb * NPmax,                           // norm partials
+          8 * m * (m + 2) * NPmax,                           // Hessenberg
+          8 * (size_t)NPmax,                                 // inv_h
+          8 * m * BgMax,                                     // cs
+          16 * m * BgMax,                                    // sn
+          16 * (m + 1) * BgMax,                              // g
+          16 * BgMax * (m * (m + 1) / 2),                    // R
+          8 * BgMax,                                         // target
+          4 * BgMax,                                         // jconv
+          4 * m,                                             // active
+          16 * m * BgMax};                                   // y
+      for (size_t b : sizes) {
+        if (ptrs) ptrs->push_back(base + t);
+        t += round_up(std::max<size_t>(b, 1), 256);
+      }
+      return t;
+    };
+    size_t m_sk = o.shift_krylov_max > 0 ? (size_t)o.shift_krylov_max : std::min<size_t>(nu, 2500);
+    m_sk = std::max<size_t>(1, std::min<size_t>(m_sk, nu));
+    if (o.shift_krylov_max == 0) {
+      size_t fr = 0, tot = 0;
+      CU(cudaMemGetInfo(&fr, &tot));
+      const size_t budget = (size_t)(0.4 * (double)fr) + h->b_sk.bytes;
+      while (m_sk > 16 && carve_all(m_sk, nullptr, nullptr) > budget) m_sk = m_sk * 7 / 8;
+    }
+    const int m = (int)m_sk;
+    CU(h->b_sk.ensure(carve_all(m_sk, nullptr, nullptr)));
+    std::vector<void*> pp;
+    carve_all(m_sk, h->b_sk.as<unsigned char>(), &pp);
+    float2* skV = static_cast<float2*>(pp[0]);
+    float2* skU = static_cast<float2*>(pp[1]);
+    float2* skW = static_cast<float2*>(pp[2]);
+    float2* skPart = static_cast<float2*>(pp[3]);
+    double* skDpart = static_cast<double*>(pp[4]);
+    double* skProj = static_cast<double*>(pp[5]);
+    float2* skUpart = static_cast<float2*>(pp[6]);
+    double* skNpart = static_cast<double*>(pp[7]);
+    double2* skY = static_cast<double2*>(pp[17]);
+    if (h->h_skact_n < m_sk) {
+      if (h->h_skact) cudaFreeHost(h->h_skact);
+      h->h_skact = nullptr;
+      h->h_skact_n = 0;
+      CU(cudaHostAlloc((void**)&h->h_skact, sizeof(int) * m_sk, cudaHostAllocDefault));
+      h->h_skact_n = m_sk;
+    }
+    for (int p0 = 0; p0 < P; p0 += 4) {
+      px::SkGroup G;
+      G.n = nu;
+      G.NP = std::min(4, P - p0);
+      G.P = P;
+      G.p0 = p0;
+      G.Bg = F * G.NP;
+      G.m = m;
+      G.H = static_cast<double*>(pp[8]);
+      G.inv_h = static_cast<double*>(pp[9]);
+      G.zq = zq_all;
+      G.cs = static_cast<double*>(pp[10]);
+      G.sn = static_cast<double2*>(pp[11]);
+      G.g = static_cast<double2*>(pp[12]);
+      G.R = static_cast<double2*>(pp[13]);
+      G.rstride = m_sk * (m_sk + 1) / 2;
+      G.target = static_cast<double*>(pp[14]);
+      G.jconv = static_cast<int*>(pp[15]);
+      G.active = static_cast<int*>(pp[16]);
+      const int NP = G.NP;
+      CU(cudaMemsetAsync(G.active, 0, sizeof(int) * m_sk, s));
+      // the least-squares estimate stops a system at half the requested relative residual
+      CU(px::launch_sk_start(G, b, bnorm, 0.5 * o.tol_rel, skV, s, &nl));
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        const float2* vj = skV + (size_t)j * nu * NP;
+        float2* Uj = skU + (size_t)j * nu * NP;
+        cudaEvent_t e0v = nullptr, e1v = nullptr;
+        if (o.profile) {
+          e0v = pool_event(h, prof_k++);
+          e1v = pool_event(h, prof_k++);
+          CU(cudaEventRecord(e0v, s));
+        }
+        CU(px::launch_sk_matvec(d.Tffh, d.Tffl, nu, np, NP, plan, vj, skPart, Uj, s, &nl));
+        if (o.profile) {
+          CU(cudaEventRecord(e1v, s));
+          sk_events.push_back({e0v, e1v});
+        }
+        CU(px::launch_sk_kbar(nu, NP, d.rowptr, d.col, d.val64, Uj, skW, s, &nl));
+        // two classical Gram-Schmidt passes (CGS2): every frequency shares this basis
+        for (int pass = 0; pass < 2; ++pass)
+          CU(px::launch_sk_gs_pass(skV, skW, nu, NP, j, m + 1, skDpart,
+                                   skProj + (size_t)pass * (m + 1) * NP, skUpart, pass == 1,
+                                   skNpart, s, &nl));
+        CU(px::launch_sk_step_end(G, j, skProj, 2, skNpart, skV, skW, s, &nl));
+        CU(cudaMemcpyAsync(h->h_skact + j, G.active + j, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecord(h->ev_iter[j & 1], s));
+        jend = j + 1;
+        // lagged poll: wait for step j-1, stop once every system of the group has stopped
+        if (j >= 1) {
+          wait_event(h, h->ev_iter[(j - 1) & 1]);
+          if (reinterpret_cast<volatile int*>(h->h_skact)[j - 1] == 0) break;
+        }
+      }
+      CU(px::launch_sk_solution(G, jend, skV, skU, skY, x, B, Y64, ldx, iters, s, &nl));
+      st.shift_steps += jend;
+      st.shift_matvec_launches += jend;
+      st.shift_matvec_bytes += 8.0 * (double)nu * nu * jend;
+      if (h->verbose)
+        std::fprintf(stderr, "px: shifted group p0=%d directions %d systems %d steps %d (basis limit %d)\n",
+                     p0, NP, G.Bg, jend, m);
+    }
+    // FP64-class true residual of every column: (T x) from the stored products T V
+    {
+      std::vector<int> all(B);
+      for (int c = 0; c < B; ++c) all[c] = c;
+      CU(cudaMemcpyAsync(act, all.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, B, zq_act, zmu_act, nullptr, s,
+                                  &nl));
+      px::ResidArgs ra{};
+      ra.nu = nu; ra.N = N; ra.model = model; ra.Bact = B; ra.P = P; ra.B = B; ra.nblk = nblk;
+      ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = d.type;
+      ra.Y = Y64; ra.ldy = ldx; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act; ra.zmu = zmu_act;
+      ra.R = r; ra.normpart = normpart;
+      CU(px::launch_resid(ra, s, &nl));
+      CU(px::launch_norm_finish(normpart, nblk, B, act, P, bnorm, inner_tol, tol_abs_frac, rnorm,
+                                beta, target_all, s, &nl));
+      CU(cudaEventRecord(h->ev_sk[1], s));
+      CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+      sync_stream(h, s);
+      float ms_sk = 0.f;
+      CU(cudaEventElapsedTime(&ms_sk, h->ev_sk[0], h->ev_sk[1]));
+      st.shift_ms = ms_sk;
+      int nb = 0;
+      double worst = 0.0;
+      for (int k = 0; k < Bout; ++k) {
+        const int c = h_outer[k];
+        if (!std::isfinite(h_col[c])) throw PxError{PX_ECUDA, "non-finite residual after the shifted solve"};
+        worst = std::max(worst, h_col[c] / h_bnorm[c % P]);
+        if (h_col[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
+      }
+      if (h->verbose)
+        std::fprintf(stderr, "px: shifted phase true residual: max rel %.3e, %d of %d columns left\n",
+                     worst, nb, Bout);
+      Bout = nb;
+      round0 = 1;
+    }
+  }
   // Refinement rounds: low-precision restarted GMRES on the current residual until every
   // column reached its inner target, then the FP64 true residual r = b - A x.
-  for (int round = 0; Bout > 0 && total_cycles < o.max_cycles && round <= o.max_refine; ++round) {
+  for (int round = round0; Bout > 0 && total_cycles < o.max_cycles && round <= o.max_refine; ++round) {
     std::copy(h_outer.begin(), h_outer.begin() + Bout, h_inner.begin());
     int Bin = Bout;
     for (int inner = 0; inner < max_inner && Bin > 0 && total_cycles < o.max_cycles; ++inner) {
@@ -891,6 +1073,11 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     CU(cudaEventElapsedTime(&t, pr.first, pr.second));
     st.resid_ms += t;
   }
+  for (auto& pr : sk_events) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, pr.first, pr.second));
+    st.shift_matvec_ms += t;
+  }
   st.kernel_launches = nl;
   if (h_err) throw PxError{PX_ETIMEOUT, "a tensor-core pipeline wait ran out of time"};
   so->relres.resize(B);
@@ -927,6 +1114,8 @@ void default_options(px_options* o) {
   o->profile = 0;
   o->hbm_budget_bytes = 0;
   o->device_wait_limit_s = 600.0;
+  o->solver = PX_SOLVER_BATCHED;
+  o->shift_krylov_max = 0;
 }
 
 }  // namespace
@@ -972,6 +1161,8 @@ px_status px_create(px_handle** out, const px_options* opt) {
     h->d_jstep = h->d_active + px::kMaxRestart;
     CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CU(cudaMalloc((void**)&h->d_err, sizeof(int)));
+    CU(cudaEventCreate(&h->ev_sk[0]));
+    CU(cudaEventCreate(&h->ev_sk[1]));
   } catch (const PxError& e) {
     g_create_error = e.msg;
     px_destroy(h);
@@ -1090,6 +1281,9 @@ px_status px_destroy(px_handle* h) {
   for (cudaEvent_t e : h->ev_iter)
     if (e) cudaEventDestroy(e);
   if (h->h_active) cudaFreeHost(h->h_active);
+  if (h->h_skact) cudaFreeHost(h->h_skact);
+  for (cudaEvent_t e : h->ev_sk)
+    if (e) cudaEventDestroy(e);
   if (h->d_active) cudaFree(h->d_active);
   if (h->d_err) cudaFree(h->d_err);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);

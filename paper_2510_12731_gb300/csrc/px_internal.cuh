@@ -310,6 +310,61 @@ bool pol_triple_inverse(const double* pol, double* inv);
 
 int reduction_blocks(int nu);
 
+// ---------------------------------------------------------------- shifted Krylov (wFQ)
+// One real Arnoldi process of A0 = Kbar T per field direction serves every frequency
+// (Eq. 1: the shift z_q(w) I is scalar, the right-hand side does not depend on w).  A
+// group holds NP <= 4 directions p0 .. p0+NP-1, i.e. the Bg = F NP systems s = f NP + pl
+// (global column c = f P + p0 + pl).  Everything in double-FP32; layouts in k_shifted.cu.
+struct SkMatvecPlan {
+  int grid = 0;      // persistent blocks (2 per SM)
+  int S = 1;         // column segments; partial products part [S][np][NP]
+  int seg_cols = 128;
+};
+SkMatvecPlan sk_matvec_plan(int np);
+struct SkGroup {
+  int n = 0, NP = 0, P = 0, p0 = 0, Bg = 0, m = 0;   // m: largest basis (Krylov steps)
+  double* H = nullptr;        // [m][m+2][NP] Hessenberg columns
+  double* inv_h = nullptr;    // [NP] scale of the next basis vector (0: invariant subspace)
+  const double2* zq = nullptr;  // [B] z_q of every global column
+  double* cs = nullptr;       // [m][Bg]
+  double2* sn = nullptr;      // [m][Bg]
+  double2* g = nullptr;       // [m+1][Bg]
+  double2* R = nullptr;       // [Bg][rstride] rotated triangular factors, packed by columns
+  size_t rstride = 0;         // m (m+1) / 2
+  double* target = nullptr;   // [Bg] absolute least-squares residual that stops a system
+  int* jconv = nullptr;       // [Bg] 0 iterating, > 0 basis size at stop, -1 zero rhs
+  int* active = nullptr;      // [m] systems still iterating after step j
+};
+// U = T v in double-FP32 (T = Th + Tl planes [np][np]; v, U [n][NP] float2), via partial
+// products over column segments (part [S][np][NP]).
+cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, int NP,
+                             const SkMatvecPlan& pl, const float2* v, float2* part, float2* U,
+                             cudaStream_t s, long long* nl);
+// W = Kbar U (Eq. 2), FP64 arithmetic.
+cudaError_t launch_sk_kbar(int n, int NP, const int* rowptr, const int* col, const double* val,
+                           const float2* U, float2* W, cudaStream_t s, long long* nl);
+int sk_row_blocks(int n);        // row blocks of the projection kernel (dpart rows)
+int sk_update_chunks(int m);     // basis-vector chunks of the update kernel (upart rows)
+// One classical Gram-Schmidt pass against V_0..V_j: h = V^T W (dpart [nrb][m1][NP] partials,
+// h [m1][NP]), W -= V h (upart [chunks][n][NP] partials); `last` adds |W|^2 partials npart
+// [(n+255)/256][NP].
+cudaError_t launch_sk_gs_pass(const float2* V, float2* W, int n, int NP, int j, int m1,
+                              double* dpart, double* h, float2* upart, bool last, double* npart,
+                              cudaStream_t s, long long* nl);
+// Hessenberg column j (from the passes' projections h [passes][m+1][NP] and npart), the
+// per-shift Givens step with its stop test, and V_{j+1} = W / h_{j+1,j}.
+cudaError_t launch_sk_step_end(const SkGroup& G, int j, const double* h, int passes,
+                               const double* npart, float2* V, const float2* W, cudaStream_t s,
+                               long long* nl);
+// V_0 = b_p / ||b_p||, g_0, targets (tol_abs_frac ||b_p||) and stop flags of the group.
+cudaError_t launch_sk_start(const SkGroup& G, const double* b, const double* bnorm,
+                            double tol_abs_frac, float2* V, cudaStream_t s, long long* nl);
+// y = R^-1 g per system (y [jend][Bg]), x[., c] = V y and (T x)[., c] = U y into the
+// residual operand layout Y [np][ldy] (columns 2c, 2c+1), iters[c] += basis size.
+cudaError_t launch_sk_solution(const SkGroup& G, int jend, const float2* V, const float2* U,
+                               double2* y, double2* x, int B, double* Y, int ldy, int* iters,
+                               cudaStream_t s, long long* nl);
+
 // Inner-iteration target of one refinement round: the requested reduction
 // inner_tol * ||r||, but never below the floor (a fraction of tol * ||b||).  Each
 // round contracts the true residual by about max(inner_tol, eps_op * kappa) with

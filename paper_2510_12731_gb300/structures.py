@@ -325,3 +325,25 @@ def build_request(desc) -> Workload:
     pols = XYZ if desc["npol"] == 3 else X_ONLY
     return _one_element(f"{desc['element']}_{desc['shape']}_{desc['model']}", el, desc["model"],
                         xyz, np.linspace(lo, hi, desc["nfreq"]), pols, tol=1e-7)
+
+
+def serving_check_mix() -> list:
+    """A fixed request mix for checking served results against the oracle: five
+    requests of 500-6,000 atoms, wFQ and wFQFmu, Ag / Au / Na, spheres and 1:1:3 rods,
+    1 or 3 field directions (the largest, an Ag rod of ~6,000 atoms, is wFQ)."""
+    out = []
+    spec = [("Na", "sphere", 30.0, "wfq", 40, XYZ),
+            ("Ag", "rod", 16.0, "wfq", 30, X_ONLY),
+            ("Au", "sphere", 15.5, "wfqfmu", 20, XYZ),
+            ("Ag", "rod", 9.0, "wfqfmu", 25, X_ONLY),
+            ("Na", "sphere", 20.0, "wfq", 60, X_ONLY)]
+    for el_name, shape, size, model, nf, pols in spec:
+        el = ELEMENTS[el_name]
+        if shape == "sphere":
+            xyz = sphere(el.lattice, el.a_ang, size)
+        else:
+            xyz = cuboid(el.lattice, el.a_ang, size, size, 3.0 * size)
+        lo, hi = (2.0, 4.0) if el_name == "Na" else (2.0, 5.0)
+        out.append(_one_element(f"{el_name}_{shape}_{len(xyz)}_{model}", el, model, xyz,
+                                np.linspace(lo, hi, nf), pols, tol=1e-7))
+    return out

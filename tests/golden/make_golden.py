@@ -5,7 +5,8 @@ Calls only the CPU oracle (``oracle/``) on the seeded inputs of
 files.  Routes:
   * wFQ workloads: the exact spectral route (Cholesky of T, symmetric eigensolve) gives
     every (frequency, polarisation) column;
-  * the wFQFmu rod: one dense LU per sampled frequency (lowest, middle, highest).
+  * the wFQFmu rod: one dense LU per sampled frequency (lowest, middle, highest);
+  * the fixed serving check mix: each request by the route of its model.
 Run:  python tests/golden/make_golden.py [name ...]   (a few minutes to ~30 min each).
 """
 import os
@@ -56,11 +57,23 @@ def lu_sample(name, w, n_samples=3):
     _write(name, w, idx, res.alpha, f"dense LU at frequency indices {idx.tolist()}")
 
 
+def serving_check():
+    """Every request of the fixed serving check mix: the spectral route for wFQ, LU at
+    three frequencies for wFQFmu."""
+    for i, w in enumerate(S.serving_check_mix()):
+        name = f"serving{i}"
+        if w.model == "wfq":
+            spectral_workload(name, w)
+        else:
+            lu_sample(name, w)
+
+
 JOBS = {
     "graphene_disk_20nm": lambda: spectral_workload("graphene_disk_20nm", S.graphene_disk_20nm()),
     "na_icosahedron_19931": lambda: spectral_workload("na_icosahedron_19931",
                                                       S.na_icosahedron_19931()),
     "ag_rod_3x3x10": lambda: lu_sample("ag_rod_3x3x10", S.ag_rod_3x3x10()),
+    "serving_check": serving_check,
 }
 
 if __name__ == "__main__":

@@ -63,11 +63,12 @@ def test_struct_layouts_match_the_header(tmp_path, libpath):
 
 def test_defaults_and_version_without_gpu(libpath):
     lib = L.load(libpath)
-    assert lib.px_abi_version() == 1
+    assert lib.px_abi_version() == 2
     o = L.Options()
     assert lib.px_options_default(C.byref(o)) == L.PX_OK
     assert o.restart_m == 0 and o.gs_passes == 1 and o.tol_rel == 1e-7
     assert o.basis == L.PX_BASIS_AUTO and o.gemm_tiles == 0 and o.cycle_graphs == 1
+    assert o.solver == L.PX_SOLVER_BATCHED and o.shift_krylov_max == 0
     assert lib.px_options_default(None) == L.PX_EINVAL
     assert lib.px_destroy(None) == L.PX_OK
 
@@ -97,6 +98,14 @@ def test_create_rejects_bad_options(libpath):
     o.cycle_graphs = 2
     assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
     assert b"cycle_graphs" in lib.px_last_error(None)
+    lib.px_options_default(C.byref(o))
+    o.solver = 2
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    assert b"solver" in lib.px_last_error(None)
+    lib.px_options_default(C.byref(o))
+    o.shift_krylov_max = -1
+    assert lib.px_create(C.byref(h), C.byref(o)) == L.PX_EINVAL
+    assert b"shift_krylov_max" in lib.px_last_error(None)
 
 
 def test_calls_on_null_handle_fail_cleanly(libpath):

@@ -56,8 +56,37 @@ def test_graphene_disk_20nm_all_300_columns():
     _check(_solve(w), fidx, ref, w.tol)
 
 
-def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies():
+@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
+def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies(precision):
+    """The rod as configured (FP32 matvec; all 150 frequencies x 3 directions solved),
+    and with the tensor-core FP16-split matvec, against oracle LU at three frequencies."""
     w = S.ag_rod_3x3x10()
-    w.precision = "fp16split"
+    w.precision = precision
     fidx, ref = _golden("ag_rod_3x3x10", w.omega_ev.size, 3)
     _check(_solve(w), fidx, ref, w.tol)
+
+
+# ---- the shifted Krylov solver (one real Arnoldi process per field direction serves the
+# whole sweep, Eq. 1 with the scalar shift of Eq. 6) on the same workloads and goldens
+
+def test_na_icosahedron_19931_shifted_all_600_columns():
+    from paper_2510_12731_gb300 import Solver
+    w = S.na_icosahedron_19931()
+    fidx, ref = _golden("na_icosahedron_19931", w.omega_ev.size, 3)
+    with Solver(precision="fp32", tol_rel=w.tol, solver="shifted") as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib, want_q=False)
+        st = s.stats()
+    _check(out, fidx, ref, w.tol)
+    assert st["solver_used"] == 1 and st["shift_steps"] > 0
+    assert st["cycles"] == 0          # no column needed the batched refinement
+
+
+def test_graphene_disk_20nm_shifted_all_300_columns():
+    from paper_2510_12731_gb300 import Solver
+    w = S.graphene_disk_20nm()
+    fidx, ref = _golden("graphene_disk_20nm", w.omega_ev.size, 1)
+    with Solver(precision="fp32", tol_rel=w.tol, solver="shifted") as s:
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        out = s.solve(w.omega_ev, w.pol_dirs, w.alpha_ib, want_q=False)
+    _check(out, fidx, ref, w.tol)

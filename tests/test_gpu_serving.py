@@ -1,6 +1,9 @@
 """Continuous-batching server: every request's result in a concurrent mix equals the
-same request solved alone, within the solver tolerance; admission respects the budget;
-repeated structures reuse the device-resident operators."""
+same request solved alone, within the solver tolerance, and equals the oracle's (a fixed
+mix of 500-5,300-atom wFQ and wFQFmu requests against the values in tests/golden/);
+admission respects the budget; repeated structures reuse the device-resident operators."""
+import os
+
 import numpy as np
 import pytest
 
@@ -102,3 +105,37 @@ def test_poll_and_unknown_ids():
         assert out is not None and out["ok"]
         with pytest.raises(KeyError):
             srv.poll(rid)
+
+
+def _golden(i, P):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"serving{i}_alpha.txt")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    rows = np.loadtxt(path)
+    fidx = np.unique(rows[:, 0].astype(int))
+    a = np.zeros((len(fidx), 3, P), dtype=np.complex128)
+    pos = {f: k for k, f in enumerate(fidx)}
+    for fi, _, p, k, re, im in rows:
+        a[pos[int(fi)], int(k), int(p)] = re + 1j * im
+    return fidx, a
+
+
+@pytest.mark.parametrize("precision", ["fp16split", "fp32"])
+def test_served_results_match_the_oracle(precision):
+    """Five requests (wFQ and wFQFmu, 893-5,287 atoms) submitted together to three slots;
+    every served alpha within 1e-5 of the oracle (spectral route for wFQ, dense LU at three
+    frequencies for wFQFmu), every column at its FP64-class tolerance."""
+    from paper_2510_12731_gb300 import Server
+    mix = S.serving_check_mix()
+    with Server(max_slots=3, precision=precision, tol_rel=1e-7) as srv:
+        ids = [srv.submit(w.model, w.xyz_ang, w.type_idx, w.types, w.omega_ev, w.pol_dirs,
+                          w.alpha_ib) for w in mix]
+        outs = [srv.wait(i, timeout_s=1800) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(mix) and st["failed"] == 0
+    assert max(w.natoms for w in mix) > 5000
+    for i, (w, o) in enumerate(zip(mix, outs)):
+        assert o["ok"] and np.all(o["rel_residual"] <= 1e-7), w.name
+        fidx, ref = _golden(i, w.pol_dirs.shape[0])
+        err = np.linalg.norm(o["alpha"][fidx] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert np.max(err) <= 1e-5, (w.name, np.max(err))
