@@ -60,7 +60,17 @@ typedef enum {
   PX_ENOTFOUND = 8   /* unknown request id */
 } px_status;
 
-typedef enum { PX_WFQ = 0, PX_WFQFMU = 1 } px_model;
+typedef enum {
+  PX_WFQ = 0,           /* Eq. 1: charges only, N unknowns */
+  PX_WFQFMU = 1,        /* Eq. 7: charges and dipoles, 4N unknowns; one n, tau for all types */
+  PX_WFQFMU_HETERO = 2  /* Eq. 9 with Eq. 10 (alloys, core-shell): atom types may differ in
+                           drude_n_au and tau_au; z_q is the charge's own type's (Eq. 6), the
+                           conductance block is 1/2 (Kbar + Hbar(w)) with
+                           H_ij = (n_j tau_j)/(n_i tau_i) (1 - i w tau_i)/(1 - i w tau_j) K_ji, and
+                           each atom's alpha^IB is Eq. 10's weighted harmonic mean over the
+                           atom and its nearest neighbours (atoms within the pair's Fermi
+                           midpoint s r0).  PX_FP32 or PX_FP64 matvecs, materialised T */
+} px_model;
 
 /* Arithmetic of the block matvec Y = T X inside the Krylov iteration.  The
  * Hessenberg least squares, the true residual and the refinement are FP64 (or
@@ -236,13 +246,15 @@ px_status px_set_options(px_handle* h, const px_options* opt);
  * Angstrom) and build its device-resident operators: the CSR of K (Eq. 3) with
  * the diagonal of Kbar (Eq. 2), and T (Eq. 5, Sec. 2.2) in the storage the
  * options select.
- *   model     PX_WFQ (n_u = N unknowns) or PX_WFQFMU (n_u = 4N).
+ *   model     PX_WFQ (n_u = N unknowns), PX_WFQFMU or PX_WFQFMU_HETERO (n_u = 4N).
  *   xyz_ang   [n_atoms][3] doubles, Angstrom.
  *   type_idx  [n_atoms] ints in [0, n_types).
- *   types     [n_types] parameter records (all share drude_n_au and tau_au).
+ *   types     [n_types] parameter records (all share drude_n_au and tau_au except
+ *             under PX_WFQFMU_HETERO).
  * Errors: PX_EINVAL (NULL, n_atoms < 1, bad type index, non-finite or
  * non-positive parameter, two atoms closer than 1e-6 Angstrom), PX_ENOMEM,
- * PX_ECUDA.  Synchronous: returns after the device work finished. */
+ * PX_ENOTIMPL (PX_WFQFMU_HETERO with a split precision), PX_ECUDA.  Synchronous:
+ * returns after the device work finished. */
 px_status px_set_structure(px_handle* h, px_model model, int n_atoms, const double* xyz_ang,
                            const int* type_idx, const px_atom_type* types, int n_types);
 
@@ -250,7 +262,8 @@ px_status px_set_structure(px_handle* h, px_model model, int n_atoms, const doub
  * write the observables (Sec. "Observables") to host buffers.
  *   n_freq, omega_ev  [n_freq] frequencies in eV, > 0.
  *   alpha_ib          [n_types][n_freq] complex interband polarisabilities
- *                     alpha^IB(w), a.u. (Eq. 8); required for PX_WFQFMU,
+ *                     alpha^IB(w), a.u. (Eq. 8); required for PX_WFQFMU and
+ *                     PX_WFQFMU_HETERO (per type: Eq. 10 forms each atom's value),
  *                     ignored (may be NULL) for PX_WFQ.
  *   n_pol, pol_dir    [n_pol][3] unit field directions.
  *   e0                field amplitude E0, a.u. (> 0; the response is linear).
@@ -296,7 +309,8 @@ px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
  * the first call on a device before any stream capture (a captured first call returns
  * PX_ECUDA).  Inputs are validated as in px_solve.  Every call shares the array: calls that overlap
  * on the GPU (two host threads, or two streams) race.  The call is synchronous.
- * A structure must be loaded with px_set_structure. */
+ * A structure must be loaded with px_set_structure (PX_WFQ or PX_WFQFMU; a
+ * PX_WFQFMU_HETERO structure returns PX_ENOTIMPL). */
 px_status px_relres_device_noalloc(px_handle* h, int n_freq, const double* omega_ev,
                                    const double* alpha_ib, int n_pol, const double* pol_dir,
                                    double e0, const double* d_q, const double* d_mu,

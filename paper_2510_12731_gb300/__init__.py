@@ -110,7 +110,7 @@ class Solver:
                "sigma_abs_pol": empty((F, P), dtype=np.float64),
                "q": empty((F, P, N), dtype=np.complex128) if want_q else None,
                "mu": (empty((F, P, N, 3), dtype=np.complex128)
-                      if (want_mu and self.model == L.PX_WFQFMU) else None),
+                      if (want_mu and self.model != L.PX_WFQ) else None),
                "rel_residual": empty((F, P), dtype=np.float64),
                "iters": empty((F, P), dtype=np.int32),
                "status": empty((F, P), dtype=np.int32)}
@@ -262,7 +262,7 @@ class Server:
         m, N, F, P = self._meta[rid]
         out = {"alpha": np.zeros((F, 3, P), np.complex128), "sigma_abs": np.zeros(F),
                "sigma_abs_pol": np.zeros((F, P)), "q": np.zeros((F, P, N), np.complex128),
-               "mu": np.zeros((F, P, N, 3), np.complex128) if m == L.PX_WFQFMU else None,
+               "mu": np.zeros((F, P, N, 3), np.complex128) if m != L.PX_WFQ else None,
                "rel_residual": np.zeros((F, P)), "iters": np.zeros((F, P), np.int32),
                "status": np.zeros((F, P), np.int32)}
         cptr = lambda a: a.view(np.float64).ctypes.data_as(L._dp) if a is not None else None

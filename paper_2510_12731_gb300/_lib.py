@@ -16,12 +16,12 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpx.so")
 PX_OK, PX_EINVAL, PX_ENOMEM, PX_ENOTCONV, PX_ETIMEOUT, PX_ECUDA, PX_EBUSY, PX_ENOTIMPL, PX_ENOTFOUND = range(9)
 STATUS_NAMES = ["PX_OK", "PX_EINVAL", "PX_ENOMEM", "PX_ENOTCONV", "PX_ETIMEOUT", "PX_ECUDA",
                 "PX_EBUSY", "PX_ENOTIMPL", "PX_ENOTFOUND"]
-PX_WFQ, PX_WFQFMU = 0, 1
+PX_WFQ, PX_WFQFMU, PX_WFQFMU_HETERO = 0, 1, 2
 PX_FP64, PX_FP32, PX_BF16SPLIT, PX_FP16SPLIT = 0, 1, 2, 3
 PX_MODE_AUTO, PX_MODE_MATFREE, PX_MODE_MATERIALISED = 0, 1, 2
 PX_BASIS_AUTO, PX_BASIS_FP64, PX_BASIS_FF32, PX_BASIS_FP32 = 0, 1, 2, 3
 
-MODELS = {"wfq": PX_WFQ, "wfqfmu": PX_WFQFMU}
+MODELS = {"wfq": PX_WFQ, "wfqfmu": PX_WFQFMU, "wfqfmu_hetero": PX_WFQFMU_HETERO}
 PRECISIONS = {"fp64": PX_FP64, "fp32": PX_FP32, "bf16split": PX_BF16SPLIT,
               "fp16split": PX_FP16SPLIT}
 MODES = {"auto": PX_MODE_AUTO, "matfree": PX_MODE_MATFREE, "materialised": PX_MODE_MATERIALISED}

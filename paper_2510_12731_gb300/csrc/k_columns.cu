@@ -150,7 +150,118 @@ __global__ void k_relres(const double* rnorm, const double* bnorm, int B, int P,
   out[c] = bn > 0.0 ? rnorm[c] / bn : 0.0;
 }
 
+// ---- heterogeneous wFQFmu (Eqs. 9-10)
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// zq[t][c], kappa[t][u][c]: one thread per column
+__global__ void k_hetero_cols(int F, int P, int ntypes, const double* omega_ev,
+                              const double* tpar, double2* zq, double2* kappa) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = F * P;
+  if (c >= B) return;
+  const double w = omega_ev[c / P] / 27.211386245988;
+  for (int t = 0; t < ntypes; ++t) {
+    const double nt = tpar[3 * t], taut = tpar[3 * t + 1], At = tpar[3 * t + 2];
+    const double den = 2.0 * nt * taut;
+    zq[(size_t)t * B + c] = make_double2(-w * w * taut / den, -w / den);   // Eq. 6
+    for (int u = 0; u < ntypes; ++u) {
+      const double nu_ = tpar[3 * u], tauu = tpar[3 * u + 1], Au = tpar[3 * u + 2];
+      // rho_tu = (n_u tau_u)/(n_t tau_t) (1 - i w tau_t)/(1 - i w tau_u)
+      const double2 r = cdiv(make_double2(1.0, -w * taut), make_double2(1.0, -w * tauu));
+      const double f = (nu_ * tauu) / (nt * taut) * Au / At;
+      kappa[((size_t)t * ntypes + u) * B + c] = make_double2(0.5 * (1.0 + f * r.x), 0.5 * f * r.y);
+    }
+  }
+}
+
+// zmu_atom[i][c] = sum_t wt_it zmu[t][c] / sum_t wt_it, wt_it = nn[i][t] + [t == type_i]
+// (Eq. 10: the inverse interband polarisability is the weighted mean of the types')
+__global__ void k_hetero_zmu(int N, int B, int ntypes, const int* type, const int* nn,
+                             const double2* zmu, double2* zmu_atom) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * B) return;
+  const int i = (int)(idx / B), c = (int)(idx % B);
+  double sw = 0.0, zr = 0.0, zi = 0.0;
+  for (int t = 0; t < ntypes; ++t) {
+    const double wt = (double)nn[(size_t)i * ntypes + t] + (type[i] == t ? 1.0 : 0.0);
+    const double2 z = zmu[(size_t)t * B + c];
+    sw += wt;
+    zr += wt * z.x;
+    zi += wt * z.y;
+  }
+  zmu_atom[idx] = make_double2(zr / sw, zi / sw);
+}
+
+__global__ void k_gather_rows(const double2* in, int rows, int B, const int* act, int Bact,
+                              double2* out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)rows * Bact) return;
+  const int t = (int)(idx / Bact), a = (int)(idx % Bact);
+  out[idx] = in[(size_t)t * B + act[a]];
+}
+
+__global__ void k_bnorm_cols(const double* bnorm, int P, int B, double* bn) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < B) bn[c] = bnorm[c % P];
+}
+
+__global__ void k_init_residual_c(const double2* bc, int nu, int B, const double* bn,
+                                  double inner_tol, double tol_abs_frac, double2* r,
+                                  double* rnorm, double* beta, double* target_all) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)nu * B) return;
+  const int i = (int)(idx / B), c = (int)(idx % B);
+  r[idx] = bc[idx];
+  if (i == 0) {
+    const double b = bn[c];
+    rnorm[c] = b;
+    beta[c] = b;
+    target_all[c] = round_target(inner_tol * b, tol_abs_frac * b);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_hetero_tables(int F, int P, int ntypes, int N, const double* omega_ev,
+                                 const double* tpar, const int* type, const int* nn,
+                                 const double2* zmu_type, double2* zq, double2* kappa,
+                                 double2* zmu_atom, cudaStream_t s, long long* nl) {
+  const int B = F * P;
+  k_hetero_cols<<<(B + 127) / 128, 128, 0, s>>>(F, P, ntypes, omega_ev, tpar, zq, kappa);
+  const size_t n = (size_t)N * B;
+  k_hetero_zmu<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, B, ntypes, type, nn, zmu_type, zmu_atom);
+  *nl += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const double2* in, int rows, int B, const int* act, int Bact,
+                               double2* out, cudaStream_t s, long long* nl) {
+  const size_t n = (size_t)rows * Bact;
+  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, rows, B, act, Bact, out);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bnorm_cols(const double* bnorm, int P, int B, double* bn, cudaStream_t s,
+                              long long* nl) {
+  k_bnorm_cols<<<(B + 127) / 128, 128, 0, s>>>(bnorm, P, B, bn);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_residual_c(const double2* bc, int nu, int B, const double* bn,
+                                   double inner_tol, double tol_abs_frac, double2* r,
+                                   double* rnorm, double* beta, double* target_all, cudaStream_t s,
+                                   long long* nl) {
+  const size_t n = (size_t)nu * B;
+  k_init_residual_c<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(bc, nu, B, bn, inner_tol, tol_abs_frac,
+                                                                r, rnorm, beta, target_all);
+  ++*nl;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_observables(int N, int model, int F, int P, const double* pos,
                                const int* perm, const double2* x, double e0, const double* omega_ev,

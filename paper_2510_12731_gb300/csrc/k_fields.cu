@@ -20,6 +20,7 @@
 #include "px.h"
 #include "px_internal.cuh"
 #include "px_handle.cuh"
+#include "px_radial.cuh"
 
 #include <cmath>
 #include <string>
@@ -31,33 +32,9 @@ constexpr int kFTile = 128;   // atoms per shared-memory tile
 constexpr int kFCols = 2;     // columns per block (grid y covers the rest)
 constexpr float kInvSqrtPi = 0.56418958354775628f;
 
-// G = erf(x)/r, G1 = G'(r) / r, G2 = G''(r) for r = x R; also the normalised Gaussian g.
 __device__ __forceinline__ void radial(float r, float R, float& G, float& G1r, float& G2,
                                        float& g) {
-  const float iR = 1.0f / R;
-  const float x = r * iR;
-  const float x2 = x * x;
-  const float ex = __expf(-x2);
-  const float c = 2.0f * kInvSqrtPi * iR;          // 2 / (sqrt(pi) R)
-  g = kInvSqrtPi * kInvSqrtPi * kInvSqrtPi * iR * iR * iR * ex;
-  if (x < 0.25f) {
-    // G = c (1 - x^2/3 + x^4/10 - x^6/42); G'/r = (c/R^2)(-2/3 + 2x^2/5 - x^4/7 + x^6/27);
-    // G'' = (c/R^2)(-2/3 + 6x^2/5 - 5x^4/7 + 7x^6/27)
-    const float x4 = x2 * x2, x6 = x4 * x2;
-    G = c * (1.0f - x2 * (1.0f / 3.0f) + x4 * 0.1f - x6 * (1.0f / 42.0f));
-    const float cr = c * iR * iR;
-    G1r = cr * (-2.0f / 3.0f + 0.4f * x2 - x4 * (1.0f / 7.0f) + x6 * (1.0f / 27.0f));
-    G2 = cr * (-2.0f / 3.0f + 1.2f * x2 - x4 * (5.0f / 7.0f) + x6 * (7.0f / 27.0f));
-  } else {
-    const float e = erff(x);
-    const float ir = 1.0f / r;
-    const float gx = 2.0f * kInvSqrtPi * ex;         // d erf / dx
-    G = e * ir;
-    const float G1 = (gx * iR - e * ir) * ir;        // G'(r)
-    G1r = G1 * ir;
-    // G'' = -2 x gx / (R^2 r) - 2 gx / (R r^2) + 2 erf / r^3
-    G2 = (-2.0f * x * gx * iR * iR - 2.0f * gx * iR * ir + 2.0f * e * ir * ir) * ir;
-  }
+  px::radial::eval_f(r, R, G, G1r, G2, g);
 }
 
 struct FieldArgs {

@@ -8,6 +8,7 @@
 // tile is written to shared memory one stage ahead of the FMA loop.  Rows / columns
 // beyond the n real atoms generate 0.
 #include "px_internal.cuh"
+#include "px_radial.cuh"
 
 namespace px {
 
@@ -202,7 +203,335 @@ k_dgemm_mf(const double* __restrict__ pos /* [n][4]: x y z Rq^2 */, int n,
   }
 }
 
+// ---------------------------------------------------------------- wFQFmu on the fly
+// The 4 x 4 block of the wFQFmu kernel (Sec. 2.2) of atoms a != b, unknowns (q, mu_x, mu_y,
+// mu_z) of each: blk[0][0] = T^qq, blk[0][1+l] = T^qmu_l = -T'(r; R_q,a mu,b) rhat_l,
+// blk[1+k][0] = T^muq_k = +T'(r; R_mu,a q,b) rhat_k,
+// blk[1+k][1+l] = T^mumu_kl = -[T'' rhat_k rhat_l + (T'/r)(delta_kl - rhat_k rhat_l)],
+// rhat = (r_a - r_b)/r, pair widths sqrt(R_a^2 + R_b^2) of the two densities involved.
+// With T' rhat = (T'/r) (r_a - r_b), only G'/r and G'' enter.  Equal charge and dipole
+// widths (the usual case) need one radial evaluation instead of four.
+__device__ __forceinline__ void pair_block_f(float4 pa, float rma2, float4 pb, float rmb2,
+                                             float blk[4][4]) {
+  const float d[3] = {pa.x - pb.x, pa.y - pb.y, pa.z - pb.z};
+  const float r2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+  const float r = sqrtf(r2), ir = 1.0f / r;
+  float Gqq, t1, t2, g;
+  float G1qm, G1mq, G1mm, G2mm;
+  radial::eval_f(r, sqrtf(pa.w + pb.w), Gqq, t1, t2, g);
+  if (pa.w == rma2 && pb.w == rmb2) {
+    G1qm = G1mq = G1mm = t1;
+    G2mm = t2;
+  } else {
+    float u0, u2;
+    radial::eval_f(r, sqrtf(pa.w + rmb2), u0, G1qm, u2, g);
+    radial::eval_f(r, sqrtf(rma2 + pb.w), u0, G1mq, u2, g);
+    radial::eval_f(r, sqrtf(rma2 + rmb2), u0, G1mm, G2mm, g);
+  }
+  blk[0][0] = Gqq;
+  const float rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+#pragma unroll
+  for (int l = 0; l < 3; ++l) blk[0][1 + l] = -G1qm * d[l];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    blk[1 + k][0] = G1mq * d[k];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const float rr = rh[k] * rh[l];
+      blk[1 + k][1 + l] = -(G2mm * rr + G1mm * ((k == l ? 1.0f : 0.0f) - rr));
+    }
+  }
+}
+
+// Diagonal 4 x 4 block of atom a: T^qq self limit, zero charge-dipole coupling, T^mumu = 0 or
+// the Gaussian self term 4/(3 sqrt(pi) R^3) I with R = sqrt(2) R_mu (mu_self_term).
+__device__ __forceinline__ void self_block_f(float rq2, float rm2, int mu_self, float blk[4][4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) blk[k][l] = 0.f;
+  blk[0][0] = kSqrt2OverPiF * rsqrtf(rq2);
+  if (mu_self) {
+    const float R2 = 2.0f * rm2;   // R = sqrt(2) R_mu
+    const float v = 4.0f / (3.0f * 1.7724538509055159f) * rsqrtf(R2) / R2;
+    blk[1][1] = blk[2][2] = blk[3][3] = v;
+  }
+}
+
+// Standard (charges first) row of unknown u of a tile whose atoms start at a0 and whose
+// first `na` unknowns are those atoms' charges, the next 3 na their dipole components.
+__device__ __forceinline__ int std_row(int N, int a0, int na, int u, int* atom) {
+  if (u < na) {
+    *atom = a0 + u;
+    return a0 + u;
+  }
+  *atom = a0 + (u - na) / 3;
+  return N + 3 * a0 + (u - na);
+}
+
+// Y = T X for wFQFmu with T generated tile by tile: 128 x 128 output tiles (32 atoms x 4
+// unknowns, charges-first order inside the tile), K steps of 4 atoms (16 unknowns).  The
+// 128 (row atom, K atom) pairs of a step are generated by threads 0..127, one 4 x 4 block
+// each, one stage ahead of the FMA loop; unknowns of atoms beyond N generate / load 0 and
+// are not stored.
+__global__ void __launch_bounds__(256, 2)
+k_sgemm_mf4(const float4* __restrict__ pos, const float* __restrict__ rm2, int N, int mu_self,
+            const float* __restrict__ X, int ldx, float* __restrict__ Y, int ldy) {
+  constexpr int BM = 128, BN = 128, BK = 16, AT = 32, KA = 4;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  __shared__ float4 Pa[AT];
+  __shared__ float Ra[AT];
+  __shared__ float4 Pb[2][KA];
+  __shared__ float Rb[2][KA];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int a0 = blockIdx.y * AT, c0 = blockIdx.x * BN;
+  if (tid < AT) {
+    const int a = a0 + tid;
+    Pa[tid] = a < N ? pos[a] : make_float4(0.f, 0.f, 0.f, 1.f);
+    Ra[tid] = a < N ? rm2[a] : 1.f;
+  }
+  auto load_x = [&](int st, int kb) {
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int idx = tid + rr * 256;
+      const int kk = idx >> 5, cc = (idx & 31) * 4;
+      int b;
+      const int row = std_row(N, kb * KA, KA, kk, &b);
+      if (b < N) cp_async16(&Bs[st][kk][cc], X + (size_t)row * ldx + c0 + cc);
+      else *reinterpret_cast<float4*>(&Bs[st][kk][cc]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cp_async_commit();
+  };
+  auto load_pb = [&](int st, int kb) {
+    if (tid < KA) {
+      const int b = kb * KA + tid;
+      Pb[st][tid] = b < N ? pos[b] : make_float4(0.f, 0.f, 0.f, 1.f);
+      Rb[st][tid] = b < N ? rm2[b] : 1.f;
+    }
+  };
+  auto gen = [&](int st, int kb) {
+    if (tid < AT * KA) {
+      const int al = tid & (AT - 1), bl = tid >> 5;
+      const int a = a0 + al, b = kb * KA + bl;
+      float blk[4][4];
+      if (a >= N || b >= N) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) blk[k][l] = 0.f;
+      } else if (a == b) {
+        self_block_f(Pa[al].w, Ra[al], mu_self, blk);
+      } else {
+        pair_block_f(Pa[al], Ra[al], Pb[st][bl], Rb[st][bl], blk);
+      }
+      // As[st][K unknown][row unknown]
+      As[st][bl][al] = blk[0][0];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) As[st][KA + 3 * bl + l][al] = blk[0][1 + l];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        As[st][bl][AT + 3 * al + k] = blk[1 + k][0];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) As[st][KA + 3 * bl + l][AT + 3 * al + k] = blk[1 + k][1 + l];
+      }
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  const int nk = (N + KA - 1) / KA;
+  load_pb(0, 0);
+  load_x(0, 0);
+  __syncthreads();
+  gen(0, 0);
+  if (nk > 1) load_pb(1, 1);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1, nx = st ^ 1;
+    if (kt + 1 < nk) {
+      load_x(nx, kt + 1);
+      gen(nx, kt + 1);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0v = *reinterpret_cast<const float4*>(&As[st][kk][ty * 4]);
+      const float4 a1v = *reinterpret_cast<const float4*>(&As[st][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[st][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[st][kk][64 + tx * 4]);
+      const float a[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (kt + 2 < nk) load_pb(st, kt + 2);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int u = r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+    int a;
+    const int row = std_row(N, a0, AT, u, &a);
+    if (a >= N) continue;
+    float* yr = Y + (size_t)row * ldy + c0;
+    *reinterpret_cast<float4*>(yr + tx * 4) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    *reinterpret_cast<float4*>(yr + 64 + tx * 4) =
+        make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+  }
+}
+
+// FP64 counterpart (the true residual of matrix-free wFQFmu solves): 64 x 64 output tiles
+// (16 atoms), K steps of 4 atoms; the blocks in FP64 closed form, as the materialised FP64
+// kernel evaluates them.
+struct RadialD { double t1r, t2; };   // T'/r, T''
+__device__ __forceinline__ RadialD radial_d(double r, double R) {
+  const double x = r / R;
+  const double e = erf(x);
+  const double g = 1.1283791670955126 * exp(-x * x);
+  const double ir = 1.0 / r;
+  RadialD o;
+  o.t1r = (g * x - e) * ir * ir * ir;
+  o.t2 = (2.0 * e - 2.0 * g * x - 2.0 * g * x * x * x) * ir * ir * ir;
+  return o;
+}
+
+__device__ void pair_block_d(const double* pa, double rma2, const double* pb, double rmb2,
+                             double blk[4][4]) {
+  const double d[3] = {pa[0] - pb[0], pa[1] - pb[1], pa[2] - pb[2]};
+  const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  blk[0][0] = erf(r / sqrt(pa[3] + pb[3])) / r;
+  const RadialD qm = radial_d(r, sqrt(pa[3] + rmb2));
+  const RadialD mq = radial_d(r, sqrt(rma2 + pb[3]));
+  const RadialD mm = radial_d(r, sqrt(rma2 + rmb2));
+  const double rh[3] = {d[0] / r, d[1] / r, d[2] / r};
+  for (int l = 0; l < 3; ++l) blk[0][1 + l] = -qm.t1r * d[l];
+  for (int k = 0; k < 3; ++k) {
+    blk[1 + k][0] = mq.t1r * d[k];
+    for (int l = 0; l < 3; ++l) {
+      const double rr = rh[k] * rh[l];
+      blk[1 + k][1 + l] = -(mm.t2 * rr + mm.t1r * ((k == l ? 1.0 : 0.0) - rr));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_dgemm_mf4(const double* __restrict__ pos /* [N][4] x y z Rq^2 */, const double* __restrict__ rm2,
+            int N, int mu_self, const double* __restrict__ X, int ldx, double* __restrict__ Y,
+            int ldy) {
+  constexpr int BM = 64, BN = 64, BK = 16, AT = 16, KA = 4;
+  __shared__ __align__(16) double As[BK][BM];
+  __shared__ __align__(16) double Bs[BK][BN];
+  __shared__ double Pa[AT][5];
+  __shared__ double Pb[KA][5];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int a0 = blockIdx.y * AT, c0 = blockIdx.x * BN;
+  if (tid < AT) {
+    const int a = a0 + tid;
+    for (int q = 0; q < 4; ++q) Pa[tid][q] = a < N ? pos[4 * (size_t)a + q] : 1.0;
+    Pa[tid][4] = a < N ? rm2[a] : 1.0;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  const int nk = (N + KA - 1) / KA;
+  for (int kt = 0; kt < nk; ++kt) {
+    if (tid < KA) {
+      const int b = kt * KA + tid;
+      for (int q = 0; q < 4; ++q) Pb[tid][q] = b < N ? pos[4 * (size_t)b + q] : 1.0;
+      Pb[tid][4] = b < N ? rm2[b] : 1.0;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int idx = tid + rr * 256;
+      const int kk = idx >> 5, cc = (idx & 31) * 2;
+      int b;
+      const int row = std_row(N, kt * KA, KA, kk, &b);
+      if (b < N) cp_async16(&Bs[kk][cc], X + (size_t)row * ldx + c0 + cc);
+      else *reinterpret_cast<double2*>(&Bs[kk][cc]) = make_double2(0.0, 0.0);
+    }
+    cp_async_commit();
+    __syncthreads();
+    if (tid < AT * KA) {
+      const int al = tid & (AT - 1), bl = tid >> 4;
+      const int a = a0 + al, b = kt * KA + bl;
+      double blk[4][4];
+      for (int k = 0; k < 4; ++k)
+        for (int l = 0; l < 4; ++l) blk[k][l] = 0.0;
+      if (a < N && b < N) {
+        if (a == b) {
+          blk[0][0] = kSqrt2OverPiD / sqrt(Pa[al][3]);
+          if (mu_self) {
+            const double R = 1.4142135623730951 * sqrt(Pa[al][4]);
+            blk[1][1] = blk[2][2] = blk[3][3] = 4.0 / (3.0 * 1.7724538509055159 * R * R * R);
+          }
+        } else {
+          pair_block_d(Pa[al], Pa[al][4], Pb[bl], Pb[bl][4], blk);
+        }
+      }
+      As[bl][al] = blk[0][0];
+      for (int l = 0; l < 3; ++l) As[KA + 3 * bl + l][al] = blk[0][1 + l];
+      for (int k = 0; k < 3; ++k) {
+        As[bl][AT + 3 * al + k] = blk[1 + k][0];
+        for (int l = 0; l < 3; ++l) As[KA + 3 * bl + l][AT + 3 * al + k] = blk[1 + k][1 + l];
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a0v = *reinterpret_cast<const double2*>(&As[kk][ty * 2]);
+      const double2 a1v = *reinterpret_cast<const double2*>(&As[kk][32 + ty * 2]);
+      const double2 b0 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 2]);
+      const double2 b1 = *reinterpret_cast<const double2*>(&Bs[kk][32 + tx * 2]);
+      const double a[4] = {a0v.x, a0v.y, a1v.x, a1v.y};
+      const double b[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int u = r < 2 ? ty * 2 + r : 32 + ty * 2 + (r - 2);
+    int a;
+    const int row = std_row(N, a0, AT, u, &a);
+    if (a >= N) continue;
+    double* yr = Y + (size_t)row * ldy + c0;
+    *reinterpret_cast<double2*>(yr + tx * 2) = make_double2(acc[r][0], acc[r][1]);
+    *reinterpret_cast<double2*>(yr + 32 + tx * 2) = make_double2(acc[r][2], acc[r][3]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sgemm_mf4(const float4* pos, const float* rm2, int N, int mu_self,
+                             const float* X, int ldx, float* Y, int ldy, int ncols, cudaStream_t s,
+                             long long* nl) {
+  if (ncols % 128) return cudaErrorInvalidValue;
+  k_sgemm_mf4<<<dim3(ncols / 128, (N + 31) / 32), 256, 0, s>>>(pos, rm2, N, mu_self, X, ldx, Y, ldy);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dgemm_mf4(const double* pos4, const double* rm2, int N, int mu_self,
+                             const double* X, int ldx, double* Y, int ldy, int ncols,
+                             cudaStream_t s, long long* nl) {
+  if (ncols % 64) return cudaErrorInvalidValue;
+  k_dgemm_mf4<<<dim3(ncols / 64, (N + 15) / 16), 256, 0, s>>>(pos4, rm2, N, mu_self, X, ldx, Y, ldy);
+  ++*nl;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, int ldx, float* Y,
                             int ldy, int ncols, cudaStream_t s, long long* nl) {

@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
     const size_t off = (size_t)i * a.Bact + col;
     const E xv = X[off];
     double yr, yi;
-    auto zz = zq;
+    // heterogeneous wFQFmu: z_q of the charge's own type (Eq. 9)
+    auto zz = (a.qtype && i < a.N) ? TT::coef(a.zq[(size_t)a.qtype[i] * a.Bact + col]) : zq;
     if (i < a.N && a.kbar_in_y) {
       // the matvec applied M = diag(Kbar, I) T: no conductance gather
       if (F32Y) {
@@ -255,11 +256,26 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
         const float* Y = static_cast<const float*>(a.Y);
         const float y0r = Y[(size_t)i * a.ldy + 2 * col], y0i = Y[(size_t)i * a.ldy + 2 * col + 1];
         float sr = 0.f, si = 0.f;
-        for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
-          const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
-          const float k = a.val32[e];
-          sr = fmaf(k, Y[jo] - y0r, sr);
-          si = fmaf(k, Y[jo + 1] - y0i, si);
+        if (a.kappa) {
+          // complex bond weights K_ij kappa[t_i][t_j] of 1/2 (Kbar + Hbar(w)) (Eq. 9)
+          const double2* kr = a.kappa + (size_t)a.qtype[i] * a.ntypes * a.Bact + col;
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const int j = a.col[e];
+            const size_t jo = (size_t)j * a.ldy + 2 * col;
+            const double2 kp = kr[(size_t)a.qtype[j] * a.Bact];
+            const float k = a.val32[e];
+            const float wr = k * (float)kp.x, wi = k * (float)kp.y;
+            const float dr = Y[jo] - y0r, di = Y[jo + 1] - y0i;
+            sr = fmaf(wr, dr, fmaf(-wi, di, sr));
+            si = fmaf(wr, di, fmaf(wi, dr, si));
+          }
+        } else {
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
+            const float k = a.val32[e];
+            sr = fmaf(k, Y[jo] - y0r, sr);
+            si = fmaf(k, Y[jo + 1] - y0i, si);
+          }
         }
         yr = sr;
         yi = si;
@@ -267,11 +283,25 @@ __global__ void __launch_bounds__(256) k_shift(ShiftArgs a) {
         const double* Y = static_cast<const double*>(a.Y);
         const double y0r = Y[(size_t)i * a.ldy + 2 * col], y0i = Y[(size_t)i * a.ldy + 2 * col + 1];
         double sr = 0.0, si = 0.0;
-        for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
-          const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
-          const double k = a.val64[e];
-          sr = fma(k, Y[jo] - y0r, sr);
-          si = fma(k, Y[jo + 1] - y0i, si);
+        if (a.kappa) {
+          const double2* kr = a.kappa + (size_t)a.qtype[i] * a.ntypes * a.Bact + col;
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const int j = a.col[e];
+            const size_t jo = (size_t)j * a.ldy + 2 * col;
+            const double2 kp = kr[(size_t)a.qtype[j] * a.Bact];
+            const double k = a.val64[e];
+            const double wr = k * kp.x, wi = k * kp.y;
+            const double dr = Y[jo] - y0r, di = Y[jo + 1] - y0i;
+            sr = fma(wr, dr, fma(-wi, di, sr));
+            si = fma(wr, di, fma(wi, dr, si));
+          }
+        } else {
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
+            const double k = a.val64[e];
+            sr = fma(k, Y[jo] - y0r, sr);
+            si = fma(k, Y[jo + 1] - y0i, si);
+          }
         }
         yr = sr;
         yi = si;
@@ -305,19 +335,34 @@ __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
   double nrm = 0.0;
   if (valid) {
     const int gc = a.act[col];
-    const double2 zq = a.zq[col];
     for (int i = blockIdx.y * 8 + ty; i < a.nu; i += 8 * gridDim.y) {
       const double2 xv = a.x[(size_t)i * a.B + gc];
       const double y0r = a.Y[(size_t)i * a.ldy + 2 * col], y0i = a.Y[(size_t)i * a.ldy + 2 * col + 1];
       double2 w;
       if (i < a.N) {
         double sr = 0.0, si = 0.0;
-        for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
-          const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
-          const double k = a.val64[e];
-          sr = fma(k, a.Y[jo] - y0r, sr);
-          si = fma(k, a.Y[jo + 1] - y0i, si);
+        if (a.kappa) {
+          // 1/2 (Kbar + Hbar(w)) with complex bond weights (Eq. 9)
+          const double2* kr = a.kappa + (size_t)a.qtype[i] * a.ntypes * a.Bact + col;
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const int j = a.col[e];
+            const size_t jo = (size_t)j * a.ldy + 2 * col;
+            const double2 kp = kr[(size_t)a.qtype[j] * a.Bact];
+            const double k = a.val64[e];
+            const double wr = k * kp.x, wi = k * kp.y;
+            const double dr = a.Y[jo] - y0r, di = a.Y[jo + 1] - y0i;
+            sr = fma(wr, dr, fma(-wi, di, sr));
+            si = fma(wr, di, fma(wi, dr, si));
+          }
+        } else {
+          for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+            const size_t jo = (size_t)a.col[e] * a.ldy + 2 * col;
+            const double k = a.val64[e];
+            sr = fma(k, a.Y[jo] - y0r, sr);
+            si = fma(k, a.Y[jo + 1] - y0i, si);
+          }
         }
+        const double2 zq = a.qtype ? a.zq[(size_t)a.qtype[i] * a.Bact + col] : a.zq[col];
         const double2 zx = cmul(zq, xv);
         w = make_double2(sr - zx.x, si - zx.y);
       } else {
@@ -325,8 +370,9 @@ __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
         const double2 zx = cmul(a.zmu[(size_t)a.type[atom] * a.Bact + col], xv);
         w = make_double2(y0r - zx.x, y0i - zx.y);
       }
-      const double bv = a.b[(size_t)i * a.P + (gc % a.P)];
-      const double2 r = make_double2(bv - w.x, -w.y);
+      const double2 bv = a.bc ? a.bc[(size_t)i * a.B + gc]
+                              : make_double2(a.b[(size_t)i * a.P + (gc % a.P)], 0.0);
+      const double2 r = make_double2(bv.x - w.x, bv.y - w.y);
       a.R[(size_t)i * a.B + gc] = r;
       nrm += r.x * r.x + r.y * r.y;
     }
@@ -364,6 +410,59 @@ __global__ void k_rhs(int nu, int N, const int* __restrict__ rowptr, const int* 
     v = e0 * e[(i - N) % 3];
   }
   b[(size_t)i * P + p] = v;
+}
+
+// Right-hand side of Eq. 9 per column: charge rows (C(w) (-V))_i = E0 sum_j w_ij(w) e.(r_j -
+// r_i) with the bond weights w_ij = K_ij kappa[t_i][t_j][c] of C = 1/2 (Kbar + Hbar(w));
+// dipole rows E0 e.  bn[c] (written by the first thread of each column's block row) is
+// computed by k_col_norms_c.
+__global__ void k_rhs_hetero(int N, int F, int P, const int* __restrict__ rowptr,
+                             const int* __restrict__ col, const double* __restrict__ val,
+                             const int* __restrict__ type, int ntypes,
+                             const double2* __restrict__ kappa, const double* __restrict__ pos,
+                             const double* __restrict__ pol, double e0, double2* bc) {
+  const int B = F * P;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nu = 4 * N;
+  if (idx >= (size_t)nu * B) return;
+  const int i = (int)(idx / B), c = (int)(idx % B);
+  const double* e = pol + 3 * (c % P);
+  double2 v = make_double2(0.0, 0.0);
+  if (i < N) {
+    const double ei = e[0] * pos[3 * i] + e[1] * pos[3 * i + 1] + e[2] * pos[3 * i + 2];
+    const int ti = type[i];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int j = col[k];
+      const double ej = e[0] * pos[3 * j] + e[1] * pos[3 * j + 1] + e[2] * pos[3 * j + 2];
+      const double2 kap = kappa[((size_t)ti * ntypes + type[j]) * B + c];
+      const double d = val[k] * (ej - ei);
+      v.x = fma(d, kap.x, v.x);
+      v.y = fma(d, kap.y, v.y);
+    }
+    v.x *= e0;
+    v.y *= e0;
+  } else {
+    v.x = e0 * e[(i - N) % 3];
+  }
+  bc[idx] = v;
+}
+
+// bn[c] = || bc[., c] ||_2, one block per column
+__global__ void k_col_norms_c(const double2* bc, int nu, int B, double* bn) {
+  const int c = blockIdx.x;
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+    const double2 v = bc[(size_t)i * B + c];
+    t += v.x * v.x + v.y * v.y;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bn[c] = sqrt(sh[0]);
 }
 
 // ------------------------------------------------------------ Gram-Schmidt
@@ -830,6 +929,19 @@ cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* c
   int n = nu * P;
   k_rhs<<<(n + 255) / 256, 256, 0, s>>>(nu, N, rowptr, col, val64, pos, pol, P, e0, b);
   ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_hetero(int N, int F, int P, const int* rowptr, const int* col,
+                              const double* val64, const int* type, int ntypes,
+                              const double2* kappa, const double* pos, const double* pol,
+                              double e0, double2* bc, double* bn, cudaStream_t s, long long* nl) {
+  const int B = F * P;
+  const size_t n = (size_t)4 * N * B;
+  k_rhs_hetero<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(N, F, P, rowptr, col, val64, type, ntypes,
+                                                          kappa, pos, pol, e0, bc);
+  k_col_norms_c<<<B, 256, 0, s>>>(bc, 4 * N, B, bn);
+  *nl += 2;
   return cudaGetLastError();
 }
 

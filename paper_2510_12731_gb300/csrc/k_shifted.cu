@@ -35,8 +35,6 @@ namespace px {
 
 namespace {
 
-constexpr int kMvRows = 4;       // matrix rows per warp in the matvec
-constexpr int kMvChunk = 1024;   // operand columns staged in shared memory at a time
 constexpr int kDotsK = 8;        // basis vectors per projection block
 constexpr int kDotsRows = 512;   // rows per projection block
 constexpr int kUpdK = 32;        // basis vectors per update block
@@ -48,14 +46,33 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 // ---------------------------------------------------------------- matvec
 // part[sg][i][p] = sum over the columns j of segment sg of (Th + Tl)[i][j] (vh + vl)[j][p],
 // for the work items (32-row block, column segment) handed out in a strided loop over a
-// persistent grid.  Each warp owns four rows; each lane reads 4 consecutive columns of
-// both planes per step (16-byte streaming loads), the operand chunk comes from shared
-// memory, and the 32 lanes' double-FP32 partial sums are added with TwoSum shuffles.
+// persistent grid.  T tiles (32 rows x 128 columns of both planes, 32 KB) and the operand's
+// planar chunks stream through a 3-stage shared-memory ring filled with 16-byte cp.async,
+// so two chunks are always in flight while the third is consumed.  Each warp owns four
+// rows; each lane takes 4 consecutive columns of a chunk; the 32 lanes' double-FP32
+// partial sums are added with TwoSum shuffles at the end of the item.
+constexpr int kMvCols = 128;     // columns per pipeline stage
+constexpr int kMvStages = 3;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int NP>
+__host__ __device__ constexpr int mv_stage_floats() { return 2 * 32 * kMvCols + 2 * NP * kMvCols; }
+
 template <int NP>
 __global__ void __launch_bounds__(256, 2)
-k_sk_matvec(const float* __restrict__ Th, const float* __restrict__ Tl, int n, int np, int S,
-            int seg_cols, const float2* __restrict__ v, float2* __restrict__ part) {
-  __shared__ __align__(16) float xs[2 * NP][kMvChunk];
+k_sk_matvec(const float* __restrict__ Th, const float* __restrict__ Tl, int np, int S,
+            int seg_cols, const float* __restrict__ vp, float2* __restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int kSt = mv_stage_floats<NP>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nrb = np / 32;
   const int items = nrb * S;
@@ -63,54 +80,71 @@ k_sk_matvec(const float* __restrict__ Th, const float* __restrict__ Tl, int n, i
     const int rb = item % nrb, sg = item / nrb;
     const int c_begin = sg * seg_cols;
     const int c_end = min(np, c_begin + seg_cols);
-    const int row0 = rb * 32 + warp * kMvRows;
-    float ah[kMvRows][NP], al[kMvRows][NP];
+    const int nch = (c_end - c_begin) / kMvCols;
+    auto issue = [&](int ch) {
+      float* st = smem + (ch % kMvStages) * kSt;
+      const int c0 = c_begin + ch * kMvCols;
+      // T: 2 planes x 32 rows x 32 chunks of 16 bytes, 8 per thread
 #pragma unroll
-    for (int r = 0; r < kMvRows; ++r)
+      for (int q = 0; q < 8; ++q) {
+        const int id = threadIdx.x + 256 * q;
+        const int pl = id >> 10, row = (id >> 5) & 31, c16 = id & 31;
+        const float* src = (pl ? Tl : Th) + (size_t)(rb * 32 + row) * np + c0 + c16 * 4;
+        cp_async16(st + (pl * 32 + row) * kMvCols + c16 * 4, src);
+      }
+      // operand: 2 NP planes x 32 chunks
+      if ((int)threadIdx.x < 2 * NP * 32) {
+        const int pl = threadIdx.x >> 5, c16 = threadIdx.x & 31;
+        cp_async16(st + 2 * 32 * kMvCols + pl * kMvCols + c16 * 4, vp + (size_t)pl * np + c0 + c16 * 4);
+      }
+    };
+    float ah[4][NP], al[4][NP];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int p = 0; p < NP; ++p) ah[r][p] = al[r][p] = 0.f;
-    for (int c0 = c_begin; c0 < c_end; c0 += kMvChunk) {
-      const int len = min(kMvChunk, c_end - c0);   // a multiple of 128
-      __syncthreads();                               // the previous chunk is consumed
-      for (int t = threadIdx.x; t < len * NP; t += blockDim.x) {
-        const int jj = t / NP, p = t - jj * NP;
-        const int j = c0 + jj;
-        const float2 x = j < n ? v[(size_t)j * NP + p] : make_float2(0.f, 0.f);
-        xs[2 * p][jj] = x.x;
-        xs[2 * p + 1][jj] = x.y;
-      }
+#pragma unroll
+    for (int c = 0; c < kMvStages - 1; ++c) {
+      if (c < nch) issue(c);
+      cp_async_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+      // chunk c + 2 goes into the stage that held chunk c - 1 (consumed: see the barrier
+      // at the end of the previous iteration)
+      if (c + kMvStages - 1 < nch) issue(c + kMvStages - 1);
+      cp_async_commit();
+      cp_async_wait<kMvStages - 1>();
       __syncthreads();
-      for (int it = 0; it < len; it += 128) {
-        const int jj = it + lane * 4;
-        float4 th[kMvRows], tl[kMvRows];
+      const float* st = smem + (c % kMvStages) * kSt;
+      float4 th[4], tl[4];
 #pragma unroll
-        for (int r = 0; r < kMvRows; ++r) {
-          const size_t o = (size_t)(row0 + r) * np + c0 + jj;
-          th[r] = __ldcs(reinterpret_cast<const float4*>(Th + o));
-          tl[r] = __ldcs(reinterpret_cast<const float4*>(Tl + o));
-        }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          const float4 xh = *reinterpret_cast<const float4*>(&xs[2 * p][jj]);
-          const float4 xl = *reinterpret_cast<const float4*>(&xs[2 * p + 1][jj]);
-#pragma unroll
-          for (int r = 0; r < kMvRows; ++r) {
-            ff::mac(ah[r][p], al[r][p], th[r].x, tl[r].x, xh.x, xl.x);
-            ff::mac(ah[r][p], al[r][p], th[r].y, tl[r].y, xh.y, xl.y);
-            ff::mac(ah[r][p], al[r][p], th[r].z, tl[r].z, xh.z, xl.z);
-            ff::mac(ah[r][p], al[r][p], th[r].w, tl[r].w, xh.w, xl.w);
-          }
-        }
+      for (int r = 0; r < 4; ++r) {
+        th[r] = *reinterpret_cast<const float4*>(st + (warp * 4 + r) * kMvCols + lane * 4);
+        tl[r] = *reinterpret_cast<const float4*>(st + (32 + warp * 4 + r) * kMvCols + lane * 4);
       }
 #pragma unroll
-      for (int r = 0; r < kMvRows; ++r)
+      for (int p = 0; p < NP; ++p) {
+        const float4 xh = *reinterpret_cast<const float4*>(st + 2 * 32 * kMvCols + (2 * p) * kMvCols + lane * 4);
+        const float4 xl = *reinterpret_cast<const float4*>(st + 2 * 32 * kMvCols + (2 * p + 1) * kMvCols + lane * 4);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) ff::renorm(ah[r][p], al[r][p]);
+        for (int r = 0; r < 4; ++r) {
+          ff::mac(ah[r][p], al[r][p], th[r].x, tl[r].x, xh.x, xl.x);
+          ff::mac(ah[r][p], al[r][p], th[r].y, tl[r].y, xh.y, xl.y);
+          ff::mac(ah[r][p], al[r][p], th[r].z, tl[r].z, xh.z, xl.z);
+          ff::mac(ah[r][p], al[r][p], th[r].w, tl[r].w, xh.w, xl.w);
+        }
+      }
+      if ((c & 7) == 7)   // keep the compensations below ulp of the sums
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int p = 0; p < NP; ++p) ff::renorm(ah[r][p], al[r][p]);
+      __syncthreads();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int r = 0; r < kMvRows; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           const float bh = __shfl_xor_sync(0xffffffffu, ah[r][p], o);
@@ -119,10 +153,10 @@ k_sk_matvec(const float* __restrict__ Th, const float* __restrict__ Tl, int n, i
         }
     if (lane == 0)
 #pragma unroll
-      for (int r = 0; r < kMvRows; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int p = 0; p < NP; ++p)
-          part[((size_t)sg * np + row0 + r) * NP + p] = make_float2(ah[r][p], al[r][p]);
+          part[((size_t)sg * np + rb * 32 + warp * 4 + r) * NP + p] = make_float2(ah[r][p], al[r][p]);
   }
 }
 
@@ -139,46 +173,79 @@ __global__ void k_sk_combine(int n, int np, int NP, int S, const float2* __restr
   U[idx] = make_float2(h, l);
 }
 
-// W[i][p] = (Kbar U)_i = sum_j K_ij (U_j - U_i)  (Eq. 2, FP64 arithmetic)
+// W[i][p] = (Kbar U)_i = sum_j K_ij (U_j - U_i)  (Eq. 2) in double-FP32: the differences by
+// TwoSum, K_ij = val32 + its FP32 remainder, products by TwoProduct (the FP64 pipe is
+// 1/64 of the FP32 rate).  Eight lanes share a row (each takes every eighth neighbour),
+// so a row's gathers are in flight together; the partial sums meet by shuffles.
 template <int NP>
-__global__ void k_sk_kbar(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                          const double* __restrict__ val, const float2* __restrict__ U,
-                          float2* __restrict__ W) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double ui[NP], acc[NP];
+__global__ void __launch_bounds__(256) k_sk_kbar(int n, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ col,
+                                                 const double* __restrict__ val,
+                                                 const float* __restrict__ val32,
+                                                 const float2* __restrict__ U,
+                                                 float2* __restrict__ W) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, sub = threadIdx.x & 7;
+  const bool valid = g < n;
+  const int i = valid ? g : n - 1;
+  float2 ui[NP];
+  float ah[NP], al[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    ui[p] = ff::join(U[(size_t)i * NP + p]);
-    acc[p] = 0.0;
+    ui[p] = U[(size_t)i * NP + p];
+    ah[p] = al[p] = 0.f;
   }
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-    const int j = col[e];
-    const double k = val[e];
+  if (valid)
+    for (int e = rowptr[i] + sub; e < rowptr[i + 1]; e += 8) {
+      const int j = col[e];
+      const float kh = val32[e];
+      const float kl = (float)(val[e] - (double)kh);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] = fma(k, ff::join(U[(size_t)j * NP + p]) - ui[p], acc[p]);
+      for (int p = 0; p < NP; ++p) {
+        float dh = U[(size_t)j * NP + p].x, dl = U[(size_t)j * NP + p].y;
+        ff::add(dh, dl, -ui[p].x, -ui[p].y);
+        ff::mac(ah[p], al[p], kh, kl, dh, dl);
+      }
+    }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, ah[p], o);
+      const float bl = __shfl_xor_sync(0xffffffffu, al[p], o);
+      ff::add(ah[p], al[p], bh, bl);
+    }
+    ff::renorm(ah[p], al[p]);
   }
+  if (valid && sub == 0)
 #pragma unroll
-  for (int p = 0; p < NP; ++p) W[(size_t)i * NP + p] = ff::split(acc[p]);
+    for (int p = 0; p < NP; ++p) W[(size_t)i * NP + p] = make_float2(ah[p], al[p]);
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt
 // dpart[rb][k][p] = sum over the rows of block rb of V_k[i][p] W[i][p], k in the block's
-// group of kDotsK basis vectors (grid x), rows in blocks of kDotsRows (grid y).
+// group of kDotsK basis vectors (grid x), rows in blocks of rows_per_blk (grid y).
 template <int NP>
 __global__ void __launch_bounds__(256)
-k_sk_dots(const float2* __restrict__ V, const float2* __restrict__ W, int n, int j, int m1,
-          double* __restrict__ dpart) {
+k_sk_dots(const float2* __restrict__ V, const float2* __restrict__ W, int n, int j,
+          int rows_per_blk, int m1, double* __restrict__ dpart) {
   const int k0 = blockIdx.x * kDotsK;
   if (k0 > j) return;   // uniform over the block
   const int nk = min(kDotsK, j + 1 - k0);
-  const int r0 = blockIdx.y * kDotsRows, r1 = min(n, r0 + kDotsRows);
+  const int r0 = blockIdx.y * rows_per_blk, r1 = min(n, r0 + rows_per_blk);
   float ah[kDotsK][NP], al[kDotsK][NP];
 #pragma unroll
   for (int kk = 0; kk < kDotsK; ++kk)
 #pragma unroll
     for (int p = 0; p < NP; ++p) ah[kk][p] = al[kk][p] = 0.f;
+  int nmac = 0;
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    if (++nmac == 32) {   // keep the compensation below ulp of the sum
+      nmac = 0;
+#pragma unroll
+      for (int kk = 0; kk < kDotsK; ++kk)
+#pragma unroll
+        for (int p = 0; p < NP; ++p) ff::renorm(ah[kk][p], al[kk][p]);
+    }
     float2 w[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) w[p] = W[(size_t)i * NP + p];
@@ -305,42 +372,66 @@ k_sk_update_fin(float2* __restrict__ W, int n, int nkc, const float2* __restrict
 // H[j][j+1][p] = ||W_p||, and the scale of the next basis vector (0 on breakdown, i.e.
 // when the new direction is negligible against the column: an invariant subspace, in
 // which every shift's least-squares residual is exact).  One block.
-__global__ void k_sk_hess(int j, int NP, int m1, int m2, int passes, const double* __restrict__ h,
-                          const double* __restrict__ npart, int nnb, double* __restrict__ H,
-                          double* __restrict__ inv_h) {
+__global__ void __launch_bounds__(256) k_sk_hess(int j, int NP, int m1, int m2, int passes,
+                                                 const double* __restrict__ h,
+                                                 const double* __restrict__ npart, int nnb,
+                                                 double* __restrict__ H, double* __restrict__ inv_h) {
   double* Hc = H + (size_t)j * m2 * NP;
+  __shared__ double sc[8][4], sn2[8][4];
+  double c2[4] = {0.0, 0.0, 0.0, 0.0}, n2[4] = {0.0, 0.0, 0.0, 0.0};
   for (int idx = threadIdx.x; idx < (j + 1) * NP; idx += blockDim.x) {
     double v = h[idx];
     if (passes > 1) v += h[(size_t)m1 * NP + idx];
     Hc[idx] = v;
+    c2[idx % NP] += v * v;
+  }
+  for (int b = threadIdx.x; b < nnb * NP; b += blockDim.x) n2[b % NP] += npart[b];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p = 0; p < NP; ++p) {
+    double a = c2[p], q = n2[p];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) {
+      sc[warp][p] = a;
+      sn2[warp][p] = q;
+    }
   }
   __syncthreads();
   if ((int)threadIdx.x < NP) {
     const int p = threadIdx.x;
-    double hn2 = 0.0;
-    for (int b = 0; b < nnb; ++b) hn2 += npart[(size_t)b * NP + p];
+    double hn2 = 0.0, cc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      hn2 += sn2[w][p];
+      cc += sc[w][p];
+    }
     const double hn = sqrt(hn2);
-    double c2 = hn2;
-    for (int k = 0; k <= j; ++k) c2 += Hc[k * NP + p] * Hc[k * NP + p];
     Hc[(size_t)(j + 1) * NP + p] = hn;
-    inv_h[p] = hn > 1e-14 * sqrt(c2) ? 1.0 / hn : 0.0;
+    inv_h[p] = hn > 1e-14 * sqrt(cc + hn2) ? 1.0 / hn : 0.0;
   }
 }
 
-// One thread per system s = f * NP + pl: rotate column j of Hbar - z Ibar by the
-// system's previous rotations, store the rotated column in R, form the new rotation,
-// update the rotated right-hand side and stop the system once its least-squares
-// residual |g_{j+1}| reaches its target (or the subspace is invariant, or the basis is
-// full).  active[j] counts the systems still iterating after step j.
-__global__ void k_sk_givens(int j, int m, int NP, int P, int p0, int Bg, int m2,
-                            const double* __restrict__ H, const double* __restrict__ inv_h,
-                            const double2* __restrict__ zq, double* __restrict__ cs,
-                            double2* __restrict__ sn, double2* __restrict__ g,
-                            double2* __restrict__ R, size_t rstride,
-                            const double* __restrict__ target, int* __restrict__ jconv,
-                            int* __restrict__ active) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= Bg || jconv[s] != 0) return;
+// One warp per system s = f * NP + pl: rotate column j of Hbar - z Ibar by the system's
+// previous rotations, store the rotated column in R, form the new rotation, update the
+// rotated right-hand side and stop the system once its least-squares residual |g_{j+1}|
+// reaches its target (or the subspace is invariant, or the basis is full).  active[j]
+// counts the systems still iterating after step j.
+//
+// Rotation k maps the carried entry x_k and the column entry h_{k+1} to
+//   R_k = c_k x_k + s_k h_{k+1},   x_{k+1} = -conj(s_k) x_k + c_k h_{k+1},
+// an affine recurrence x_{k+1} = A_k x_k + B_k.  Affine maps compose associatively, so
+// the 32 lanes take 32 consecutive rotations and an inclusive shuffle scan gives each
+// lane the composed map from the chunk's carried-in entry: the dependent FP64 chain is
+// 5 scan steps per 32 rotations instead of 32 (GB300's FP64 pipe has a long latency).
+__global__ void __launch_bounds__(128)
+k_sk_givens(int j, int m, int NP, int P, int p0, int Bg, int m2, const double* __restrict__ H,
+            const double* __restrict__ inv_h, const double2* __restrict__ zq,
+            double* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
+            double2* __restrict__ R, size_t rstride, const double* __restrict__ target,
+            int* __restrict__ jconv, int* __restrict__ active) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= Bg || jconv[s] != 0) return;   // uniform over the warp
   const int f = s / NP, pl = s - f * NP;
   const double2 z = zq[(size_t)f * P + p0 + pl];
   const double* Hc = H + (size_t)j * m2 * NP;
@@ -349,18 +440,42 @@ __global__ void k_sk_givens(int j, int m, int NP, int P, int p0, int Bg, int m2,
     return k == j ? make_double2(v - z.x, -z.y) : make_double2(v, 0.0);
   };
   double2* Rs = R + (size_t)s * rstride + (size_t)j * (j + 1) / 2;
-  double2 x0 = hcol(0);
-  for (int k = 0; k < j; ++k) {
-    const double c = cs[(size_t)k * Bg + s];
-    const double2 sk = sn[(size_t)k * Bg + s];
-    const double2 x1 = hcol(k + 1);
-    const double2 sx1 = cmul(sk, x1);
-    Rs[k] = make_double2(c * x0.x + sx1.x, c * x0.y + sx1.y);
-    // -conj(s) x0 + c x1
-    x0 = make_double2(-(sk.x * x0.x + sk.y * x0.y) + c * x1.x, -(sk.x * x0.y - sk.y * x0.x) + c * x1.y);
+  double2 x = hcol(0);   // carried entry entering the chunk (the same on every lane)
+  for (int k0 = 0; k0 < j; k0 += 32) {
+    const int k = k0 + lane;
+    const bool ok = k < j;
+    const double c = ok ? cs[(size_t)k * Bg + s] : 1.0;
+    const double2 sk = ok ? sn[(size_t)k * Bg + s] : make_double2(0.0, 0.0);
+    const double2 h1 = ok ? hcol(k + 1) : make_double2(0.0, 0.0);
+    // this lane's map: A = -conj(s), B = c h_{k+1}; identity beyond the last rotation
+    double2 A = ok ? make_double2(-sk.x, sk.y) : make_double2(1.0, 0.0);
+    double2 Bv = ok ? make_double2(c * h1.x, c * h1.y) : make_double2(0.0, 0.0);
+    // inclusive scan: (A, B) <- (A, B) o (A', B') of the lane d below = (A A', A B' + B)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double ar = __shfl_up_sync(0xffffffffu, A.x, d), ai = __shfl_up_sync(0xffffffffu, A.y, d);
+      const double br = __shfl_up_sync(0xffffffffu, Bv.x, d), bi = __shfl_up_sync(0xffffffffu, Bv.y, d);
+      if (lane >= d) {
+        const double2 nb = make_double2(fma(A.x, br, fma(-A.y, bi, Bv.x)), fma(A.x, bi, fma(A.y, br, Bv.y)));
+        A = cmul(A, make_double2(ar, ai));
+        Bv = nb;
+      }
+    }
+    // x_{k+1} from the composed map; x_k is the previous lane's (the carry for lane 0)
+    const double2 xn = make_double2(fma(A.x, x.x, fma(-A.y, x.y, Bv.x)), fma(A.x, x.y, fma(A.y, x.x, Bv.y)));
+    double2 xk = make_double2(__shfl_up_sync(0xffffffffu, xn.x, 1), __shfl_up_sync(0xffffffffu, xn.y, 1));
+    if (lane == 0) xk = x;
+    if (ok) {
+      const double2 sh = cmul(sk, h1);
+      Rs[k] = make_double2(fma(c, xk.x, sh.x), fma(c, xk.y, sh.y));
+    }
+    // carry: x after the chunk's last rotation
+    const int last = min(31, j - 1 - k0);
+    x = make_double2(__shfl_sync(0xffffffffu, xn.x, last), __shfl_sync(0xffffffffu, xn.y, last));
   }
+  if (lane != 0) return;
   const double hn = Hc[(size_t)(j + 1) * NP + pl];
-  const double aa = sqrt(x0.x * x0.x + x0.y * x0.y);
+  const double aa = sqrt(x.x * x.x + x.y * x.y);
   const double rho = sqrt(aa * aa + hn * hn);
   double c;
   double2 sj, r;
@@ -369,7 +484,7 @@ __global__ void k_sk_givens(int j, int m, int NP, int P, int p0, int Bg, int m2,
     sj = make_double2(1.0, 0.0);
     r = make_double2(hn, 0.0);
   } else {
-    const double2 ph = make_double2(x0.x / aa, x0.y / aa);
+    const double2 ph = make_double2(x.x / aa, x.y / aa);
     c = aa / rho;
     sj = make_double2(ph.x * hn / rho, ph.y * hn / rho);
     r = make_double2(ph.x * rho, ph.y * rho);
@@ -389,32 +504,39 @@ __global__ void k_sk_givens(int j, int m, int NP, int P, int p0, int Bg, int m2,
   }
 }
 
-// V[j+1][i][p] = W[i][p] * inv_h[p]
+// V[j+1][i][p] = W[i][p] * inv_h[p], and its planar copy vp[2p][i], vp[2p+1][i] (hi, lo:
+// the matvec operand, rows n .. np-1 stay zero)
 template <int NP>
-__global__ void k_sk_normalize(int n, int j, const float2* __restrict__ W,
-                               const double* __restrict__ inv_h, float2* __restrict__ V) {
+__global__ void k_sk_normalize(int n, int np, int j, const float2* __restrict__ W,
+                               const double* __restrict__ inv_h, float2* __restrict__ V,
+                               float* __restrict__ vp) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * NP) return;
-  const int p = idx % NP;
+  const int i = idx / NP, p = idx - i * NP;
   const float2 sc = ff::split(inv_h[p]);
   const float2 w = W[idx];
   float h = 0.f, l = 0.f;
   ff::mac(h, l, w.x, w.y, sc.x, sc.y);
   ff::renorm(h, l);
   V[(size_t)(j + 1) * n * NP + idx] = make_float2(h, l);
+  vp[(size_t)(2 * p) * np + i] = h;
+  vp[(size_t)(2 * p + 1) * np + i] = l;
 }
 
 // Start: V_0 = b_p / beta_p, g_0 = beta_p for every system of direction p, targets,
 // jconv = 0 (iterating) or -1 (zero right-hand side: x = 0 exactly).
-__global__ void k_sk_start(int n, int NP, int P, int p0, int Bg, const double* __restrict__ b,
+__global__ void k_sk_start(int n, int np, int NP, int P, int p0, int Bg, const double* __restrict__ b,
                            const double* __restrict__ bnorm, double tol_abs_frac,
-                           float2* __restrict__ V, double2* __restrict__ g,
+                           float2* __restrict__ V, float* __restrict__ vp, double2* __restrict__ g,
                            double* __restrict__ target, int* __restrict__ jconv) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < n * NP) {
     const int i = idx / NP, p = idx - i * NP;
     const double bn = bnorm[p0 + p];
-    V[idx] = ff::split(bn > 0.0 ? b[(size_t)i * P + p0 + p] / bn : 0.0);
+    const float2 v = ff::split(bn > 0.0 ? b[(size_t)i * P + p0 + p] / bn : 0.0);
+    V[idx] = v;
+    vp[(size_t)(2 * p) * np + i] = v.x;
+    vp[(size_t)(2 * p + 1) * np + i] = v.y;
   }
   if (idx < Bg) {
     const int pl = idx % NP;
@@ -601,23 +723,33 @@ SkMatvecPlan sk_matvec_plan(int np) {
 }
 
 cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, int NP,
-                             const SkMatvecPlan& pl, const float2* v, float2* part, float2* U,
+                             const SkMatvecPlan& pl, const float* vp, float2* part, float2* U,
                              cudaStream_t s, long long* nl) {
   if (np % 128 || NP < 1 || NP > 4) return cudaErrorInvalidValue;
+  cudaError_t err = cudaSuccess;
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
-    k_sk_matvec<K><<<pl.grid, 256, 0, s>>>(Th, Tl, n, np, pl.S, pl.seg_cols, v, part);
+    const int shm = kMvStages * mv_stage_floats<K>() * (int)sizeof(float);
+    static bool attr_set[5] = {false, false, false, false, false};
+    if (!attr_set[K]) {
+      err = cudaFuncSetAttribute(k_sk_matvec<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+      attr_set[K] = err == cudaSuccess;
+    }
+    if (err == cudaSuccess) k_sk_matvec<K><<<pl.grid, 256, shm, s>>>(Th, Tl, np, pl.S, pl.seg_cols, vp, part);
   });
+  if (err != cudaSuccess) return err;
   k_sk_combine<<<(n * NP + 255) / 256, 256, 0, s>>>(n, np, NP, pl.S, part, U);
   *nl += 2;
   return cudaGetLastError();
 }
 
 cudaError_t launch_sk_kbar(int n, int NP, const int* rowptr, const int* col, const double* val,
-                           const float2* U, float2* W, cudaStream_t s, long long* nl) {
+                           const float* val32, const float2* U, float2* W, cudaStream_t s,
+                           long long* nl) {
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
-    k_sk_kbar<K><<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, col, val, U, W);
+    k_sk_kbar<K><<<(unsigned)(((size_t)n * 8 + 255) / 256), 256, 0, s>>>(n, rowptr, col, val, val32,
+                                                                         U, W);
   });
   ++*nl;
   return cudaGetLastError();
@@ -629,11 +761,15 @@ int sk_update_chunks(int m) { return (m + 1 + kUpdK - 1) / kUpdK; }
 cudaError_t launch_sk_gs_pass(const float2* V, float2* W, int n, int NP, int j, int m1,
                               double* dpart, double* h, float2* upart, bool last, double* npart,
                               cudaStream_t s, long long* nl) {
-  const int nrb = sk_row_blocks(n);
+  // row blocks of the projections: enough blocks to fill the GPU (about one per SM), and
+  // no more, so that each thread sums many rows before the block reduction
+  const int ngk = (j + 1 + kDotsK - 1) / kDotsK;
+  const int nrb = std::max(1, std::min(sk_row_blocks(n), (sm_count() + ngk - 1) / ngk));
+  const int rows_per_blk = (n + nrb - 1) / nrb;
   const int nkc = (j + 1 + kUpdK - 1) / kUpdK;
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
-    k_sk_dots<K><<<dim3((j + 1 + kDotsK - 1) / kDotsK, nrb), 256, 0, s>>>(V, W, n, j, m1, dpart);
+    k_sk_dots<K><<<dim3(ngk, nrb), 256, 0, s>>>(V, W, n, j, rows_per_blk, m1, dpart);
     k_sk_dots_reduce<<<((j + 1) * K + 255) / 256, 256, 0, s>>>(j, K, nrb, m1, dpart, h);
     k_sk_update<K><<<dim3(nkc, (n + 255) / 256), 256, 0, s>>>(V, n, j, h, upart);
     k_sk_update_fin<K><<<(n + 255) / 256, 256, 0, s>>>(W, n, nkc, upart, last ? 1 : 0, npart);
@@ -647,12 +783,13 @@ cudaError_t launch_sk_step_end(const SkGroup& G, int j, const double* h, int pas
                                long long* nl) {
   const int nnb = (G.n + 255) / 256;
   k_sk_hess<<<1, 256, 0, s>>>(j, G.NP, G.m + 1, G.m + 2, passes, h, npart, nnb, G.H, G.inv_h);
-  k_sk_givens<<<(G.Bg + 127) / 128, 128, 0, s>>>(j, G.m, G.NP, G.P, G.p0, G.Bg, G.m + 2, G.H,
+  // one warp per system, 4 systems per block
+  k_sk_givens<<<(G.Bg + 3) / 4, 128, 0, s>>>(j, G.m, G.NP, G.P, G.p0, G.Bg, G.m + 2, G.H,
                                                  G.inv_h, G.zq, G.cs, G.sn, G.g, G.R, G.rstride,
                                                  G.target, G.jconv, G.active);
   with_np(G.NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
-    k_sk_normalize<K><<<(G.n * K + 255) / 256, 256, 0, s>>>(G.n, j, W, G.inv_h, V);
+    k_sk_normalize<K><<<(G.n * K + 255) / 256, 256, 0, s>>>(G.n, G.np, j, W, G.inv_h, V, G.vp);
   });
   *nl += 3;
   return cudaGetLastError();
@@ -661,8 +798,10 @@ cudaError_t launch_sk_step_end(const SkGroup& G, int j, const double* h, int pas
 cudaError_t launch_sk_start(const SkGroup& G, const double* b, const double* bnorm,
                             double tol_abs_frac, float2* V, cudaStream_t s, long long* nl) {
   const int n = std::max(G.n * G.NP, G.Bg);
-  k_sk_start<<<(n + 255) / 256, 256, 0, s>>>(G.n, G.NP, G.P, G.p0, G.Bg, b, bnorm, tol_abs_frac, V,
-                                             G.g, G.target, G.jconv);
+  cudaError_t e = cudaMemsetAsync(G.vp, 0, sizeof(float) * 2 * G.NP * (size_t)G.np, s);
+  if (e != cudaSuccess) return e;
+  k_sk_start<<<(n + 255) / 256, 256, 0, s>>>(G.n, G.np, G.NP, G.P, G.p0, G.Bg, b, bnorm, tol_abs_frac,
+                                             V, G.vp, G.g, G.target, G.jconv);
   ++*nl;
   return cudaGetLastError();
 }

@@ -112,6 +112,26 @@ __global__ void k_neigh_fill(const double* __restrict__ pos, int N, const int* _
   }
 }
 
+// Eq. 10's nearest neighbours: nn[i][t] = atoms j of type t in row i of the CSR (so within
+// r_cut) with r_ij <= s_ij r0_ij, the Fermi midpoint of the pair (f = 1/2, Eq. 4); the first
+// shell of an fcc or bcc lattice for s = 1.1.  ident[i] = i.  One thread per atom.
+__global__ void k_nn_counts(const double* __restrict__ pos, int N, const int* __restrict__ type,
+                            int ntypes, const double* __restrict__ r0t, const double* __restrict__ st,
+                            const int* __restrict__ rowptr, const int* __restrict__ col, int* nn,
+                            int* ident) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  ident[i] = i;
+  for (int t = 0; t < ntypes; ++t) nn[(size_t)i * ntypes + t] = 0;
+  const int ti = type[i];
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int j = col[e];
+    const int tp = ti * ntypes + type[j];
+    const double rm = st[tp] * r0t[tp];
+    if (dist2(pos, i, j) <= rm * rm) nn[(size_t)i * ntypes + type[j]] += 1;
+  }
+}
+
 // T^qq (Eq. 5).  Thread per (i, j) atom pair.
 __global__ void k_build_Tqq(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
                             int ld, double* T) {
@@ -260,10 +280,16 @@ __global__ void k_split_op(const double* __restrict__ A, size_t n, uint16_t* hi,
   }
 }
 
-__global__ void k_stage_pos4(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
-                             float4* p4f, double* p4d) {
+__global__ void k_stage_pos4(const double* __restrict__ pos, const double* __restrict__ Rq,
+                             const double* __restrict__ Rmu, int N, float4* p4f, double* p4d,
+                             float* rm2f, double* rm2d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (rm2f) {
+    const double m2 = Rmu[i] * Rmu[i];
+    rm2f[i] = (float)m2;
+    rm2d[i] = m2;
+  }
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], r2 = Rq[i] * Rq[i];
   p4f[i] = make_float4((float)x, (float)y, (float)z, (float)r2);
   p4d[4 * (size_t)i] = x;
@@ -275,7 +301,8 @@ __global__ void k_stage_pos4(const double* __restrict__ pos, const double* __res
 }  // namespace
 
 cudaError_t launch_stage_pos4(const DevStructure& d, cudaStream_t s, long long* nl) {
-  k_stage_pos4<<<(d.N + 255) / 256, 256, 0, s>>>(d.pos64, d.Rq, d.N, d.pos4f, d.pos4d);
+  k_stage_pos4<<<(d.N + 255) / 256, 256, 0, s>>>(d.pos64, d.Rq, d.Rmu, d.N, d.pos4f, d.pos4d,
+                                                  d.rm2f, d.rm2d);
   ++*nl;
   return cudaGetLastError();
 }
@@ -339,6 +366,14 @@ cudaError_t launch_build_M64(const DevStructure& d, double* M64,
 cudaError_t launch_split_op(const double* A, size_t n, uint16_t* hi, uint16_t* lo, bool f16,
                             int scale_exp, cudaStream_t s, long long* nl) {
   k_split_op<<<152 * 16, 256, 0, s>>>(A, n, hi, lo, f16 ? 1 : 0, ldexp(1.0, scale_exp));
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nn_counts(const double* pos, int N, const int* type, int ntypes,
+                             const double* r0t, const double* st, const int* rowptr,
+                             const int* col, int* nn, int* ident, cudaStream_t s, long long* nl) {
+  k_nn_counts<<<(N + 127) / 128, 128, 0, s>>>(pos, N, type, ntypes, r0t, st, rowptr, col, nn, ident);
   ++*nl;
   return cudaGetLastError();
 }

@@ -77,6 +77,7 @@ struct px_handle {
   DevBuf b_perm;   // [N] caller index of internal atom i
   DevBuf b_stage;  // staging inputs (caller order) and sort scratch
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
+  DevBuf b_rm2;    // matrix-free wFQFmu: R_mu^2 in FP32 and FP64
   DevBuf b_M64;    // FP64 M = diag(Kbar, I) T while its split planes are built
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
@@ -86,6 +87,8 @@ struct px_handle {
   int* d_err = nullptr;         // device flag: a bounded pipeline wait ran out of time
   DevBuf b_alpha, b_q, b_mu;
   DevBuf b_sk;                  // shifted Krylov work space (carved per solve)
+  DevBuf b_het;                 // heterogeneous wFQFmu: per-column tables and right-hand sides
+  DevBuf b_hstruct;             // heterogeneous wFQFmu: type parameters, Eq. 10 counts, identity
   int* h_skact = nullptr;       // pinned host copy of the shifted solve's active counts
   size_t h_skact_n = 0;
   cudaEvent_t ev_sk[2] = {nullptr, nullptr};   // start / end of the shifted phase
@@ -115,12 +118,12 @@ void drop_graphs(px_handle* h) {
 void free_all(px_handle* h) {
   DevBuf* bufs[] = {&h->b_M64, &h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
-                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_rm2, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
                     &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl, &h->b_dpart,
-                    &h->b_alpha, &h->b_q, &h->b_mu, &h->b_sk};
+                    &h->b_alpha, &h->b_q, &h->b_mu, &h->b_sk, &h->b_het, &h->b_hstruct};
   for (DevBuf* b : bufs) b->release();
 }
 
@@ -200,15 +203,23 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   if (!xyz || !tidx || !types) throw PxError{PX_EINVAL, "NULL input"};
   if (N < 1) throw PxError{PX_EINVAL, "n_atoms must be >= 1"};
   if (ntypes < 1) throw PxError{PX_EINVAL, "n_types must be >= 1"};
-  if (model != PX_WFQ && model != PX_WFQFMU) throw PxError{PX_EINVAL, "bad model"};
+  if (model != PX_WFQ && model != PX_WFQFMU && model != PX_WFQFMU_HETERO)
+    throw PxError{PX_EINVAL, "bad model"};
+  const bool hetero = model == PX_WFQFMU_HETERO;
   for (int t = 0; t < ntypes; ++t) {
     const px_atom_type& a = types[t];
     double v[] = {a.r0_ang, a.d, a.s, a.area_bohr2, a.Rq_bohr, a.Rmu_bohr, a.drude_n_au, a.tau_au};
     for (double x : v)
       if (!std::isfinite(x) || !(x > 0.0)) throw PxError{PX_EINVAL, "atom type parameters must be finite and > 0"};
-    if (a.drude_n_au != types[0].drude_n_au || a.tau_au != types[0].tau_au)
-      throw PxError{PX_EINVAL, "all atom types must share drude_n_au and tau_au (Eq. 1 has one z_q)"};
+    if (!hetero && (a.drude_n_au != types[0].drude_n_au || a.tau_au != types[0].tau_au))
+      throw PxError{PX_EINVAL, "all atom types must share drude_n_au and tau_au (Eqs. 1 and 7 have "
+                               "one z_q; use PX_WFQFMU_HETERO for Eq. 9)"};
   }
+  if (hetero && (h->opt.precision == PX_BF16SPLIT || h->opt.precision == PX_FP16SPLIT))
+    throw PxError{PX_ENOTIMPL, "PX_WFQFMU_HETERO runs PX_FP32 or PX_FP64 matvecs (its conductance "
+                               "block depends on the frequency, Eq. 9)"};
+  // internally the heterogeneous model is wFQFmu (4N unknowns) with per-type Drude data
+  if (hetero) model = PX_WFQFMU;
   for (int i = 0; i < N; ++i) {
     if (tidx[i] < 0 || tidx[i] >= ntypes) throw PxError{PX_EINVAL, "type index out of range"};
     for (int k = 0; k < 3; ++k)
@@ -256,6 +267,7 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   px::DevStructure& d = h->ds;
   h->have_structure = false;
   d.model = model;
+  d.hetero = hetero;
   d.N = N;
   d.nu = model == PX_WFQ ? N : 4 * N;
   d.np = (int)round_up(d.nu, px::kTile);
@@ -317,6 +329,29 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.val32 = h->b_val32.as<float>();
   CU(px::launch_neigh_fill(d.pos64, N, d.type, ntypes, d_rcut2, d_r0, d_d, d_s, d.area, d.rowptr,
                            d.col, d.val64, d.val32, s, &h->nl));
+  d.tpar = nullptr;
+  d.nncnt = nullptr;
+  d.ident = nullptr;
+  if (hetero) {
+    // per-type n, tau, area; Eq. 10's nearest-neighbour counts; the identity numbering
+    std::vector<double> tp(3 * (size_t)ntypes);
+    for (int t = 0; t < ntypes; ++t) {
+      tp[3 * t] = types[t].drude_n_au;
+      tp[3 * t + 1] = types[t].tau_au;
+      tp[3 * t + 2] = types[t].area_bohr2;
+    }
+    const size_t o1 = round_up(sizeof(double) * tp.size(), 256);
+    const size_t o2 = o1 + round_up(sizeof(int) * (size_t)N * ntypes, 256);
+    CU(h->b_hstruct.ensure(o2 + sizeof(int) * (size_t)N));
+    unsigned char* hb = h->b_hstruct.as<unsigned char>();
+    d.tpar = reinterpret_cast<double*>(hb);
+    d.nncnt = reinterpret_cast<int*>(hb + o1);
+    d.ident = reinterpret_cast<int*>(hb + o2);
+    CU(cudaMemcpyAsync(d.tpar, tp.data(), sizeof(double) * tp.size(), cudaMemcpyHostToDevice, s));
+    CU(px::launch_nn_counts(d.pos64, N, d.type, ntypes, d_r0, d_s, d.rowptr, d.col, d.nncnt, d.ident,
+                            s, &h->nl));
+    sync_stream(h, s);   // tp is read by the copy
+  }
 
   // T storage: materialised (FP64 for the true residual, plus the low-precision copy of the
   // matvec) when it fits the HBM budget, else generated on the fly inside the matvecs.
@@ -347,13 +382,20 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.op_has_kbar = false;
   d.op_scale_exp = 12;
   d.t_f16 = prec == PX_FP16SPLIT;
+  d.mu_self = h->opt.mu_self_term;
+  d.rm2f = nullptr;
+  d.rm2d = nullptr;
   if (d.matfree) {
-    if (model != PX_WFQ) throw PxError{PX_ENOTIMPL, "matrix-free mode supports PX_WFQ only in this build"};
     if (split) throw PxError{PX_ENOTIMPL, "matrix-free mode runs PX_FP32 or PX_FP64 matvecs"};
     CU(h->b_pos4f.ensure(sizeof(float4) * N));
     CU(h->b_pos4d.ensure(sizeof(double) * 4 * N));
     d.pos4f = h->b_pos4f.as<float4>();
     d.pos4d = h->b_pos4d.as<double>();
+    if (model == PX_WFQFMU) {
+      CU(h->b_rm2.ensure(round_up(sizeof(float) * N, 256) + sizeof(double) * N));
+      d.rm2f = h->b_rm2.as<float>();
+      d.rm2d = reinterpret_cast<double*>(h->b_rm2.as<unsigned char>() + round_up(sizeof(float) * N, 256));
+    }
     CU(px::launch_stage_pos4(d, s, &h->nl));
   } else {
     CU(h->b_T64.ensure(np2 * sizeof(double)));
@@ -531,21 +573,63 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   CU(px::launch_shifts(F, P, ntypes, model, d_omega, d_aib, h->drude_n, h->tau, zq_all, zmu_all,
                        s, &nl));
   double* b = grow<double>(h->b_b, (size_t)nu * P);
-  CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
-  double* bnorm = grow<double>(h->b_bnorm, P);
+  double* bnorm = grow<double>(h->b_bnorm, P + (size_t)B);
+  double* bn = bnorm + P;                                   // [B] per-column ||b||
   double* colv = grow<double>(h->b_rnorm, 3 * (size_t)B);   // rnorm | beta | target_all
   double* rnorm = colv;
   double* beta = colv + B;
   double* target_all = colv + 2 * (size_t)B;
-  CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
   double2* x = grow<double2>(h->b_x, (size_t)nu * B);
   double2* r = grow<double2>(h->b_r, (size_t)nu * B);
   int* iters = grow<int>(h->b_iters, B);
   int* act = grow<int>(h->b_act, B);
   CU(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)nu * B, s));
   CU(cudaMemsetAsync(iters, 0, sizeof(int) * B, s));
-  CU(px::launch_init_residual(b, nu, P, B, bnorm, inner_tol, tol_abs_frac, r, rnorm, beta,
-                              target_all, s, &nl));
+  // heterogeneous wFQFmu (Eq. 9): z_q per type, the per-atom z_mu of Eq. 10, complex bond
+  // weights of 1/2 (Kbar + Hbar(w)) and a complex right-hand side per column
+  const bool het = d.hetero;
+  double2* zq_het = nullptr;       // [ntypes][B] | act [ntypes][B]
+  double2* kap_all = nullptr;      // [ntypes^2][B] | act [ntypes^2][B]
+  double2* kap_act = nullptr;
+  double2* bc = nullptr;           // [nu][B]
+  double2* zmu_het = nullptr;      // per-atom z_mu: [N][B] all | [N][B] active | alpha^IB [N][B]
+  if (het) {
+    const size_t nt2 = (size_t)ntypes * ntypes;
+    double2* hb = grow<double2>(h->b_het, (2 * ntypes + 2 * nt2 + 3 * (size_t)N + nu) * (size_t)B);
+    zq_het = hb;
+    kap_all = zq_het + 2 * (size_t)ntypes * B;
+    kap_act = kap_all + nt2 * B;
+    zmu_het = kap_act + nt2 * B;
+    bc = zmu_het + 3 * (size_t)N * B;
+    CU(px::launch_hetero_tables(F, P, ntypes, N, d_omega, d.tpar, d.type, d.nncnt, zmu_all, zq_het,
+                                kap_all, zmu_het, s, &nl));
+    CU(px::launch_rhs_hetero(N, F, P, d.rowptr, d.col, d.val64, d.type, ntypes, kap_all, d.pos64,
+                             d_pol, e0, bc, bn, s, &nl));
+    CU(px::launch_init_residual_c(bc, nu, B, bn, inner_tol, tol_abs_frac, r, rnorm, beta, target_all,
+                                  s, &nl));
+  } else {
+    CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
+    CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
+    CU(px::launch_bnorm_cols(bnorm, P, B, bn, s, &nl));
+    CU(px::launch_init_residual(b, nu, P, B, bnorm, inner_tol, tol_abs_frac, r, rnorm, beta,
+                                target_all, s, &nl));
+  }
+  // the active columns' shifts: homogeneous z_q per column and z_mu per type; the
+  // heterogeneous model indexes z_mu per atom (dipole "types" = atoms) and z_q per type
+  const int* dip_type = het ? d.ident : d.type;
+  const int n_dip_types = het ? N : ntypes;
+  const double2* zmu_src = het ? zmu_het : zmu_all;
+  double2* zmu_act_h = het ? zmu_het + (size_t)N * B : zmu_act;
+  double2* amu_act_h = het ? zmu_het + 2 * (size_t)N * B : amu_act;
+  double2* zq_act_h = het ? zq_het + (size_t)ntypes * B : zq_act;
+  auto gather_active = [&](int Bact, bool with_amu) {
+    CU(px::launch_gather_shifts(het ? zq_het : zq_all, zmu_src, n_dip_types, B, act, Bact, zq_act_h,
+                                zmu_act_h, with_amu ? amu_act_h : nullptr, s, &nl));
+    if (het) {
+      CU(px::launch_gather_rows(zq_het, ntypes, B, act, Bact, zq_act_h, s, &nl));
+      CU(px::launch_gather_rows(kap_all, ntypes * ntypes, B, act, Bact, kap_act, s, &nl));
+    }
+  };
 
   // ---- Krylov workspace for up to B active columns
   px::KrylovArgs A{};
@@ -601,18 +685,18 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   A.y = yv; A.u = yv + (size_t)m * B;
   A.active_count = h->d_active;
   A.N = N;
-  A.type = d.type;
-  A.amu = amu_act;
+  A.type = dip_type;
+  A.amu = amu_act ? amu_act_h : nullptr;
 
   std::vector<int> h_outer(B), h_inner(B), h_iters(B);
-  std::vector<double> h_col(3 * (size_t)B), h_bnorm(P);
-  CU(cudaMemcpyAsync(h_bnorm.data(), bnorm, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+  std::vector<double> h_col(3 * (size_t)B), h_bn(B);
+  CU(cudaMemcpyAsync(h_bn.data(), bn, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   sync_stream(h, s);
   // a column whose right-hand side is zero (e.g. no bond has a component along the
   // field) has the exact solution x = 0 and needs no iteration
   int Bout = 0;
   for (int c = 0; c < B; ++c)
-    if (h_bnorm[c % P] > 0.0) h_outer[Bout++] = c;
+    if (h_bn[c] > 0.0) h_outer[Bout++] = c;
 
   size_t prof_k = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> mv_events, rs_events, sk_events;
@@ -649,7 +733,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           8 * BgMax,                                         // target
           4 * BgMax,                                         // jconv
           4 * m,                                             // active
-          16 * m * BgMax};                                   // y
+          16 * m * BgMax,                                    // y
+          4 * 2 * (size_t)NPmax * np};                       // planar matvec operand
       for (size_t b : sizes) {
         if (ptrs) ptrs->push_back(base + t);
         t += round_up(std::max<size_t>(b, 1), 256);
@@ -703,13 +788,14 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       G.target = static_cast<double*>(pp[14]);
       G.jconv = static_cast<int*>(pp[15]);
       G.active = static_cast<int*>(pp[16]);
+      G.np = np;
+      G.vp = static_cast<float*>(pp[18]);
       const int NP = G.NP;
       CU(cudaMemsetAsync(G.active, 0, sizeof(int) * m_sk, s));
       // the least-squares estimate stops a system at half the requested relative residual
       CU(px::launch_sk_start(G, b, bnorm, 0.5 * o.tol_rel, skV, s, &nl));
       int jend = 0;
       for (int j = 0; j < m; ++j) {
-        const float2* vj = skV + (size_t)j * nu * NP;
         float2* Uj = skU + (size_t)j * nu * NP;
         cudaEvent_t e0v = nullptr, e1v = nullptr;
         if (o.profile) {
@@ -717,12 +803,12 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           e1v = pool_event(h, prof_k++);
           CU(cudaEventRecord(e0v, s));
         }
-        CU(px::launch_sk_matvec(d.Tffh, d.Tffl, nu, np, NP, plan, vj, skPart, Uj, s, &nl));
+        CU(px::launch_sk_matvec(d.Tffh, d.Tffl, nu, np, NP, plan, G.vp, skPart, Uj, s, &nl));
         if (o.profile) {
           CU(cudaEventRecord(e1v, s));
           sk_events.push_back({e0v, e1v});
         }
-        CU(px::launch_sk_kbar(nu, NP, d.rowptr, d.col, d.val64, Uj, skW, s, &nl));
+        CU(px::launch_sk_kbar(nu, NP, d.rowptr, d.col, d.val64, d.val32, Uj, skW, s, &nl));
         // two classical Gram-Schmidt passes (CGS2): every frequency shares this basis
         for (int pass = 0; pass < 2; ++pass)
           CU(px::launch_sk_gs_pass(skV, skW, nu, NP, j, m + 1, skDpart,
@@ -751,15 +837,14 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       std::vector<int> all(B);
       for (int c = 0; c < B; ++c) all[c] = c;
       CU(cudaMemcpyAsync(act, all.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
-      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, B, zq_act, zmu_act, nullptr, s,
-                                  &nl));
+      gather_active(B, false);
       px::ResidArgs ra{};
       ra.nu = nu; ra.N = N; ra.model = model; ra.Bact = B; ra.P = P; ra.B = B; ra.nblk = nblk;
       ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = d.type;
       ra.Y = Y64; ra.ldy = ldx; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act; ra.zmu = zmu_act;
       ra.R = r; ra.normpart = normpart;
       CU(px::launch_resid(ra, s, &nl));
-      CU(px::launch_norm_finish(normpart, nblk, B, act, P, bnorm, inner_tol, tol_abs_frac, rnorm,
+      CU(px::launch_norm_finish(normpart, nblk, B, act, B, bn, inner_tol, tol_abs_frac, rnorm,
                                 beta, target_all, s, &nl));
       CU(cudaEventRecord(h->ev_sk[1], s));
       CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
@@ -773,8 +858,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       for (int k = 0; k < Bout; ++k) {
         const int c = h_outer[k];
         if (!std::isfinite(h_col[c])) throw PxError{PX_ECUDA, "non-finite residual after the shifted solve"};
-        worst = std::max(worst, h_col[c] / h_bnorm[c % P]);
-        if (h_col[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
+        worst = std::max(worst, h_col[c] / h_bn[c]);
+        if (h_col[c] > o.tol_rel * h_bn[c] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
       }
       if (h->verbose)
         std::fprintf(stderr, "px: shifted phase true residual: max rel %.3e, %d of %d columns left\n",
@@ -792,8 +877,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       ++total_cycles;
       const int Bact = Bin;
       CU(cudaMemcpyAsync(act, h_inner.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
-      CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, amu_act,
-                                  s, &nl));
+      gather_active(Bact, amu_act != nullptr);
       A.Bact = Bact;
       // restart length of this cycle: the work space holds (m+1) basis vectors of B
       // columns, so a shrunken active set runs a longer restart (up to kMaxRestart)
@@ -812,8 +896,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
                                 lowp ? nullptr : X64, ldxa, s, &nl));
       px::ShiftArgs sa{};
       sa.nu = nu; sa.N = N; sa.model = model; sa.Bact = Bact; sa.nblk = nblk; sa.basis = A.basis;
-      sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = d.type;
-      sa.zq = zq_act; sa.zmu = zmu_act;
+      sa.rowptr = d.rowptr; sa.col = d.col; sa.val64 = d.val64; sa.val32 = d.val32; sa.type = dip_type;
+      sa.zq = zq_act_h; sa.zmu = zmu_act_h;
+      sa.qtype = het ? d.type : nullptr; sa.ntypes = ntypes; sa.kappa = het ? kap_act : nullptr;
       sa.Y = lowp ? (const void*)Y32 : (const void*)Y64;
       sa.ldy = ldxa;
       sa.y_is_f32 = lowp;
@@ -838,7 +923,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           e1v = pool_event(h, prof_k++);
           CU(cudaEventRecord(e0v, q));
         }
-        if (d.matfree) {
+        if (d.matfree && model == PX_WFQFMU) {
+          if (lowp) CU(px::launch_sgemm_mf4(d.pos4f, d.rm2f, N, d.mu_self, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
+          else CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
+        } else if (d.matfree) {
           if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
         } else if (tc) {
@@ -993,8 +1081,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     const int Bact = Bout;
     const int ldxa = (int)round_up(2 * (size_t)Bact, colpad);
     CU(cudaMemcpyAsync(act, h_outer.data(), sizeof(int) * Bact, cudaMemcpyHostToDevice, s));
-    CU(px::launch_gather_shifts(zq_all, zmu_all, ntypes, B, act, Bact, zq_act, zmu_act, nullptr,
-                                s, &nl));
+    gather_active(Bact, false);
     CU(cudaMemsetAsync(X64, 0, sizeof(double) * (size_t)np * ldxa, s));
     CU(px::launch_gather_x(x, B, act, Bact, nu, X64, ldxa, s, &nl));
     cudaEvent_t r0e = nullptr, r1e = nullptr;
@@ -1003,7 +1090,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       r1e = pool_event(h, prof_k++);
       CU(cudaEventRecord(r0e, s));
     }
-    if (d.matfree) {
+    if (d.matfree && model == PX_WFQFMU) {
+      CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    } else if (d.matfree) {
       CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
     } else if (2 * Bact <= 8) {
       CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
@@ -1024,11 +1113,14 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     if (h->verbose) std::fprintf(stderr, "px: round %d true residual of %d columns\n", round, Bact);
     px::ResidArgs ra{};
     ra.nu = nu; ra.N = N; ra.model = model; ra.Bact = Bact; ra.P = P; ra.B = B; ra.nblk = nblk;
-    ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = d.type;
-    ra.Y = Y64; ra.ldy = ldxa; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act; ra.zmu = zmu_act;
+    ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = dip_type;
+    ra.Y = Y64; ra.ldy = ldxa; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act_h; ra.zmu = zmu_act_h;
     ra.R = r; ra.normpart = normpart;
+    ra.qtype = het ? d.type : nullptr; ra.ntypes = ntypes; ra.kappa = het ? kap_act : nullptr;
+    ra.bc = bc;
     CU(px::launch_resid(ra, s, &nl));
-    CU(px::launch_norm_finish(normpart, nblk, Bact, act, P, bnorm, inner_tol, tol_abs_frac, rnorm,
+    // per-column norms: bn indexed as [c % B]
+    CU(px::launch_norm_finish(normpart, nblk, Bact, act, B, bn, inner_tol, tol_abs_frac, rnorm,
                               beta, target_all, s, &nl));
     CU(cudaMemcpyAsync(h_col.data(), colv, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h_iters.data(), iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
@@ -1038,8 +1130,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     for (int k = 0; k < Bout; ++k) {
       const int c = h_outer[k];
       if (!std::isfinite(h_col[c])) throw PxError{PX_ECUDA, "non-finite residual"};
-      worst = std::max(worst, h_col[c] / h_bnorm[c % P]);
-      if (h_col[c] > o.tol_rel * h_bnorm[c % P] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
+      worst = std::max(worst, h_col[c] / h_bn[c]);
+      if (h_col[c] > o.tol_rel * h_bn[c] && h_iters[c] < o.max_iter) h_outer[nb++] = c;
     }
     if (h->verbose)
       std::fprintf(stderr, "px: round %d true residual: max rel %.3e over %d columns, %d left\n",
@@ -1052,7 +1144,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   CU(px::launch_observables(N, model, F, P, d.pos64, d.perm, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
                             so->d_mu, so->d_sigma_pol, so->d_sigma, have_triple ? pol_inv : nullptr,
                             s, &nl));
-  if (so->d_relres) CU(px::launch_relres(rnorm, bnorm, B, P, so->d_relres, s, &nl));
+  if (so->d_relres) CU(px::launch_relres(rnorm, bn, B, B, so->d_relres, s, &nl));
   std::vector<double> h_rnorm(B);
   int h_err = 0;
   CU(cudaMemcpyAsync(&h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1085,7 +1177,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   so->status.resize(B);
   px_status ret = PX_OK;
   for (int c = 0; c < B; ++c) {
-    so->relres[c] = h_bnorm[c % P] > 0.0 ? h_rnorm[c] / h_bnorm[c % P] : 0.0;
+    so->relres[c] = h_bn[c] > 0.0 ? h_rnorm[c] / h_bn[c] : 0.0;
     so->iters[c] = h_iters[c];
     so->status[c] = so->relres[c] <= o.tol_rel ? PX_OK : PX_ENOTCONV;
     if (so->status[c] != PX_OK) ret = PX_ENOTCONV;

@@ -51,6 +51,9 @@ struct DevStructure {
   float* Tffl = nullptr;       //   low-precision modes): T = Tffh + Tffl
   float4* pos4f = nullptr;     // matrix-free: x, y, z, R_q^2 (FP32)
   double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
+  float* rm2f = nullptr;       // matrix-free wFQFmu: R_mu^2 (FP32)
+  double* rm2d = nullptr;      // matrix-free wFQFmu: R_mu^2 (FP64)
+  int mu_self = 0;             // Gaussian self term on the T^mumu diagonal (options at set-up)
   bool matfree = false;
   int* perm = nullptr;         // [N] caller's index of internal (Morton-sorted) atom i
   // tensor-core planes Thi / Tlo hold M = diag(Kbar, I) T (split-precision modes), fp16
@@ -61,6 +64,12 @@ struct DevStructure {
   uint16_t* Thi = nullptr;     // hi part of M: bf16, or fp16 of 2^e M (e = op_scale_exp)
   uint16_t* Tlo = nullptr;     // lo part of M: bf16, or fp16 of (2^e M - hi) 2^11
   bool t_f16 = false;          // the split planes are fp16 (else bf16)
+  // heterogeneous wFQFmu (Eqs. 9-10; model stays 1): per-type Drude parameters and the
+  // nearest-neighbour counts of Eq. 10
+  bool hetero = false;
+  double* tpar = nullptr;      // [ntypes][3] n, tau, area of each type
+  int* nncnt = nullptr;        // [N][ntypes] nearest neighbours of each type (r <= s r0)
+  int* ident = nullptr;        // [N] 0..N-1: per-atom indexing of the dipole shifts
 };
 
 // ---------------------------------------------------------------- launch wrappers
@@ -127,7 +136,15 @@ cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, in
                             int ldy, int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm_mf(const double* pos4, int n, int np, const double* X, int ldx,
                             double* Y, int ldy, int ncols, cudaStream_t s, long long* nl);
-// pos4f / pos4d of a structure from pos64 and R_q.
+// wFQFmu matrix-free matvecs: the 4 x 4 blocks of T (Sec. 2.2) generated per atom pair;
+// rows in the charges-first order of the unknowns; unknown rows of Y beyond 4N untouched.
+cudaError_t launch_sgemm_mf4(const float4* pos, const float* rm2, int N, int mu_self,
+                             const float* X, int ldx, float* Y, int ldy, int ncols, cudaStream_t s,
+                             long long* nl);
+cudaError_t launch_dgemm_mf4(const double* pos4, const double* rm2, int N, int mu_self,
+                             const double* X, int ldx, double* Y, int ldy, int ncols,
+                             cudaStream_t s, long long* nl);
+// pos4f / pos4d (and rm2f / rm2d when set) of a structure from pos64, R_q and R_mu.
 cudaError_t launch_stage_pos4(const DevStructure& d, cudaStream_t s, long long* nl);
 // FP64 matvec for nc <= 8 real operand columns (bandwidth/FP64-pipe bound GEMV).
 cudaError_t launch_dgemv(const double* T, int np, const double* X, int ldx, double* Y, int ldy,
@@ -217,6 +234,10 @@ struct ShiftArgs {
   const int* jdev;                              // set: X is V_0 and the step is *jdev
   int kbar_in_y;                                // 1: Y = M X already holds Kbar T X
   float yscale;                                 // power of two applied to Y (kbar_in_y)
+  // heterogeneous wFQFmu (Eq. 9): charge rows use z_q of their atom's type (zq [ntypes][Bact]
+  // indexed by qtype) and the complex bond weights K_ij kappa[t_i][t_j][col] of
+  // 1/2 (Kbar + Hbar(w)); null for the homogeneous models
+  const int* qtype; int ntypes; const double2* kappa;
 };
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s, long long* nl);
 
@@ -229,8 +250,36 @@ struct ResidArgs {
   const double2* x; const int* act; const double* b;
   const double2* zq; const double2* zmu;
   double2* R; double* normpart;
+  // heterogeneous wFQFmu: as in ShiftArgs, plus the complex right-hand side of every
+  // column bc [nu][B] (replaces b)
+  const int* qtype; int ntypes; const double2* kappa; const double2* bc;
 };
 cudaError_t launch_resid(const ResidArgs& a, cudaStream_t s, long long* nl);
+
+// ---- heterogeneous wFQFmu (Eqs. 9-10)
+// nn[i][t] = atoms of type t within the Fermi midpoint s_ij r0_ij of atom i (Eq. 10's
+// nearest neighbours), from the CSR rows and positions; ident[i] = i.
+cudaError_t launch_nn_counts(const double* pos, int N, const int* type, int ntypes,
+                             const double* r0t, const double* st, const int* rowptr,
+                             const int* col, int* nn, int* ident, cudaStream_t s, long long* nl);
+// Per-column tables: zq[t][c] = z_q of type t (Eq. 6 with the type's n, tau),
+// kappa[t][u][c] = 1/2 (1 + rho_tu(w) A_u / A_t) with rho_tu = (n_u tau_u)/(n_t tau_t)
+// (1 - i w tau_t)/(1 - i w tau_u) (the weight of bond t -> u in 1/2 (Kbar + Hbar), Eq. 9),
+// zmu_atom[i][c] = z_mu of atom i: the Eq. 10 weighted mean of the types' z_mu[t][c]
+// (weights nn[i][t] + [t == type_i]).  tpar [ntypes][3] = n, tau, area.
+cudaError_t launch_hetero_tables(int F, int P, int ntypes, int N, const double* omega_ev,
+                                 const double* tpar, const int* type, const int* nn,
+                                 const double2* zmu_type, double2* zq, double2* kappa,
+                                 double2* zmu_atom, cudaStream_t s, long long* nl);
+// Complex right-hand side of Eq. 9 per column, bc[i][c] = (diag(C(w), I) (-V; E))_i, and
+// per-column norms bn[c].
+cudaError_t launch_rhs_hetero(int N, int F, int P, const int* rowptr, const int* col,
+                              const double* val64, const int* type, int ntypes,
+                              const double2* kappa, const double* pos, const double* pol,
+                              double e0, double2* bc, double* bn, cudaStream_t s, long long* nl);
+// out[t][a] = in[t][act[a]] for t < rows
+cudaError_t launch_gather_rows(const double2* in, int rows, int B, const int* act, int Bact,
+                               double2* out, cudaStream_t s, long long* nl);
 
 // RHS b[i][p] (real): -Kbar V for charge rows, E0 e_p for dipole rows.
 cudaError_t launch_rhs(int nu, int N, int model, const int* rowptr, const int* col,
@@ -291,6 +340,14 @@ cudaError_t launch_init_residual(const double* b, int nu, int P, int B, const do
                                  double inner_tol, double tol_abs_frac, double2* r,
                                  double* rnorm, double* beta, double* target_all, cudaStream_t s,
                                  long long* nl);
+// The same from a per-column complex right-hand side bc [nu][B] with norms bn [B].
+cudaError_t launch_init_residual_c(const double2* bc, int nu, int B, const double* bn,
+                                   double inner_tol, double tol_abs_frac, double2* r,
+                                   double* rnorm, double* beta, double* target_all, cudaStream_t s,
+                                   long long* nl);
+// bn[c] = bnorm[c % P]: per-column right-hand-side norms of the real right-hand sides.
+cudaError_t launch_bnorm_cols(const double* bnorm, int P, int B, double* bn, cudaStream_t s,
+                              long long* nl);
 cudaError_t launch_relres(const double* rnorm, const double* bnorm, int B, int P, double* out,
                           cudaStream_t s, long long* nl);
 
@@ -323,6 +380,8 @@ struct SkMatvecPlan {
 SkMatvecPlan sk_matvec_plan(int np);
 struct SkGroup {
   int n = 0, NP = 0, P = 0, p0 = 0, Bg = 0, m = 0;   // m: largest basis (Krylov steps)
+  int np = 0;                 // n rounded up to 128
+  float* vp = nullptr;        // [2 NP][np] the current basis vector, planar hi / lo (matvec operand)
   double* H = nullptr;        // [m][m+2][NP] Hessenberg columns
   double* inv_h = nullptr;    // [NP] scale of the next basis vector (0: invariant subspace)
   const double2* zq = nullptr;  // [B] z_q of every global column
@@ -335,14 +394,16 @@ struct SkGroup {
   int* jconv = nullptr;       // [Bg] 0 iterating, > 0 basis size at stop, -1 zero rhs
   int* active = nullptr;      // [m] systems still iterating after step j
 };
-// U = T v in double-FP32 (T = Th + Tl planes [np][np]; v, U [n][NP] float2), via partial
-// products over column segments (part [S][np][NP]).
+// U = T v in double-FP32 (T = Th + Tl planes [np][np]; v as planar hi / lo rows vp [2 NP][np],
+// zero beyond n; U [n][NP] float2), via partial products over column segments
+// (part [S][np][NP]).
 cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, int NP,
-                             const SkMatvecPlan& pl, const float2* v, float2* part, float2* U,
+                             const SkMatvecPlan& pl, const float* vp, float2* part, float2* U,
                              cudaStream_t s, long long* nl);
-// W = Kbar U (Eq. 2), FP64 arithmetic.
+// W = Kbar U (Eq. 2), double-FP32 arithmetic (K = val64 split as val32 + remainder).
 cudaError_t launch_sk_kbar(int n, int NP, const int* rowptr, const int* col, const double* val,
-                           const float2* U, float2* W, cudaStream_t s, long long* nl);
+                           const float* val32, const float2* U, float2* W, cudaStream_t s,
+                           long long* nl);
 int sk_row_blocks(int n);        // row blocks of the projection kernel (dpart rows)
 int sk_update_chunks(int m);     // basis-vector chunks of the update kernel (upart rows)
 // One classical Gram-Schmidt pass against V_0..V_j: h = V^T W (dpart [nrb][m1][NP] partials,

@@ -119,6 +119,8 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
   const px::DevStructure* dsp = px_structure(h);
   if (!dsp) return fail_h(h, PX_EINVAL, "no structure loaded");
   const px::DevStructure& d = *dsp;
+  if (d.hetero)
+    return fail_h(h, PX_ENOTIMPL, "px_relres_device_noalloc does not cover PX_WFQFMU_HETERO");
   if (n_freq < 1 || n_pol < 1 || !omega_ev || !pol_dir || !d_q || !d_relres)
     return fail_h(h, PX_EINVAL, "need n_freq, n_pol >= 1, omega_ev, pol_dir, d_q and d_relres");
   if (d.model == PX_WFQFMU && (!alpha_ib || !d_mu))
@@ -217,7 +219,9 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
       N, model, B, d.perm, reinterpret_cast<const double2*>(d_q), reinterpret_cast<const double2*>(d_mu), x,
       X, ldx);
   NA_CU(cudaGetLastError());
-  if (d.matfree) NA_CU(px::launch_dgemm_mf(d.pos4d, N, np, X, ldx, Y, ldx, ldx, s, &nl));
+  if (d.matfree && model == PX_WFQFMU)
+    NA_CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X, ldx, Y, ldx, ldx, s, &nl));
+  else if (d.matfree) NA_CU(px::launch_dgemm_mf(d.pos4d, N, np, X, ldx, Y, ldx, ldx, s, &nl));
   else if (2 * B <= 8) NA_CU(px::launch_dgemv(d.T64, np, X, ldx, Y, ldx, 2 * B, s, &nl));
   else NA_CU(px::launch_dgemm(d.T64, np, X, ldx, Y, ldx, ldx, s, &nl));
   px::ResidArgs ra{};

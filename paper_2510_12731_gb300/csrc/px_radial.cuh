@@ -1,0 +1,43 @@
+// Radial functions of the Gaussian kernel of Eq. 5 and its derivatives (Sec. 2.2):
+//   G(r) = erf(r/R)/r,   G'(r)/r,   G''(r)   (and the normalised Gaussian g(r; R))
+// For x = r/R below 0.25 the closed forms cancel (G' and G'' are O(x) and O(1) differences
+// of O(1/x) terms), so a Taylor series of erf is used there:
+//   G    = c (1 - x^2/3 + x^4/10 - x^6/42)
+//   G'/r = (c/R^2)(-2/3 + 2x^2/5 - x^4/7 + x^6/27)
+//   G''  = (c/R^2)(-2/3 + 6x^2/5 - 5x^4/7 + 7x^6/27),      c = 2 / (sqrt(pi) R)
+// (the next terms are below 3e-7 relative at x = 0.25).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace px {
+namespace radial {
+
+constexpr float kInvSqrtPiF = 0.56418958354775628f;
+
+__device__ __forceinline__ void eval_f(float r, float R, float& G, float& G1r, float& G2,
+                                       float& g) {
+  const float iR = 1.0f / R;
+  const float x = r * iR;
+  const float x2 = x * x;
+  const float ex = __expf(-x2);
+  const float c = 2.0f * kInvSqrtPiF * iR;
+  g = kInvSqrtPiF * kInvSqrtPiF * kInvSqrtPiF * iR * iR * iR * ex;
+  if (x < 0.25f) {
+    const float x4 = x2 * x2, x6 = x4 * x2;
+    G = c * (1.0f - x2 * (1.0f / 3.0f) + x4 * 0.1f - x6 * (1.0f / 42.0f));
+    const float cr = c * iR * iR;
+    G1r = cr * (-2.0f / 3.0f + 0.4f * x2 - x4 * (1.0f / 7.0f) + x6 * (1.0f / 27.0f));
+    G2 = cr * (-2.0f / 3.0f + 1.2f * x2 - x4 * (5.0f / 7.0f) + x6 * (7.0f / 27.0f));
+  } else {
+    const float e = erff(x);
+    const float ir = 1.0f / r;
+    const float gx = 2.0f * kInvSqrtPiF * ex;   // d erf / dx
+    G = e * ir;
+    const float G1 = (gx * iR - e * ir) * ir;   // G'(r)
+    G1r = G1 * ir;
+    G2 = (-2.0f * x * gx * iR * iR - 2.0f * gx * iR * ir + 2.0f * e * ir * ir) * ir;
+  }
+}
+
+}  // namespace radial
+}  // namespace px

@@ -70,7 +70,7 @@ size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 // Device bytes a solve of this request needs on a fresh handle (operators + Krylov
 // work space), for materialised (mat) or on-the-fly operators.
 size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
-  const size_t nu = model == PX_WFQ ? N : 4 * (size_t)N;
+  const size_t nu = model == PX_WFQ ? N : 4 * (size_t)N;   // wFQFmu and its heterogeneous form
   const size_t np = round_up(nu, 128);
   const size_t ldx = round_up(2 * (size_t)B, 256);
   const size_t m = o.restart_m > 0 ? o.restart_m
@@ -258,7 +258,7 @@ px_status copy_out(const Req* r, px_result* out) {
   if (out->sigma_abs && P == 3) cp(out->sigma_abs, r->sigma);
   cp(out->sigma_abs_pol, r->sigma_pol);
   cp(out->q, r->q);
-  if (out->mu && r->model == PX_WFQFMU) cp(out->mu, r->mu);
+  if (out->mu && r->model != PX_WFQ) cp(out->mu, r->mu);
   cp(out->rel_residual, r->relres);
   if (out->iters) std::memcpy(out->iters, r->iters.data(), F * P * sizeof(int));
   if (out->status) std::memcpy(out->status, r->status.data(), F * P * sizeof(int));
@@ -302,10 +302,10 @@ px_status px_server_create(px_server** out, const px_options* opt, int max_slots
 
 px_status px_submit(px_server* s, const px_request* r, uint64_t* req_id) {
   if (!s || !r || !req_id) return PX_EINVAL;
-  if (r->model != PX_WFQ && r->model != PX_WFQFMU) return PX_EINVAL;
+  if (r->model != PX_WFQ && r->model != PX_WFQFMU && r->model != PX_WFQFMU_HETERO) return PX_EINVAL;
   if (r->n_atoms < 1 || r->n_types < 1 || r->n_freq < 1 || r->n_pol < 1) return PX_EINVAL;
   if (!r->xyz_ang || !r->type_idx || !r->types || !r->omega_ev || !r->pol_dir) return PX_EINVAL;
-  if (r->model == PX_WFQFMU && !r->alpha_ib) return PX_EINVAL;
+  if (r->model != PX_WFQ && !r->alpha_ib) return PX_EINVAL;
   Req* q = new (std::nothrow) Req();
   if (!q) return PX_ENOMEM;
   q->model = r->model;
@@ -319,7 +319,7 @@ px_status px_submit(px_server* s, const px_request* r, uint64_t* req_id) {
   q->types.assign(r->types, r->types + r->n_types);
   q->omega.assign(r->omega_ev, r->omega_ev + r->n_freq);
   q->pol.assign(r->pol_dir, r->pol_dir + 3 * (size_t)r->n_pol);
-  if (r->model == PX_WFQFMU) q->aib.assign(r->alpha_ib, r->alpha_ib + 2 * (size_t)r->n_types * r->n_freq);
+  if (r->model != PX_WFQ) q->aib.assign(r->alpha_ib, r->alpha_ib + 2 * (size_t)r->n_types * r->n_freq);
   const size_t B = (size_t)q->F * q->P, N = q->N;
   // materialised operators when they fit a share of the budget, else on the fly (wFQ)
   const size_t fmat = footprint(s->opt, q->model, q->N, (int)B, true);
@@ -348,7 +348,7 @@ px_status px_submit(px_server* s, const px_request* r, uint64_t* req_id) {
   q->sigma.resize(q->F);
   q->sigma_pol.resize(B);
   q->q.resize(2 * B * N);
-  if (q->model == PX_WFQFMU) q->mu.resize(6 * B * N);
+  if (q->model != PX_WFQ) q->mu.resize(6 * B * N);
   q->relres.resize(B);
   q->iters.resize(B);
   q->status.resize(B);

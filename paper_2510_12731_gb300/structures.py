@@ -347,3 +347,27 @@ def serving_check_mix() -> list:
         out.append(_one_element(f"{el_name}_{shape}_{len(xyz)}_{model}", el, model, xyz,
                                 np.linspace(lo, hi, nf), pols, tol=1e-7))
     return out
+
+
+def alloy_sphere(radius=17.5, frac_au=0.5, seed=12731, nfreq=251, wmin=2.0, wmax=5.0,
+                 pols=XYZ, au_overrides=None) -> Workload:
+    """Heterogeneous wFQFmu (Eqs. 9-10): an Ag/Au alloy sphere on the Ag fcc lattice
+    (a = 4.09 A); radius 17.5 A (diameter 3.5 nm) gives 1,289 atoms.  A seeded random
+    fraction frac_au of the sites (numpy PCG64, ``seed``) carries Au.  Types: Ag, Au with
+    their stand-in parameters (``au_overrides`` may replace Au entries, e.g. n or tau);
+    alpha^IB per type."""
+    xyz = sphere("fcc", 4.09, radius)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_au = int(round(frac_au * len(xyz)))
+    tidx = np.zeros(len(xyz), dtype=np.int32)
+    if n_au:
+        tidx[rng.choice(len(xyz), size=n_au, replace=False)] = 1
+    ag, au = ELEMENTS["Ag"], ELEMENTS["Au"]
+    t_au = au.atom_type()
+    if au_overrides:
+        t_au.update(au_overrides)
+    w = np.linspace(wmin, wmax, nfreq)
+    aib = np.stack([ag.alpha_ib(w), au.alpha_ib(w)])
+    return Workload(f"agau_sphere_r{radius:g}A_au{frac_au:g}_wfqfmu_hetero", "wfqfmu_hetero", xyz,
+                    tidx, [ag.atom_type(), t_au], w, np.asarray(pols, dtype=np.float64), aib,
+                    precision="fp32", tol=1e-7)

@@ -6,7 +6,8 @@ files.  Routes:
   * wFQ workloads: the exact spectral route (Cholesky of T, symmetric eigensolve) gives
     every (frequency, polarisation) column;
   * the wFQFmu rod: one dense LU per sampled frequency (lowest, middle, highest);
-  * the fixed serving check mix: each request by the route of its model.
+  * the fixed serving check mix: each request by the route of its model;
+  * the 1,289-atom Ag/Au alloy sphere (Eqs. 9-10): dense LU at three frequencies.
 Run:  python tests/golden/make_golden.py [name ...]   (a few minutes to ~30 min each).
 """
 import os
@@ -68,12 +69,24 @@ def serving_check():
             lu_sample(name, w)
 
 
+def alloy_lu(name, w, n_samples=3):
+    """Heterogeneous wFQFmu (Eqs. 9-10) by the oracle's dense LU at sampled frequencies."""
+    from oracle import hetero as HT
+    idx = np.unique(np.linspace(0, w.omega_ev.size - 1, n_samples).round().astype(int))
+    t = time.time()
+    alpha, _, _, rel = HT.solve(w.xyz_ang, w.type_idx, w.types, w.omega_ev[idx], w.pol_dirs,
+                                w.alpha_ib[:, idx])
+    print(name, "LU", round(time.time() - t, 1), "s, max rel residual", rel.max(), flush=True)
+    _write(name, w, idx, alpha, f"dense LU of Eq. 9 at frequency indices {idx.tolist()}")
+
+
 JOBS = {
     "graphene_disk_20nm": lambda: spectral_workload("graphene_disk_20nm", S.graphene_disk_20nm()),
     "na_icosahedron_19931": lambda: spectral_workload("na_icosahedron_19931",
                                                       S.na_icosahedron_19931()),
     "ag_rod_3x3x10": lambda: lu_sample("ag_rod_3x3x10", S.ag_rod_3x3x10()),
     "serving_check": serving_check,
+    "agau_sphere_1289": lambda: alloy_lu("agau_sphere_1289", S.alloy_sphere()),
 }
 
 if __name__ == "__main__":

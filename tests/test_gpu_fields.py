@@ -14,8 +14,8 @@ from paper_2510_12731_gb300 import structures as S
 pytestmark = pytest.mark.gpu
 
 
-def _grid(xyz_ang, n=9, pad=4.0, z=None):
-    lo, hi = xyz_ang.min(axis=0) - pad, xyz_ang.max(axis=0) + pad
+def _grid(xyz_ang, n=9, pad=4.0, z=None, shift=0.0):
+    lo, hi = xyz_ang.min(axis=0) - pad + shift, xyz_ang.max(axis=0) + pad + shift
     ax = [np.linspace(lo[k], hi[k], n) for k in range(3)]
     if z is not None:
         ax[2] = np.array([z])
@@ -55,8 +55,8 @@ def test_maps_match_oracle_on_seeded_charges(model):
     N, C = w.natoms, 3
     q = rng.normal(size=(C, N)) + 1j * rng.normal(size=(C, N))
     mu = (rng.normal(size=(C, N, 3)) + 1j * rng.normal(size=(C, N, 3))) if model == "wfqfmu" else None
-    pts = _grid(w.xyz_ang)
-    rho, phi, E = _maps(w, pts, q, mu)
+    pts = _grid(w.xyz_ang, shift=0.37)          # off the atom centres (the oracle's field
+    rho, phi, E = _maps(w, pts, q, mu)          # is undefined there)
     st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
     pb = pts / M.BOHR_ANG
     for c in range(C):

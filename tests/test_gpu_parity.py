@@ -436,12 +436,44 @@ def test_matfree_matches_materialised_on_multi_tile_sphere():
         assert np.max(num / np.linalg.norm(a_ref, axis=1)) <= 1e-5
 
 
-def test_matfree_wfqfmu_is_not_implemented():
-    from paper_2510_12731_gb300 import PxError
-    w = S.small_cluster(element="Ag", radius=6.0, model="wfqfmu", nfreq=2)
-    with _solver(mode="matfree") as s:
-        with pytest.raises(PxError, match="ENOTIMPL"):
-            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+@pytest.mark.parametrize("precision,tol,alpha_tol", [("fp32", 1e-9, 1e-7), ("fp64", 1e-10, 1e-8)])
+def test_matfree_wfqfmu_parity(precision, tol, alpha_tol):
+    """wFQFmu with every 4 x 4 block of T^qq / T^qmu / T^muq / T^mumu generated inside the
+    matvec (Sec. 2.2): Ag sphere r = 9 A, N = 177 (6 tiles of 32 atoms, the last ragged;
+    K steps of 4 atoms, the last ragged)."""
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfqfmu", nfreq=5, wmin=2.5, wmax=5.0)
+    assert w.natoms % 32 and w.natoms % 4
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision=precision, tol_rel=tol, mode="matfree")
+    assert stats["used_mode"] == 1 and out["ok"]
+    assert _alpha_err(out, ref) <= alpha_tol
+    assert np.abs(out["mu"] - ref.mu).max() <= 1e2 * alpha_tol * np.abs(ref.mu).max()
+
+
+def test_matfree_wfqfmu_unequal_widths_and_self_term():
+    """R_mu != R_q (four distinct pair widths per block) and the Gaussian dipole self
+    term on the T^mumu diagonal: matrix-free against the oracle."""
+    w = S.small_cluster(element="Au", radius=8.0, model="wfqfmu", nfreq=4, wmin=2.5, wmax=5.0)
+    w.types = [{**w.types[0], "Rmu_bohr": 0.8 * w.types[0]["Rq_bohr"]}]
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    ref = M.solve(st, w.model, w.omega_ev, w.pol_dirs, alpha_ib=w.alpha_ib, mu_self_term=True)
+    out, _ = _run(w, precision="fp32", tol_rel=1e-9, mode="matfree", mu_self_term=1)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-7
+
+
+def test_matfree_wfqfmu_matches_materialised_rod():
+    """Ag rod 18 x 18 x 54 A (N = 1,093: 35 atom tiles, ragged) at 12 frequencies x 3
+    directions: on the fly and materialised reach the same refined solution."""
+    el = S.ELEMENTS["Ag"]
+    xyz = S.cuboid("fcc", el.a_ang, 9.0, 9.0, 27.0)
+    w = S.Workload("ag_rod_small", "wfqfmu", xyz, np.zeros(len(xyz), np.int32), [el.atom_type()],
+                   np.linspace(2.5, 5.0, 12), np.eye(3), el.alpha_ib(np.linspace(2.5, 5.0, 12))[None, :])
+    out_mf, _ = _run(w, precision="fp32", tol_rel=1e-9, mode="matfree")
+    out_m, _ = _run(w, precision="fp32", tol_rel=1e-9, mode="materialised")
+    assert out_mf["ok"] and out_m["ok"]
+    num = np.linalg.norm(out_mf["alpha"] - out_m["alpha"], axis=1)
+    assert np.max(num / np.linalg.norm(out_m["alpha"], axis=1)) <= 1e-7
 
 
 def test_wfqfmu_rod_converges_with_dipole_preconditioner():
