@@ -187,7 +187,9 @@ class ClockSampler:
 # (the FP32 GEMM shares its file with the FP64 kernels).  Code outside it does not change
 # what the profiled kernel executes.
 DEVICE_PART_END = {"k_gemm_tc.cu": b"PFN_cuTensorMapEncodeTiled_v12000 encode_fn()"}
-DEVICE_PART_SPAN = {"k_gemm_simt.cu": (b"namespace px {", b"// FP64: BM = BN = 64, BK = 16")}
+DEVICE_PART_SPAN = {"k_gemm_simt.cu": (b"namespace px {", b"// FP64: BM = BN = 64, BK = 16"),
+                    "k_shifted.cu": (b"// ---------------------------------------------------------------- matvec",
+                                     b"// U[i][p] = sum over segments")}
 
 
 def kernel_source_sha(kernel_file):
@@ -303,6 +305,8 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2510_12731_gb300 import Solver
+    if getattr(args, "solver", "batched") == "shifted":
+        return run_shifted_main(args, rank, world, local_rank)
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -337,6 +341,9 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if getattr(args, "profile_run", False):
+        return _profile_step(step_device, solver, wl.name, "batched")
 
     # the clock sampler starts before the warm-up (nvidia-smi's start-up then overlaps the
     # warm-up steps, not the timed ones); only samples inside the timed region are used
@@ -468,6 +475,16 @@ def run_ours(args, rank, world, local_rank):
         shifted = run_shifted_leg(args, wl, nsk, dev, dist, world, d_alpha, d_q, d_rr, pinned,
                                   value)
 
+    # ---- P0, second variant (wFQ, N <= 12,000): one complex LU per frequency of
+    # A(w) = Kbar T - z_q(w) I (cuSOLVER through torch) for every direction at once, on
+    # the operator the library exports; the faster P0 variant is the denominator
+    p0_lu = None
+    if args.p0_cols > 0 and wl.model == "wfq" and N <= 12000:
+        p0_lu = _p0_lu(wl, dev, args.p0_cols)
+    p0_best = p0
+    if p0_lu is not None and (p0 is None or p0_lu["value"] > p0["value"]):
+        p0_best = p0_lu
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, pts = _oracle_sample(wl, args.cpu_freqs)
@@ -492,7 +509,8 @@ def run_ours(args, rank, world, local_rank):
                                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches, "graph_launches_last_step": graph_launches,
             "roofline": {**roofline, "kernel_timing": kernel_timing}, "cpu_baseline": cpu,
-            "p0_fp64_gpu": p0, "vs_p0": (value / world / p0["value"]) if p0 else None,
+            "p0_fp64_gpu": p0, "p0_lu_gpu": p0_lu,
+            "vs_p0": (value / world / p0_best["value"]) if p0_best else None,
             "shifted_krylov": shifted,
             "points_per_step": points_per_step, "iters_per_step": iters / args.steps,
             "wall_s": wall, "step_wall_ms": [round(x, 1) for x in step_wall],
@@ -501,6 +519,65 @@ def run_ours(args, rank, world, local_rank):
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def _p0_lu(wl, dev, nsample):
+    """Plain FP64 direct solve on the GPU: A(w) = A0 - z_q(w) I assembled in complex128 from
+    the library's exported A0 = Kbar T (Eq. 1), one LU with all directions per frequency
+    (torch.linalg.solve: cuSOLVER getrf / getrs); timed on sampled frequencies."""
+    import torch
+    from paper_2510_12731_gb300 import Solver
+    N, P = wl.natoms, wl.pol_dirs.shape[0]
+    A0 = torch.empty((N, N), dtype=torch.float64, device=dev)
+    b = torch.empty((N, P), dtype=torch.float64, device=dev)
+    with Solver(precision="fp64", tol_rel=wl.tol) as s:
+        s.set_structure(wl.model, wl.xyz_ang, wl.type_idx, wl.types)
+        s.system_device(wl.pol_dirs, 1.0, d_A0=A0, d_b=b)
+    n, tau = wl.types[0]["drude_n_au"], wl.types[0]["tau_au"]
+    bc = b.to(torch.complex128)
+    eye = torch.eye(N, dtype=torch.complex128, device=dev)
+    fidx = np.unique(np.linspace(0, wl.omega_ev.size - 1, nsample).round().astype(int))
+
+    def solve_one(fi):
+        w = wl.omega_ev[fi] / 27.211386245988
+        zq = complex(-w * w * tau / (2 * n * tau), -w / (2 * n * tau))   # Eq. 6
+        A = A0.to(torch.complex128) - zq * eye
+        x = torch.linalg.solve(A, bc)
+        rel = (torch.linalg.norm(bc - A @ x, dim=0) / torch.linalg.norm(bc, dim=0)).max()
+        return x, rel
+
+    solve_one(fidx[0])                       # library warm-up (cuSOLVER handles, workspace)
+    torch.cuda.synchronize()
+    t = 0.0
+    worst = 0.0
+    for fi in fidx:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, rel = solve_one(fi)
+        e1.record()
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        worst = max(worst, float(rel))
+    del A0, eye
+    return {"value": len(fidx) * P / t, "unit": UNIT, "frequencies_timed": int(len(fidx)),
+            "max_rel_residual": worst,
+            "sample": f"{len(fidx)} frequencies x {P} directions, complex128 LU per frequency "
+                      "(torch.linalg.solve), A(w) assembled from the exported Kbar T; "
+                      "residual check included"}
+
+
+def _profile_step(step, solver, workload, solver_name):
+    """--profile-run: one step of the path, no warm-up and no timing, for launch lists and
+    counter captures under a profiler.  Prints a line that carries no bench value."""
+    import torch
+    step()
+    torch.cuda.synchronize()
+    st = solver.stats()
+    print(json.dumps({"profile_run": True, "workload": workload, "solver": solver_name,
+                      "kernel_launches": st["kernel_launches"] + st["setup_launches"],
+                      "note": "one untimed step for a profiler; not a bench value"}), flush=True)
     return 0
 
 
@@ -525,6 +602,9 @@ def run_shifted_leg(args, wl, steps, dev, dist, world, d_alpha, d_q, d_rr, pinne
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if getattr(args, "profile_run", False):
+        return _profile_step(step, sk, wl.name, "shifted")
 
     for _ in range(max(3, min(args.warmup, 5))):
         step()
@@ -571,6 +651,8 @@ def run_shifted_leg(args, wl, steps, dev, dist, world, d_alpha, d_q, d_rr, pinne
     hbm = float(peaks["hbm_gbs"])
     avg_s = (mv_ms / mv_n) / 1e3 if mv_n else float("nan")
     achieved = (mv_bytes / mv_n) / avg_s / 1e9 if mv_n else float("nan")
+    ratio = _profile_ratio("k_shifted.cu", "k_sk_matvec_na_sphere_7119.md")
+    traffic = ratio * (mv_bytes / mv_n) if (ratio is not None and mv_n) else None
     h2d = wl.xyz_ang.nbytes + wl.type_idx.nbytes + wl.omega_ev.nbytes + wl.pol_dirs.nbytes + \
         64 * len(wl.types)
     d2h = sum(v.nbytes for k, v in out.items() if isinstance(v, np.ndarray)
@@ -582,7 +664,7 @@ def run_shifted_leg(args, wl, steps, dev, dist, world, d_alpha, d_q, d_rr, pinne
         "e2e": {"value": whole_job_value(pts / e2e_steps, world, e2e_ms / e2e_steps), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "k_sk_matvec (double-FP32 matvec of T's two FP32 planes on one "
                                "column per field direction)",
                      "peak_source": f"STREAM-style copy ({src})",
@@ -591,6 +673,184 @@ def run_shifted_leg(args, wl, steps, dev, dist, world, d_alpha, d_q, d_rr, pinne
                      "kernel_timing": "CUDA events around every shifted matvec over the timed region"},
         "note": "separate mode (Eq. 1: one Krylov space per field direction serves all "
                 "frequencies); not part of the batched-vs-P0 comparison"}
+
+
+def run_shifted_main(args, rank, world, local_rank):
+    """The shifted Krylov solver as the line's own measurement (--solver shifted): the same
+    step, timed as in the shifted leg, with that leg's roofline, e2e and launch count."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = _workload(args.workload)
+    if wl.model != "wfq":
+        raise SystemExit("--solver shifted applies to wFQ workloads")
+    F, P, N = wl.omega_ev.size, wl.pol_dirs.shape[0], wl.natoms
+    dev = torch.device("cuda", local_rank)
+    d_alpha = torch.empty((F, 3, P), dtype=torch.complex128, device=dev)
+    d_q = torch.empty((F, P, N), dtype=torch.complex128, device=dev)
+    d_rr = torch.empty((F, P), dtype=torch.float64, device=dev)
+
+    def pinned(shape, dtype):
+        t = torch.empty(shape, dtype={np.complex128: torch.complex128, np.float64: torch.float64,
+                                      np.int32: torch.int32}[np.dtype(dtype).type], pin_memory=True)
+        return t.numpy()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    sk = run_shifted_leg(args, wl, args.steps, dev, dist, world, d_alpha, d_q, d_rr, pinned, None)
+    clk = clocks.stop(t0, time.perf_counter())
+    if getattr(args, "profile_run", False):
+        return 0
+    if rank == 0:
+        line = {"metric": METRIC, "value": sk["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, min(args.warmup, 5)),
+                "ms_per_step": sk["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32-pair (double-FP32) matvec, basis and "
+                                              "orthogonalisation + f64 least squares",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "natoms": N, "n_unknowns": N, "n_freq": F,
+                           "n_pol": P, "columns": F * P, "tol_rel": wl.tol, "solver": "shifted",
+                           "l2": "no flush: the per-step working set (T planes) is far larger than L2",
+                           "parallelism": f"replicas x{world}"},
+                "clocks": clk, "e2e": sk["e2e"], "gpu_launches": sk["gpu_launches"],
+                "roofline": sk["roofline"], "cpu_baseline": None,
+                "points_per_step": sk["points_per_step"],
+                "krylov_steps_per_step": sk["krylov_steps_per_step"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- boundary elements
+def run_bem(args, rank, world, local_rank):
+    """Boundary-element (DPCM, Eq. 11) sweep: a Drude sphere meshed by --bem-tess tesserae,
+    200 frequencies x (x, y, z).  One step = px_set_mesh (Ft in FP64 and the solver's
+    planes) + px_solve_bem of every column with the results copied to pinned host memory
+    (the host-buffer call is the only one: value and e2e coincide except for the tesserae's
+    charges, which e2e also copies back).  Shifted solver by default (one Krylov space per
+    direction, Lambda(w) as the shift); --solver batched runs the block GMRES."""
+    import torch
+    from paper_2510_12731_gb300 import Solver
+    from paper_2510_12731_gb300 import structures as S
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    wl = S.drude_sphere_mesh(args.bem_tess, nfreq=200)
+    F, P, n = wl.omega_ev.size, wl.pol_dirs.shape[0], wl.pos_ang.shape[0]
+    prec = args.precision or ("fp32" if args.solver == "shifted" else "bf16split")
+    sv = Solver(solver=args.solver, precision=prec, tol_rel=wl.tol, profile=1)
+
+    def pinned(shape, dtype):
+        t = torch.empty(shape, dtype={np.complex128: torch.complex128, np.float64: torch.float64,
+                                      np.int32: torch.int32}[np.dtype(dtype).type], pin_memory=True)
+        return t.numpy()
+
+    sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang)
+    out_small = sv.alloc_outputs(F, P, want_q=False, want_mu=False, empty=pinned)
+    out_full = sv.alloc_outputs(F, P, want_q=True, want_mu=False, empty=pinned)
+
+    def step(out):
+        sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang)
+        return sv.solve_bem(wl.omega_ev, wl.eps2, wl.eps1, wl.pol_dirs, out=out,
+                            want_q=out is out_full)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    if getattr(args, "profile_run", False):
+        return _profile_step(lambda: step(out_small), sv, wl.name, args.solver)
+
+    warm = max(3, min(args.warmup, 5))
+    for _ in range(warm):
+        step(out_small)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = time.perf_counter()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    pts = 0
+    mv_ms = mv_n = mv_bytes = ksteps = launches = 0.0
+    mm_ms = mm_n = mm_flops = 0.0
+    e0.record()
+    for _ in range(args.steps):
+        r = step(out_small)
+        st = sv.stats()
+        pts += int((r["status"] == 0).sum())
+        mv_ms += st["shift_matvec_ms"]
+        mv_n += st["shift_matvec_launches"]
+        mv_bytes += st["shift_matvec_bytes"]
+        mm_ms += st["matvec_ms"]
+        mm_n += st["matvec_launches"]
+        mm_flops += st["matvec_flops"]
+        ksteps += st["shift_steps"]
+        launches += st["kernel_launches"] + st["setup_launches"]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    e0.record()
+    pts2 = 0
+    for _ in range(e2e_steps):
+        pts2 += int((step(out_full)["status"] == 0).sum())
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    clk = clocks.stop(t0, time.perf_counter())
+    sv.close()
+    peaks, src = _measured_peaks()
+    if mv_n:
+        avg_s = (mv_ms / mv_n) / 1e3
+        achieved = (mv_bytes / mv_n) / avg_s / 1e9
+        hbm = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": "k_sk_matvec (double-FP32 matvec of Ft's two FP32 planes)",
+                "peak_source": f"STREAM-style copy ({src})",
+                "algorithmic_bytes_per_launch": mv_bytes / mv_n, "avg_launch_ms": avg_s * 1e3,
+                "launches": int(mv_n)}
+    elif mm_n:
+        roof = _roofline(prec, "materialised", mm_flops / mm_n, (mm_ms / mm_n) / 1e3, int(mm_n), n)
+    else:
+        roof = None
+    h2d = wl.pos_ang.nbytes + wl.normals.nbytes + wl.area_ang2.nbytes + wl.omega_ev.nbytes + \
+        4 * 8 * F + wl.pol_dirs.nbytes
+    d2h = sum(v.nbytes for k, v in out_full.items() if isinstance(v, np.ndarray))
+    if rank == 0:
+        line = {"metric": "BEM (DPCM) spectrum points/s", "value": whole_job_value(pts / args.steps, world, ms / args.steps),
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warm,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": (DTYPES.get(prec, prec) if args.solver == "batched"
+                          else "f32-pair (double-FP32) matvec, basis and orthogonalisation + f64 least squares"),
+                "data": "synthetic",
+                "config": {"workload": wl.name, "n_tesserae": n, "n_freq": F, "n_pol": P,
+                           "columns": F * P, "tol_rel": wl.tol, "solver": args.solver,
+                           "precision": prec,
+                           "l2": "no flush: the operator planes are far larger than L2",
+                           "parallelism": f"replicas x{world}"},
+                "clocks": clk, "gpu_launches": int(launches),
+                "e2e": {"value": whole_job_value(pts2 / e2e_steps, world, e2e_ms / e2e_steps),
+                        "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": e2e_steps},
+                "roofline": roof, "cpu_baseline": None,
+                "krylov_steps_per_step": ksteps / args.steps,
+                "note": "boundary-element model of Sec. 2.3 (Eq. 11), a separate workload"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
 
 
 # ---------------------------------------------------------------- serving mix
@@ -608,7 +868,8 @@ def run_serving(args, rank, world, local_rank):
     prec = args.precision or "fp16split"
 
     def run(arrivals):
-        with Server(max_slots=args.serve_slots, precision=prec, tol_rel=1e-7) as srv:
+        with Server(max_slots=args.serve_slots, precision=prec, tol_rel=1e-7,
+                    solver=args.serve_solver) as srv:
             t0 = time.perf_counter()
             ids = []
             for wl, ta in zip(wls, arrivals):
@@ -640,6 +901,7 @@ def run_serving(args, rank, world, local_rank):
                        "natoms_range": [min(w.natoms for w in wls), max(w.natoms for w in wls)],
                        "wfqfmu_requests": sum(w.model == "wfqfmu" for w in wls),
                        "slots": args.serve_slots, "precision": prec,
+                       "wfq_solver": args.serve_solver,
                        "arrivals": f"Poisson, rate 0.7 x measured capacity = {rate:.3f} req/s"},
             "clocks": clk,
             "serving": {"capacity_points_per_s": pts0 / wall0, "capacity_wall_s": wall0,
@@ -669,6 +931,8 @@ def main():
     ap.add_argument("--graphs", action=argparse.BooleanOptionalAction, default=True,
                     help="run restart cycles as graph launches in the timed region (default; "
                          "--no-graphs: one launch per kernel, every matvec event-timed)")
+    ap.add_argument("--solver", default="batched", choices=["batched", "shifted"],
+                    help="solver of the main line (the batched line also reports a shifted leg)")
     ap.add_argument("--shifted-steps", dest="shifted_steps", type=int, default=-1,
                     help="timed steps of the shifted Krylov leg (wFQ workloads; -1 = --steps, "
                          "0 = skip)")
@@ -682,6 +946,13 @@ def main():
     ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=40)
     ap.add_argument("--serve-nmax", dest="serve_nmax", type=int, default=8000)
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
+    ap.add_argument("--serve-solver", dest="serve_solver", default="shifted",
+                    choices=["batched", "shifted"],
+                    help="solver of the served wFQ requests (wFQFmu requests are batched)")
+    ap.add_argument("--profile-run", dest="profile_run", action="store_true",
+                    help="run one untimed step of the selected path and exit (for profilers)")
+    ap.add_argument("--bem-tess", dest="bem_tess", type=int, default=20000,
+                    help="tesserae of the boundary-element workload (--workload bem_sphere)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -690,6 +961,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serving":
         return run_serving(args, rank, world, local_rank)
+    if args.workload == "bem_sphere":
+        return run_bem(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

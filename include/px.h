@@ -338,6 +338,57 @@ px_status px_fields(px_handle* h, int n_points, const double* points_ang, int n_
                     const double* d_q, const double* d_mu, double* d_rho, double* d_phi,
                     double* d_E, void* cuda_stream);
 
+/* The frequency-independent dense system of the loaded structure, for callers that
+ * factorise it themselves (e.g. a direct LU per frequency, the "inversion" solver of
+ * Sec. "Solvers"): A0 = Kbar T (Eq. 1) or diag(Kbar, I_3N) T (Eq. 7), so that
+ * A(w) = A0 - z_q(w) I (wFQ) or A0 - diag(z_q(w) I_N, z_mu(w) I_3N) (wFQFmu), and the
+ * real right-hand sides b (-Kbar V; E) of the field directions.
+ *   d_A0    device [n_u][ld_A0] doubles (row-major, ld_A0 >= n_u), or NULL
+ *   d_b     device [n_u][n_pol] doubles, or NULL
+ * Unknowns in the caller's atom order: charges 0..N-1, then the dipole components
+ * N + 3 i + k (the order of px_result's q and mu).
+ * Needs the materialised FP64 T (not PX_MODE_MATFREE); PX_ENOTIMPL for
+ * PX_WFQFMU_HETERO (its conductance block depends on the frequency).  Allocates a
+ * transient n_u^2 FP64 buffer.  Synchronous. */
+px_status px_system_device(px_handle* h, int n_pol, const double* pol_dir, double e0,
+                           double* d_A0, size_t ld_A0, double* d_b, void* cuda_stream);
+
+/* Boundary-element (DPCM) surface of a dielectric or metal particle (Sec. 2.3, Eq. 11):
+ * replaces any loaded structure.  Tessera i has barycentre s_i, outward unit normal n_i
+ * and area A_i; the unknowns are the surface charge densities sigma_i.  The library
+ * solves the normal-field form of Eq. 11,
+ *   (Ft - Lambda(w) I) sigma = -E0 e . n,   Lambda(w) = 2 pi (e2 + e1)/(e2 - e1),
+ *   Ft_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j),
+ *   Ft_ii = 1.0694 sqrt(4 pi A_i) / (2 R),
+ * which is the printed equation read dimensionally (the area matrix on the diagonal term
+ * dropped, F taken with the receiving tessera's normal); on a sphere it converges to the
+ * exact quasistatic polarisability R^3 (e2 - e1)/(e2 + 2 e1).  Ft is dense and
+ * frequency-independent, so it is built once (FP64, plus the planes the selected
+ * precision and solver read), and every frequency is a column shift Lambda(w), exactly
+ * as z_q(w) in Eq. 1: both PX_SOLVER_BATCHED and PX_SOLVER_SHIFTED apply.
+ *   pos_ang     host [n_tess][3] barycentres, Angstrom
+ *   normals     host [n_tess][3] outward unit normals
+ *   area_ang2   host [n_tess] areas, Angstrom^2 (> 0)
+ *   radius_ang  R of the self term: the radius of the sphere enclosing the mesh, Angstrom
+ * PX_EINVAL for NULL / non-finite inputs, non-unit normals, non-positive areas or R;
+ * PX_ENOTIMPL in PX_MODE_MATFREE; PX_ENOMEM when the n_tess^2 operator planes do not fit.
+ * Tesserae keep the caller's order.  px_fields, px_system_device and
+ * px_relres_device_noalloc return PX_ENOTIMPL while a mesh is loaded. */
+px_status px_set_mesh(px_handle* h, int n_tess, const double* pos_ang, const double* normals,
+                      const double* area_ang2, double radius_ang);
+
+/* Solve the loaded mesh (px_set_mesh) for F frequencies x P field directions.
+ *   omega_ev  host [F] frequencies, eV (> 0; they enter sigma_abs only)
+ *   eps       host [F][4] doubles: Re e2, Im e2, Re e1, Im e1 -- the particle's and the
+ *             medium's permittivities at each frequency (finite, e2 != e1)
+ * Everything else is as in px_solve: out->q holds the tesserae's charges A_i sigma_i
+ * (there are no dipoles: out->mu is left untouched), out->alpha the dipole
+ * sum_i A_i sigma_i s_i / E0 (bohr^3), out->sigma_abs 4 pi w/(3c) Im Tr(alpha) for three
+ * independent directions.  PX_EINVAL when no mesh is loaded. */
+px_status px_solve_bem(px_handle* h, int n_freq, const double* omega_ev, const double* eps,
+                       int n_pol, const double* pol_dir, double e0, px_result* out,
+                       void* cuda_stream);
+
 /* Counters of the last px_solve / px_set_structure. */
 px_status px_get_stats(const px_handle* h, px_stats* st);
 

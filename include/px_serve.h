@@ -53,9 +53,11 @@ typedef struct {
   size_t peak_reserved_bytes; /* largest sum of admitted footprint estimates */
 } px_server_stats;
 
-/* Create a server.  opt: solver options for every request (NULL = defaults).
- * max_slots in [1, 32]; hbm_budget_bytes = 0 means 80% of the free device memory.
- * PX_EINVAL, PX_ECUDA. */
+/* Create a server.  opt: solver options for every request (NULL = defaults); with
+ * solver = PX_SOLVER_SHIFTED the PX_WFQ requests use the shifted solver (PX_WFQFMU ones
+ * stay batched) and an automatic shift_krylov_max becomes 1500, so that admission can
+ * count the shifted work space.  max_slots in [1, 32]; hbm_budget_bytes = 0 means 80% of
+ * the free device memory.  PX_EINVAL, PX_ECUDA. */
 px_status px_server_create(px_server** s, const px_options* opt, int max_slots,
                            size_t hbm_budget_bytes);
 

@@ -102,6 +102,19 @@ class Solver:
         self.model = m
         self.natoms = xyz.shape[0]
 
+    def set_mesh(self, pos_ang, normals, area_ang2, radius_ang):
+        """Boundary-element surface (Sec. 2.3, Eq. 11): barycentres (n, 3) Angstrom, outward
+        unit normals (n, 3), areas (n,) Angstrom^2, enclosing radius R (Angstrom)."""
+        pos = np.ascontiguousarray(pos_ang, dtype=np.float64).reshape(-1, 3)
+        nrm = np.ascontiguousarray(normals, dtype=np.float64).reshape(-1, 3)
+        area = np.ascontiguousarray(area_ang2, dtype=np.float64).reshape(-1)
+        if nrm.shape != pos.shape or area.size != pos.shape[0]:
+            raise ValueError("pos_ang, normals and area_ang2 describe different meshes")
+        self._check(self._lib.px_set_mesh(self._h, pos.shape[0], L.dptr(pos), L.dptr(nrm),
+                                          L.dptr(area), float(radius_ang)))
+        self.model = L.PX_WFQ   # one scalar unknown per tessera, no dipoles
+        self.natoms = pos.shape[0]
+
     def alloc_outputs(self, n_freq, n_pol, want_q=True, want_mu=True, empty=np.zeros):
         """Host result arrays for solve(); ``empty`` may allocate pinned memory."""
         F, P, N = int(n_freq), int(n_pol), self.natoms
@@ -142,6 +155,32 @@ class Solver:
         self._check(st, allow=(L.PX_ENOTCONV,))
         result = dict(o)
         result["ok"] = st == L.PX_OK
+        if P != 3:
+            result.pop("sigma_abs", None)
+        return result
+
+    def solve_bem(self, omega_ev, eps2, eps1, pol_dirs, e0=1.0, want_q=True, stream=None,
+                  out=None):
+        """Solve the loaded mesh for the permittivities eps2 (particle) and eps1 (medium),
+        (F,) complex each (eps1 may be a scalar).  Returns the dict of solve(); q holds the
+        tesserae's charges A_i sigma_i."""
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64).reshape(-1)
+        pol = np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        F, P = w.size, pol.shape[0]
+        e2 = np.broadcast_to(np.asarray(eps2, dtype=np.complex128), (F,))
+        e1 = np.broadcast_to(np.asarray(eps1, dtype=np.complex128), (F,))
+        eps = np.ascontiguousarray(np.stack([e2.real, e2.imag, e1.real, e1.imag], axis=1))
+        o = out if out is not None else self.alloc_outputs(F, P, want_q, False)
+        cptr = lambda a: a.view(np.float64).ctypes.data_as(L._dp) if a is not None else None
+        res = L.Result(cptr(o["alpha"]), L.dptr(o["sigma_abs"]), L.dptr(o["sigma_abs_pol"]),
+                       cptr(o["q"]), None, L.dptr(o["rel_residual"]),
+                       L.iptr(o["iters"]), L.iptr(o["status"]))
+        st = self._lib.px_solve_bem(self._h, F, L.dptr(w), L.dptr(eps), P, L.dptr(pol), float(e0),
+                                    C.byref(res), C.c_void_p(stream) if stream else None)
+        self._check(st, allow=(L.PX_ENOTCONV,))
+        result = dict(o)
+        result["ok"] = st == L.PX_OK
+        result.pop("mu", None)
         if P != 3:
             result.pop("sigma_abs", None)
         return result
@@ -192,6 +231,17 @@ class Solver:
         self._check(self._lib.px_fields(self._h, pts.shape[0], L.dptr(pts), C_, ptr(d_q), ptr(d_mu),
                                         ptr(d_rho), ptr(d_phi), ptr(d_E),
                                         C.c_void_p(stream) if stream else None))
+
+    def system_device(self, pol_dirs=None, e0=1.0, d_A0=None, d_b=None, stream=None):
+        """The frequency-independent dense operator A0 (n_u x n_u, float64 CUDA tensor,
+        row-major) and right-hand sides b (n_u x P) of the loaded structure (see
+        px_system_device in include/px.h)."""
+        pol = None if pol_dirs is None else np.ascontiguousarray(pol_dirs, dtype=np.float64).reshape(-1, 3)
+        ld = d_A0.stride(0) if d_A0 is not None else 0
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self._lib.px_system_device(
+            self._h, 0 if pol is None else pol.shape[0], L.dptr(pol) if pol is not None else None,
+            float(e0), ptr(d_A0), ld, ptr(d_b), C.c_void_p(stream) if stream else None))
 
     def stats(self) -> dict:
         s = L.Stats()

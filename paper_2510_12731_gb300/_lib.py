@@ -110,6 +110,11 @@ SIGNATURES = {
                                            C.c_void_p]),
     "px_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "px_system_device": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_double, C.c_void_p, C.c_size_t,
+                                   C.c_void_p, C.c_void_p]),
+    "px_set_mesh": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double]),
+    "px_solve_bem": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, C.c_int, _dp, C.c_double,
+                               C.POINTER(Result), C.c_void_p]),
     "px_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "px_destroy": (C.c_int, [C.c_void_p]),
     "px_last_error": (C.c_char_p, [C.c_void_p]),

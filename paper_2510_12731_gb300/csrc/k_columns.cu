@@ -14,13 +14,18 @@ namespace {
 __global__ void k_observables(int N, int model, int F, int P, const double* __restrict__ pos,
                               const int* __restrict__ perm, const double2* __restrict__ x, double e0,
                               const double* __restrict__ omega_ev, const double* __restrict__ pol,
-                              double2* alpha, double2* qout, double2* muout, double* sigma_pol) {
+                              double2* alpha, double2* qout, double2* muout, double* sigma_pol,
+                              const double* __restrict__ weight) {
   const int c = blockIdx.x;
   const int B = F * P;
   const int f = c / P, p = c % P;
   double d[6] = {0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     double2 q = x[(size_t)i * B + c];
+    if (weight) {   // boundary elements: the tessera's charge A_i sigma_i
+      q.x *= weight[i];
+      q.y *= weight[i];
+    }
     for (int k = 0; k < 3; ++k) {
       d[2 * k] += q.x * pos[3 * i + k];
       d[2 * k + 1] += q.y * pos[3 * i + k];
@@ -223,7 +228,37 @@ __global__ void k_init_residual_c(const double2* bc, int nu, int B, const double
   }
 }
 
+// Boundary elements (Sec. 2.3): the scalar shift of every column, Lambda(w_f) =
+// 2 pi (e2 + e1) / (e2 - e1) (Eq. 11), and the right-hand side b_i = -E0 e_p . n_i.
+__global__ void k_bem_shifts(int F, int P, const double* eps, double2* zq) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= F * P) return;
+  const int f = c / P;
+  const double2 e2 = make_double2(eps[4 * f], eps[4 * f + 1]);
+  const double2 e1 = make_double2(eps[4 * f + 2], eps[4 * f + 3]);
+  const double2 num = make_double2(e2.x + e1.x, e2.y + e1.y);
+  const double2 den = make_double2(e2.x - e1.x, e2.y - e1.y);
+  const double2 q = cdiv(num, den);
+  zq[c] = make_double2(2.0 * 3.141592653589793 * q.x, 2.0 * 3.141592653589793 * q.y);
+}
+
+__global__ void k_rhs_bem(int n, const double* nrm, const double* pol, int P, double e0, double* b) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * P) return;
+  const int i = idx / P, p = idx - i * P;
+  b[idx] = -e0 * (pol[3 * p] * nrm[3 * i] + pol[3 * p + 1] * nrm[3 * i + 1] + pol[3 * p + 2] * nrm[3 * i + 2]);
+}
+
 }  // namespace
+
+cudaError_t launch_bem_setup(int F, int P, int n, const double* eps, const double* nrm,
+                             const double* pol, double e0, double2* zq, double* b, cudaStream_t s,
+                             long long* nl) {
+  k_bem_shifts<<<(F * P + 127) / 128, 128, 0, s>>>(F, P, eps, zq);
+  k_rhs_bem<<<(n * P + 255) / 256, 256, 0, s>>>(n, nrm, pol, P, e0, b);
+  *nl += 2;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_hetero_tables(int F, int P, int ntypes, int N, const double* omega_ev,
                                  const double* tpar, const int* type, const int* nn,
@@ -267,9 +302,9 @@ cudaError_t launch_observables(int N, int model, int F, int P, const double* pos
                                const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
                                double* sigma_pol, double* sigma, const double* pol_inv,
-                               cudaStream_t s, long long* nl) {
+                               const double* weight, cudaStream_t s, long long* nl) {
   k_observables<<<F * P, 256, 0, s>>>(N, model, F, P, pos, perm, x, e0, omega_ev, pol, alpha, qout,
-                                      muout, sigma_pol);
+                                      muout, sigma_pol, weight);
   ++*nl;
   if (sigma && alpha && pol_inv && P == 3) {
     Mat3 ei;

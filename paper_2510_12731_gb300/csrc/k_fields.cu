@@ -191,6 +191,7 @@ extern "C" px_status px_fields(px_handle* h, int n_points, const double* points_
   const px::DevStructure* dsp = px_structure(h);
   if (!dsp) return fail_f(h, PX_EINVAL, "no structure loaded");
   const px::DevStructure& d = *dsp;
+  if (d.bem) return fail_f(h, PX_ENOTIMPL, "field maps of a mesh are not implemented");
   if (n_points < 1 || n_cols < 1 || !points_ang || !d_q)
     return fail_f(h, PX_EINVAL, "need n_points >= 1, n_cols >= 1, points_ang and d_q");
   if (d_mu && d.model != PX_WFQFMU) return fail_f(h, PX_EINVAL, "d_mu is only meaningful for PX_WFQFMU");

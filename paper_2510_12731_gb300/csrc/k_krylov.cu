@@ -339,7 +339,11 @@ __global__ void __launch_bounds__(256) k_resid(ResidArgs a) {
       const double2 xv = a.x[(size_t)i * a.B + gc];
       const double y0r = a.Y[(size_t)i * a.ldy + 2 * col], y0i = a.Y[(size_t)i * a.ldy + 2 * col + 1];
       double2 w;
-      if (i < a.N) {
+      if (a.op_full) {
+        // boundary elements: Y = Ft x is the whole operator (Eq. 11): w = Y - Lambda x
+        const double2 zx = cmul(a.zq[col], xv);
+        w = make_double2(y0r - zx.x, y0i - zx.y);
+      } else if (i < a.N) {
         double sr = 0.0, si = 0.0;
         if (a.kappa) {
           // 1/2 (Kbar + Hbar(w)) with complex bond weights (Eq. 9)

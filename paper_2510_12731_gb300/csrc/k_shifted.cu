@@ -35,7 +35,6 @@ namespace px {
 
 namespace {
 
-constexpr int kDotsK = 8;        // basis vectors per projection block
 constexpr int kDotsRows = 512;   // rows per projection block
 constexpr int kUpdK = 32;        // basis vectors per update block
 
@@ -222,65 +221,53 @@ __global__ void __launch_bounds__(256) k_sk_kbar(int n, const int* __restrict__ 
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt
-// dpart[rb][k][p] = sum over the rows of block rb of V_k[i][p] W[i][p], k in the block's
-// group of kDotsK basis vectors (grid x), rows in blocks of rows_per_blk (grid y).
+// dpart[rb][k][p] = sum over the rows of block rb of V_k[i][p] W[i][p]: one basis vector k
+// per block column (grid x = j + 1), rows in blocks of rows_per_blk (grid y).  Each thread
+// keeps NP double-FP32 sums over many rows, so the block reduction is a small part of
+// the work; W is re-read per basis vector from L2 (it is n NP 8 bytes).
 template <int NP>
 __global__ void __launch_bounds__(256)
 k_sk_dots(const float2* __restrict__ V, const float2* __restrict__ W, int n, int j,
           int rows_per_blk, int m1, double* __restrict__ dpart) {
-  const int k0 = blockIdx.x * kDotsK;
-  if (k0 > j) return;   // uniform over the block
-  const int nk = min(kDotsK, j + 1 - k0);
+  const int k = blockIdx.x;
   const int r0 = blockIdx.y * rows_per_blk, r1 = min(n, r0 + rows_per_blk);
-  float ah[kDotsK][NP], al[kDotsK][NP];
+  const float2* Vk = V + (size_t)k * n * NP;
+  float ah[NP], al[NP];
 #pragma unroll
-  for (int kk = 0; kk < kDotsK; ++kk)
-#pragma unroll
-    for (int p = 0; p < NP; ++p) ah[kk][p] = al[kk][p] = 0.f;
+  for (int p = 0; p < NP; ++p) ah[p] = al[p] = 0.f;
   int nmac = 0;
+#pragma unroll 4
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 v = Vk[(size_t)i * NP + p];
+      const float2 w = W[(size_t)i * NP + p];
+      ff::mac(ah[p], al[p], v.x, v.y, w.x, w.y);
+    }
     if (++nmac == 32) {   // keep the compensation below ulp of the sum
       nmac = 0;
 #pragma unroll
-      for (int kk = 0; kk < kDotsK; ++kk)
-#pragma unroll
-        for (int p = 0; p < NP; ++p) ff::renorm(ah[kk][p], al[kk][p]);
+      for (int p = 0; p < NP; ++p) ff::renorm(ah[p], al[p]);
     }
-    float2 w[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) w[p] = W[(size_t)i * NP + p];
-    float2 vv[kDotsK][NP];
-#pragma unroll
-    for (int kk = 0; kk < kDotsK; ++kk)
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        vv[kk][p] = kk < nk ? V[((size_t)(k0 + kk) * n + i) * NP + p] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int kk = 0; kk < kDotsK; ++kk)
-#pragma unroll
-      for (int p = 0; p < NP; ++p) ff::mac(ah[kk][p], al[kk][p], vv[kk][p].x, vv[kk][p].y, w[p].x, w[p].y);
   }
-  __shared__ double sred[8][kDotsK * NP];
+  __shared__ double sred[8][NP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int kk = 0; kk < kDotsK; ++kk)
+  for (int p = 0; p < NP; ++p) {
+    float h = ah[p], l = al[p];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      float h = ah[kk][p], l = al[kk][p];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float bh = __shfl_xor_sync(0xffffffffu, h, o);
-        const float bl = __shfl_xor_sync(0xffffffffu, l, o);
-        ff::add(h, l, bh, bl);
-      }
-      if (lane == 0) sred[warp][kk * NP + p] = ff::join(h, l);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, h, o);
+      const float bl = __shfl_xor_sync(0xffffffffu, l, o);
+      ff::add(h, l, bh, bl);
     }
+    if (lane == 0) sred[warp][p] = ff::join(h, l);
+  }
   __syncthreads();
-  if ((int)threadIdx.x < nk * NP) {
+  if ((int)threadIdx.x < NP) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += sred[w][threadIdx.x];
-    const int kk = threadIdx.x / NP, p = threadIdx.x - kk * NP;
-    dpart[((size_t)blockIdx.y * m1 + k0 + kk) * NP + p] = t;
+    dpart[((size_t)blockIdx.y * m1 + k) * NP + threadIdx.x] = t;
   }
 }
 
@@ -761,15 +748,15 @@ int sk_update_chunks(int m) { return (m + 1 + kUpdK - 1) / kUpdK; }
 cudaError_t launch_sk_gs_pass(const float2* V, float2* W, int n, int NP, int j, int m1,
                               double* dpart, double* h, float2* upart, bool last, double* npart,
                               cudaStream_t s, long long* nl) {
-  // row blocks of the projections: enough blocks to fill the GPU (about one per SM), and
-  // no more, so that each thread sums many rows before the block reduction
-  const int ngk = (j + 1 + kDotsK - 1) / kDotsK;
-  const int nrb = std::max(1, std::min(sk_row_blocks(n), (sm_count() + ngk - 1) / ngk));
+  // row blocks of the projections: enough blocks (basis vectors x row blocks) to fill
+  // the GPU twice, each thread summing at least 16 rows
+  const int nrb = std::max(1, std::min(std::min(sk_row_blocks(n), (n + 4095) / 4096),
+                                       (2 * sm_count() + j) / (j + 1)));
   const int rows_per_blk = (n + nrb - 1) / nrb;
   const int nkc = (j + 1 + kUpdK - 1) / kUpdK;
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
-    k_sk_dots<K><<<dim3(ngk, nrb), 256, 0, s>>>(V, W, n, j, rows_per_blk, m1, dpart);
+    k_sk_dots<K><<<dim3(j + 1, nrb), 256, 0, s>>>(V, W, n, j, rows_per_blk, m1, dpart);
     k_sk_dots_reduce<<<((j + 1) * K + 255) / 256, 256, 0, s>>>(j, K, nrb, m1, dpart, h);
     k_sk_update<K><<<dim3(nkc, (n + 255) / 256), 256, 0, s>>>(V, n, j, h, upart);
     k_sk_update_fin<K><<<(n + 255) / 256, 256, 0, s>>>(W, n, nkc, upart, last ? 1 : 0, npart);

@@ -132,21 +132,42 @@ __global__ void k_nn_counts(const double* __restrict__ pos, int N, const int* __
   }
 }
 
-// T^qq (Eq. 5).  Thread per (i, j) atom pair.
-__global__ void k_build_Tqq(const double* __restrict__ pos, const double* __restrict__ Rq, int N,
-                            int ld, double* T) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
-  double v;
-  if (i == j) {
-    v = kSqrt2OverPi / Rq[i];
-  } else {
-    double r = sqrt(dist2(pos, i, j));
-    double R = sqrt(Rq[i] * Rq[i] + Rq[j] * Rq[j]);
-    v = erf(r / R) / r;
+// T^qq (Eq. 5), symmetric: each 32 x 32 tile of the upper triangle (tile row <= tile
+// column) is evaluated once, written in place and, through shared memory, to its mirror
+// tile, so every pair costs one erf.  32 x 8 threads per tile, 4 rows each.
+__global__ void __launch_bounds__(256) k_build_Tqq(const double* __restrict__ pos,
+                                                   const double* __restrict__ Rq, int N, int ld,
+                                                   double* T) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = bj * 32 + tx;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int il = ty + 8 * q;
+    const int i = bi * 32 + il;
+    double v = 0.0;
+    if (i < N && j < N) {
+      if (i == j) {
+        v = kSqrt2OverPi / Rq[i];
+      } else {
+        const double r = sqrt(dist2(pos, i, j));
+        const double R = sqrt(Rq[i] * Rq[i] + Rq[j] * Rq[j]);
+        v = erf(r / R) / r;
+      }
+      T[(size_t)i * ld + j] = v;
+    }
+    tile[il][tx] = v;
   }
-  T[(size_t)i * ld + j] = v;
+  if (bi == bj) return;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jl = ty + 8 * q;
+    const int jr = bj * 32 + jl, ic = bi * 32 + tx;
+    if (jr < N && ic < N) T[(size_t)jr * ld + ic] = tile[tx][jl];
+  }
 }
 
 struct Radial { double t0, t1, t2; };   // T, T', T'' of erf(r/R)/r at r
@@ -340,11 +361,13 @@ cudaError_t launch_build_T64(const DevStructure& d, int mu_self_term, cudaStream
   cudaError_t e = cudaMemsetAsync(d.T64, 0, sizeof(double) * (size_t)d.np * d.np, s);
   if (e != cudaSuccess) return e;
   dim3 blk(32, 8);
-  dim3 grd((d.N + 31) / 32, (d.N + 7) / 8);
-  if (d.model == 0)
-    k_build_Tqq<<<grd, blk, 0, s>>>(d.pos64, d.Rq, d.N, d.np, d.T64);
-  else
+  if (d.model == 0) {
+    const int nt = (d.N + 31) / 32;
+    k_build_Tqq<<<dim3(nt, nt), blk, 0, s>>>(d.pos64, d.Rq, d.N, d.np, d.T64);
+  } else {
+    dim3 grd((d.N + 31) / 32, (d.N + 7) / 8);
     k_build_T4<<<grd, blk, 0, s>>>(d.pos64, d.Rq, d.Rmu, d.N, d.np, mu_self_term, d.T64);
+  }
   ++*nl;
   return cudaGetLastError();
 }
@@ -374,6 +397,80 @@ cudaError_t launch_nn_counts(const double* pos, int N, const int* type, int ntyp
                              const double* r0t, const double* st, const int* rowptr,
                              const int* col, int* nn, int* ident, cudaStream_t s, long long* nl) {
   k_nn_counts<<<(N + 127) / 128, 128, 0, s>>>(pos, N, type, ntypes, r0t, st, rowptr, col, nn, ident);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+namespace {
+// caller index of internal unknown u: charges follow perm, dipole component k of internal
+// atom a goes to N + 3 perm[a] + k
+__device__ __forceinline__ int caller_unknown(int u, int N, const int* perm) {
+  if (u < N) return perm[u];
+  const int a = (u - N) / 3;
+  return N + 3 * perm[a] + (u - N - 3 * a);
+}
+
+__global__ void k_unpermute_op(const double* __restrict__ M, int np, int nu, int N,
+                               const int* __restrict__ perm, double* A, size_t lda) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nu) return;
+  const int cc = caller_unknown(c, N, perm);
+  for (int r = blockIdx.y; r < nu; r += gridDim.y)
+    A[(size_t)caller_unknown(r, N, perm) * lda + cc] = M[(size_t)r * np + c];
+}
+
+__global__ void k_unpermute_rows(const double* __restrict__ b, int nu, int N, int P,
+                                 const int* __restrict__ perm, double* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nu * P) return;
+  const int r = idx / P, p = idx - r * P;
+  out[(size_t)caller_unknown(r, N, perm) * P + p] = b[idx];
+}
+}  // namespace
+
+cudaError_t launch_unpermute_system(const double* M, int np, int nu, int N, const int* perm,
+                                    double* A, size_t lda, const double* b, int P, double* bout,
+                                    cudaStream_t s, long long* nl) {
+  if (A) {
+    k_unpermute_op<<<dim3((nu + 255) / 256, nu < 65535 ? nu : 65535), 256, 0, s>>>(M, np, nu, N, perm, A,
+                                                                              lda);
+    ++*nl;
+  }
+  if (bout) {
+    k_unpermute_rows<<<(nu * P + 255) / 256, 256, 0, s>>>(b, nu, N, P, perm, bout);
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+// DPCM operator of a meshed surface (Sec. 2.3, Eq. 11, normal-field form):
+// Ft_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j), Ft_ii = 1.0694 sqrt(4 pi A_i) / (2R).
+__global__ void k_build_F(const double* __restrict__ pos, const double* __restrict__ nrm,
+                          const double* __restrict__ area, double R, int n, int ld, double* F) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  double v;
+  if (i == j) {
+    v = 1.0694 * sqrt(4.0 * 3.141592653589793 * area[i]) / (2.0 * R);
+  } else {
+    const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                 dz = pos[3 * i + 2] - pos[3 * j + 2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double dn = dx * nrm[3 * i] + dy * nrm[3 * i + 1] + dz * nrm[3 * i + 2];
+    v = area[j] * dn / (r2 * sqrt(r2));
+  }
+  F[(size_t)i * ld + j] = v;
+}
+}  // namespace
+
+cudaError_t launch_build_F(const double* pos, const double* nrm, const double* area, double R,
+                           int n, int np, double* F, cudaStream_t s, long long* nl) {
+  cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * (size_t)np * np, s);
+  if (e != cudaSuccess) return e;
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  k_build_F<<<grd, blk, 0, s>>>(pos, nrm, area, R, n, np, F);
   ++*nl;
   return cudaGetLastError();
 }

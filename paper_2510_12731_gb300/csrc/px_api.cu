@@ -78,6 +78,7 @@ struct px_handle {
   DevBuf b_stage;  // staging inputs (caller order) and sort scratch
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
   DevBuf b_rm2;    // matrix-free wFQFmu: R_mu^2 in FP32 and FP64
+  DevBuf b_mesh;   // boundary elements: normals [N][3], areas [N]
   DevBuf b_M64;    // FP64 M = diag(Kbar, I) T while its split planes are built
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
@@ -118,7 +119,7 @@ void drop_graphs(px_handle* h) {
 void free_all(px_handle* h) {
   DevBuf* bufs[] = {&h->b_M64, &h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
-                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_rm2, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_rm2, &h->b_mesh, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
@@ -268,6 +269,9 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   h->have_structure = false;
   d.model = model;
   d.hetero = hetero;
+  d.bem = false;
+  d.nrm = nullptr;
+  d.tarea = nullptr;
   d.N = N;
   d.nu = model == PX_WFQ ? N : 4 * N;
   d.np = (int)round_up(d.nu, px::kTile);
@@ -457,6 +461,115 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
 }
 
 
+// ------------------------------------------------------------------ boundary elements
+// A meshed surface (Sec. 2.3): tesserae with barycentres, outward normals and areas; the
+// dense DPCM operator Ft (Eq. 11, normal-field form) takes the place of Kbar T, so both
+// solvers apply unchanged with the column shift Lambda(w) = 2 pi (e2 + e1)/(e2 - e1).
+void set_mesh(px_handle* h, int n, const double* pos_ang, const double* nrm,
+              const double* area_ang2, double radius_ang) {
+  if (!pos_ang || !nrm || !area_ang2) throw PxError{PX_EINVAL, "NULL input"};
+  if (n < 1) throw PxError{PX_EINVAL, "n_tess must be >= 1"};
+  if (!std::isfinite(radius_ang) || !(radius_ang > 0.0)) throw PxError{PX_EINVAL, "radius must be finite and > 0"};
+  std::vector<double> pos(3 * (size_t)n), area(n);
+  for (int i = 0; i < n; ++i) {
+    double n2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double p = pos_ang[3 * (size_t)i + k], v = nrm[3 * (size_t)i + k];
+      if (!std::isfinite(p) || !std::isfinite(v)) throw PxError{PX_EINVAL, "non-finite mesh data"};
+      pos[3 * (size_t)i + k] = p / kBohrAng;
+      n2 += v * v;
+    }
+    if (std::fabs(std::sqrt(n2) - 1.0) > 1e-6) throw PxError{PX_EINVAL, "normals must be unit vectors"};
+    if (!std::isfinite(area_ang2[i]) || !(area_ang2[i] > 0.0)) throw PxError{PX_EINVAL, "areas must be > 0"};
+    area[i] = area_ang2[i] / (kBohrAng * kBohrAng);
+  }
+  const int prec = h->opt.precision;
+  const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
+  if (h->opt.mode == PX_MODE_MATFREE) throw PxError{PX_ENOTIMPL, "meshes need the materialised operator"};
+  cudaStream_t s = h->own_stream;
+  px::DevStructure& d = h->ds;
+  h->have_structure = false;
+  d = px::DevStructure{};
+  d.model = PX_WFQ;   // one unknown per element, one scalar shift per column
+  d.bem = true;
+  d.N = n;
+  d.nu = n;
+  d.np = (int)round_up(n, px::kTile);
+  d.ntypes = 1;
+  h->nl = 0;
+  CU(cudaEventRecord(h->ev_a, s));
+  CU(h->b_pos.ensure(sizeof(double) * 3 * n));
+  CU(h->b_mesh.ensure(round_up(sizeof(double) * 3 * n, 256) + sizeof(double) * n));
+  CU(h->b_perm.ensure(sizeof(int) * n));
+  CU(h->b_type.ensure(sizeof(int) * n));
+  d.pos64 = h->b_pos.as<double>();
+  d.nrm = h->b_mesh.as<double>();
+  d.tarea = reinterpret_cast<double*>(h->b_mesh.as<unsigned char>() + round_up(sizeof(double) * 3 * n, 256));
+  d.perm = h->b_perm.as<int>();
+  d.type = h->b_type.as<int>();
+  std::vector<int> iota(n);
+  for (int i = 0; i < n; ++i) iota[i] = i;
+  CU(cudaMemcpyAsync(d.pos64, pos.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.nrm, nrm, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.tarea, area.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d.perm, iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(d.type, 0, sizeof(int) * n, s));
+  const size_t np2 = (size_t)d.np * d.np;
+  CU(h->b_T64.ensure(np2 * sizeof(double)));
+  d.T64 = h->b_T64.as<double>();
+  CU(px::launch_build_F(d.pos64, d.nrm, d.tarea, radius_ang / kBohrAng, n, d.np, d.T64, s, &h->nl));
+  if (prec == PX_FP32) {
+    CU(h->b_T32.ensure(np2 * sizeof(float)));
+    d.T32 = h->b_T32.as<float>();
+    CU(px::launch_convert_T(d, s, &h->nl));
+  }
+  d.t_f16 = prec == PX_FP16SPLIT;
+  if (split) {
+    CU(h->b_Thi.ensure(np2 * sizeof(uint16_t)));
+    CU(h->b_Tlo.ensure(np2 * sizeof(uint16_t)));
+    d.Thi = h->b_Thi.as<uint16_t>();
+    d.Tlo = h->b_Tlo.as<uint16_t>();
+    // the planes hold the whole operator; max |Ft| from the row-copy pass (no charge rows)
+    CU(h->b_M64.ensure(np2 * sizeof(double) + 256));
+    double* M64 = h->b_M64.as<double>();
+    unsigned long long* d_amax = reinterpret_cast<unsigned long long*>(M64 + np2);
+    CU(cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s));
+    px::DevStructure dcopy = d;
+    dcopy.N = 0;
+    CU(px::launch_build_M64(dcopy, M64, d_amax, s, &h->nl));
+    unsigned long long amax_bits = 0;
+    CU(cudaMemcpyAsync(&amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double amax = 0.0;
+    std::memcpy(&amax, &amax_bits, sizeof(amax));
+    if (!std::isfinite(amax)) throw PxError{PX_EINVAL, "non-finite operator entries"};
+    int e = 12;
+    if (amax > 0.0) e = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / amax))));
+    d.op_scale_exp = e;
+    d.op_has_kbar = true;
+    CU(px::launch_split_op(M64, np2, d.Thi, d.Tlo, d.t_f16, e, s, &h->nl));
+    CU(cudaStreamSynchronize(s));
+    h->b_M64.release();
+  }
+  if (prec != PX_FP64 || h->opt.solver == PX_SOLVER_SHIFTED) {
+    CU(h->b_Tffh.ensure(np2 * sizeof(float)));
+    CU(h->b_Tffl.ensure(np2 * sizeof(float)));
+    d.Tffh = h->b_Tffh.as<float>();
+    d.Tffl = h->b_Tffl.as<float>();
+    CU(px::launch_split_ff(d.T64, np2, d.Tffh, d.Tffl, s, &h->nl));
+  }
+  CU(cudaEventRecord(h->ev_b, s));
+  wait_event(h, h->ev_b);
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, h->ev_a, h->ev_b));
+  h->stats.setup_ms = ms;
+  h->stats.setup_launches = h->nl;
+  h->stats.n_unknowns = n;
+  h->stats.used_mode = PX_MODE_MATERIALISED;
+  h->drude_n = h->tau = 1.0;   // unused: the column shifts come from the permittivities
+  h->have_structure = true;
+}
+
 // ------------------------------------------------------------------ solve
 struct SolveOut {
   double2* d_alpha = nullptr;  // device [F][3][P]
@@ -479,7 +592,8 @@ T* grow(DevBuf& b, size_t n) {
 }
 
 px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha_ib, int P,
-                const double* pol, double e0, SolveOut* so, cudaStream_t s) {
+                const double* pol, double e0, SolveOut* so, cudaStream_t s,
+                const double* eps = nullptr) {
   if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
   if (F < 1 || P < 1 || !omega_ev || !pol)
     throw PxError{PX_EINVAL, "need n_freq >= 1, n_pol >= 1, omega_ev and pol_dir"};
@@ -487,6 +601,15 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const px::DevStructure& d = h->ds;
   const int model = d.model;
   if (model == PX_WFQFMU && !alpha_ib) throw PxError{PX_EINVAL, "alpha_ib is required for PX_WFQFMU"};
+  if (d.bem && !eps) throw PxError{PX_EINVAL, "a mesh is solved with px_solve_bem"};
+  if (!d.bem && eps) throw PxError{PX_EINVAL, "px_solve_bem needs a mesh loaded with px_set_mesh"};
+  if (d.bem)
+    for (size_t k = 0; k < 4 * (size_t)F; ++k)
+      if (!std::isfinite(eps[k])) throw PxError{PX_EINVAL, "non-finite permittivity"};
+  if (d.bem)
+    for (int f = 0; f < F; ++f)
+      if (eps[4 * f] == eps[4 * f + 2] && eps[4 * f + 1] == eps[4 * f + 3])
+        throw PxError{PX_EINVAL, "e2 == e1: the particle does not polarise"};
   for (int f = 0; f < F; ++f)
     if (!std::isfinite(omega_ev[f]) || !(omega_ev[f] > 0.0))
       throw PxError{PX_EINVAL, "frequencies must be finite and > 0"};
@@ -557,9 +680,11 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   CU(cudaEventRecord(h->ev_a, s));
 
   // ---- inputs, shifts (Eq. 6, Eq. 8) and right-hand sides
-  double* d_omega = grow<double>(h->b_pol, 3 * (size_t)P + F + 2 * (size_t)ntypes * F);
+  double* d_omega = grow<double>(h->b_pol, 3 * (size_t)P + F + 2 * (size_t)ntypes * F + 4 * (size_t)F);
   double* d_pol = d_omega + F;
   double* d_aib = d_pol + 3 * P;
+  double* d_eps = d_aib + 2 * (size_t)ntypes * F;
+  if (d.bem) CU(cudaMemcpyAsync(d_eps, eps, sizeof(double) * 4 * F, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(d_omega, omega_ev, sizeof(double) * F, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(d_pol, pol, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, s));
   if (model == PX_WFQFMU)
@@ -608,7 +733,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     CU(px::launch_init_residual_c(bc, nu, B, bn, inner_tol, tol_abs_frac, r, rnorm, beta, target_all,
                                   s, &nl));
   } else {
-    CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
+    if (d.bem)   // Eq. 11: Lambda(w) per column (overwrites z_q) and b = -E0 e . n
+      CU(px::launch_bem_setup(F, P, nu, d_eps, d.nrm, d_pol, e0, zq_all, b, s, &nl));
+    else
+      CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
     CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
     CU(px::launch_bnorm_cols(bnorm, P, B, bn, s, &nl));
     CU(px::launch_init_residual(b, nu, P, B, bnorm, inner_tol, tol_abs_frac, r, rnorm, beta,
@@ -808,7 +936,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           CU(cudaEventRecord(e1v, s));
           sk_events.push_back({e0v, e1v});
         }
-        CU(px::launch_sk_kbar(nu, NP, d.rowptr, d.col, d.val64, d.val32, Uj, skW, s, &nl));
+        if (d.bem)   // the operator Ft is complete: W = U
+          CU(cudaMemcpyAsync(skW, Uj, sizeof(float2) * (size_t)nu * NP, cudaMemcpyDeviceToDevice, s));
+        else
+          CU(px::launch_sk_kbar(nu, NP, d.rowptr, d.col, d.val64, d.val32, Uj, skW, s, &nl));
         // two classical Gram-Schmidt passes (CGS2): every frequency shares this basis
         for (int pass = 0; pass < 2; ++pass)
           CU(px::launch_sk_gs_pass(skV, skW, nu, NP, j, m + 1, skDpart,
@@ -843,6 +974,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       ra.rowptr = d.rowptr; ra.col = d.col; ra.val64 = d.val64; ra.type = d.type;
       ra.Y = Y64; ra.ldy = ldx; ra.x = x; ra.act = act; ra.b = b; ra.zq = zq_act; ra.zmu = zmu_act;
       ra.R = r; ra.normpart = normpart;
+      ra.op_full = d.bem ? 1 : 0;
       CU(px::launch_resid(ra, s, &nl));
       CU(px::launch_norm_finish(normpart, nblk, B, act, B, bn, inner_tol, tol_abs_frac, rnorm,
                                 beta, target_all, s, &nl));
@@ -906,7 +1038,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       sa.precond_mu = amu_act ? 1 : 0;
       // the tensor-core planes hold M = diag(Kbar, I) T, fp16 parts scaled by 2^e (the
       // epilogue undoes 2^12)
-      sa.kbar_in_y = tc && d.op_has_kbar ? 1 : 0;
+      sa.kbar_in_y = (tc && d.op_has_kbar) || d.bem ? 1 : 0;
       sa.yscale = tc_f16 && d.op_has_kbar ? std::ldexp(1.0f, 12 - d.op_scale_exp) : 1.0f;
       sa.W = W;
       // one Krylov step: j >= 0 eagerly (host-side step index, per-step poll), or
@@ -1118,6 +1250,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     ra.R = r; ra.normpart = normpart;
     ra.qtype = het ? d.type : nullptr; ra.ntypes = ntypes; ra.kappa = het ? kap_act : nullptr;
     ra.bc = bc;
+    ra.op_full = d.bem ? 1 : 0;
     CU(px::launch_resid(ra, s, &nl));
     // per-column norms: bn indexed as [c % B]
     CU(px::launch_norm_finish(normpart, nblk, Bact, act, B, bn, inner_tol, tol_abs_frac, rnorm,
@@ -1143,7 +1276,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   // ---- observables (Sec. "Observables")
   CU(px::launch_observables(N, model, F, P, d.pos64, d.perm, x, e0, d_omega, d_pol, so->d_alpha, so->d_q,
                             so->d_mu, so->d_sigma_pol, so->d_sigma, have_triple ? pol_inv : nullptr,
-                            s, &nl));
+                            d.bem ? d.tarea : nullptr, s, &nl));
   if (so->d_relres) CU(px::launch_relres(rnorm, bn, B, B, so->d_relres, s, &nl));
   std::vector<double> h_rnorm(B);
   int h_err = 0;
@@ -1293,9 +1426,38 @@ px_status px_set_structure(px_handle* h, px_model model, int n_atoms, const doub
   return PX_OK;
 }
 
+px_status solve_host(px_handle* h, int n_freq, const double* omega_ev, const double* alpha_ib,
+                     const double* eps, int n_pol, const double* pol_dir, double e0, px_result* out,
+                     void* cuda_stream);
+
 px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const double* alpha_ib,
                    int n_pol, const double* pol_dir, double e0, px_result* out,
                    void* cuda_stream) {
+  return solve_host(h, n_freq, omega_ev, alpha_ib, nullptr, n_pol, pol_dir, e0, out, cuda_stream);
+}
+
+px_status px_set_mesh(px_handle* h, int n_tess, const double* pos_ang, const double* normals,
+                      const double* area_ang2, double radius_ang) {
+  if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
+  try {
+    set_mesh(h, n_tess, pos_ang, normals, area_ang2, radius_ang);
+  } catch (const PxError& e) {
+    h->have_structure = false;
+    return fail(h, e.st, e.msg);
+  }
+  return PX_OK;
+}
+
+px_status px_solve_bem(px_handle* h, int n_freq, const double* omega_ev, const double* eps,
+                       int n_pol, const double* pol_dir, double e0, px_result* out,
+                       void* cuda_stream) {
+  if (!eps) return fail(h, PX_EINVAL, "NULL permittivities");
+  return solve_host(h, n_freq, omega_ev, nullptr, eps, n_pol, pol_dir, e0, out, cuda_stream);
+}
+
+px_status solve_host(px_handle* h, int n_freq, const double* omega_ev, const double* alpha_ib,
+                     const double* eps, int n_pol, const double* pol_dir, double e0, px_result* out,
+                     void* cuda_stream) {
   if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
   if (!out) return fail(h, PX_EINVAL, "NULL result");
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
@@ -1312,7 +1474,7 @@ px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const doubl
     if (out->q) so.d_q = grow<double2>(h->b_q, B * N);
     if (out->mu && h->ds.model == PX_WFQFMU) so.d_mu = grow<double2>(h->b_mu, B * N * 3);
     so.sigma_required = out->sigma_abs != nullptr;
-    px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s);
+    px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s, eps);
     if (out->alpha) CU(cudaMemcpyAsync(out->alpha, so.d_alpha, sizeof(double2) * F * 3 * P, cudaMemcpyDeviceToHost, s));
     if (out->sigma_abs_pol) CU(cudaMemcpyAsync(out->sigma_abs_pol, so.d_sigma_pol, sizeof(double) * F * P, cudaMemcpyDeviceToHost, s));
     if (out->sigma_abs && P == 3) CU(cudaMemcpyAsync(out->sigma_abs, so.d_sigma, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
@@ -1354,6 +1516,48 @@ px_status px_solve_device(px_handle* h, int n_freq, const double* omega_ev,
   } catch (const PxError& e) {
     return fail(h, e.st, e.msg);
   }
+}
+
+px_status px_system_device(px_handle* h, int n_pol, const double* pol_dir, double e0, double* d_A0,
+                           size_t ld_A0, double* d_b, void* cuda_stream) {
+  if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
+  try {
+    if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
+    const px::DevStructure& d = h->ds;
+    if (d.hetero) throw PxError{PX_ENOTIMPL, "Eq. 9's conductance block depends on the frequency"};
+    if (d.bem) throw PxError{PX_ENOTIMPL, "the mesh operator is not exported"};
+    if (d.matfree || !d.T64) throw PxError{PX_EINVAL, "needs the materialised T (FP64)"};
+    if (d_A0 && ld_A0 < (size_t)d.nu) throw PxError{PX_EINVAL, "ld_A0 must be >= n_u"};
+    if (d_b && (n_pol < 1 || !pol_dir || !std::isfinite(e0) || !(e0 > 0.0)))
+      throw PxError{PX_EINVAL, "need n_pol >= 1, pol_dir and a finite e0 > 0 for d_b"};
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+    long long nl = 0;
+    // built in the library's internal (Morton) atom order, written in the caller's
+    if (d_A0) {
+      const size_t np2 = (size_t)d.np * d.np;
+      CU(h->b_M64.ensure(np2 * sizeof(double) + 256));
+      double* M64 = h->b_M64.as<double>();
+      unsigned long long* d_amax = reinterpret_cast<unsigned long long*>(M64 + np2);
+      CU(cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s));
+      CU(px::launch_build_M64(d, M64, d_amax, s, &nl));
+      CU(px::launch_unpermute_system(M64, d.np, d.nu, d.N, d.perm, d_A0, ld_A0, nullptr, 0, nullptr,
+                                     s, &nl));
+    }
+    if (d_b) {
+      double* dp = grow<double>(h->b_pol, 3 * (size_t)n_pol);
+      double* bi = grow<double>(h->b_b, (size_t)d.nu * n_pol);
+      CU(cudaMemcpyAsync(dp, pol_dir, sizeof(double) * 3 * n_pol, cudaMemcpyHostToDevice, s));
+      CU(px::launch_rhs(d.nu, d.N, d.model, d.rowptr, d.col, d.val64, d.pos64, dp, n_pol, e0, bi, s,
+                        &nl));
+      CU(px::launch_unpermute_system(nullptr, d.np, d.nu, d.N, d.perm, nullptr, 0, bi, n_pol, d_b, s,
+                                     &nl));
+    }
+    sync_stream(h, s);
+    h->b_M64.release();
+  } catch (const PxError& e) {
+    return fail(h, e.st, e.msg);
+  }
+  return PX_OK;
 }
 
 px_status px_get_stats(const px_handle* h, px_stats* st) {

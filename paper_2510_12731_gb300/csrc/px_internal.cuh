@@ -70,6 +70,10 @@ struct DevStructure {
   double* tpar = nullptr;      // [ntypes][3] n, tau, area of each type
   int* nncnt = nullptr;        // [N][ntypes] nearest neighbours of each type (r <= s r0)
   int* ident = nullptr;        // [N] 0..N-1: per-atom indexing of the dipole shifts
+  // boundary elements (Sec. 2.3): the "atoms" are tesserae; T holds the DPCM operator Ft
+  bool bem = false;
+  double* nrm = nullptr;       // [N][3] outward normals
+  double* tarea = nullptr;     // [N] tessera areas (bohr^2)
 };
 
 // ---------------------------------------------------------------- launch wrappers
@@ -105,6 +109,11 @@ cudaError_t launch_convert_T(const DevStructure& d, cudaStream_t s, long long* n
 // non-negative double, so its bit pattern orders like its value; zero it first).
 cudaError_t launch_build_M64(const DevStructure& d, double* M64,
                              unsigned long long* absmax_bits, cudaStream_t s, long long* nl);
+// Operator M [np][np] (internal order) -> A [nu][lda] in the caller's atom order, and
+// right-hand sides b [nu][P] (internal) -> bout [nu][P] (caller's order); either may be null.
+cudaError_t launch_unpermute_system(const double* M, int np, int nu, int N, const int* perm,
+                                    double* A, size_t lda, const double* b, int P, double* bout,
+                                    cudaStream_t s, long long* nl);
 // Thi / Tlo split of an FP64 operator A [np][np]: bf16 hi/lo, or (f16) fp16 hi of
 // 2^scale_exp A and fp16 lo of the remainder times 2^11.
 cudaError_t launch_split_op(const double* A, size_t n, uint16_t* hi, uint16_t* lo, bool f16,
@@ -253,8 +262,20 @@ struct ResidArgs {
   // heterogeneous wFQFmu: as in ShiftArgs, plus the complex right-hand side of every
   // column bc [nu][B] (replaces b)
   const int* qtype; int ntypes; const double2* kappa; const double2* bc;
+  int op_full;   // boundary elements: Y already holds the whole operator; every row w = Y - z x
 };
 cudaError_t launch_resid(const ResidArgs& a, cudaStream_t s, long long* nl);
+
+// ---- boundary elements (Sec. 2.3, Eq. 11 in the normal-field DPCM form)
+// Ft [np][np] (zero padded) of a mesh: pos, nrm [n][3] (bohr, unit), area [n] (bohr^2),
+// R the radius of the enclosing sphere.
+cudaError_t launch_build_F(const double* pos, const double* nrm, const double* area, double R,
+                           int n, int np, double* F, cudaStream_t s, long long* nl);
+// zq[c] = Lambda(w_f) = 2 pi (e2 + e1)/(e2 - e1) from eps [F][4] = (Re e2, Im e2, Re e1, Im e1),
+// and b[i][p] = -e0 e_p . n_i: the system (Ft - Lambda I) sigma = -E . n.
+cudaError_t launch_bem_setup(int F, int P, int n, const double* eps, const double* nrm,
+                             const double* pol, double e0, double2* zq, double* b, cudaStream_t s,
+                             long long* nl);
 
 // ---- heterogeneous wFQFmu (Eqs. 9-10)
 // nn[i][t] = atoms of type t within the Fermi midpoint s_ij r0_ij of atom i (Eq. 10's
@@ -360,7 +381,7 @@ cudaError_t launch_observables(int N, int model, int F, int P, const double* pos
                                const int* perm, const double2* x, double e0, const double* omega_ev,
                                const double* pol, double2* alpha, double2* qout, double2* muout,
                                double* sigma_pol, double* sigma, const double* pol_inv,
-                               cudaStream_t s, long long* nl);
+                               const double* weight, cudaStream_t s, long long* nl);
 // Row-major inverse of E = [e_0 e_1 e_2] (columns = the three field directions pol[3][3]);
 // false when the directions are not linearly independent (|det E| < 1e-6).
 bool pol_triple_inverse(const double* pol, double* inv);

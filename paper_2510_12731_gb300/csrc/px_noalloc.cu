@@ -121,6 +121,7 @@ extern "C" px_status px_relres_device_noalloc(px_handle* h, int n_freq, const do
   const px::DevStructure& d = *dsp;
   if (d.hetero)
     return fail_h(h, PX_ENOTIMPL, "px_relres_device_noalloc does not cover PX_WFQFMU_HETERO");
+  if (d.bem) return fail_h(h, PX_ENOTIMPL, "px_relres_device_noalloc does not cover meshes");
   if (n_freq < 1 || n_pol < 1 || !omega_ev || !pol_dir || !d_q || !d_relres)
     return fail_h(h, PX_EINVAL, "need n_freq, n_pol >= 1, omega_ev, pol_dir, d_q and d_relres");
   if (d.model == PX_WFQFMU && (!alpha_ib || !d_mu))

@@ -90,6 +90,15 @@ size_t footprint(const px_options& o, int model, int N, int B, bool mat) {
   t += 2 * (m + 1) * B * 16 * 4;       // projections, Hessenberg, partials (bound)
   t += (size_t)128 * (m + 1) * B * 16; // partial projections
   t += 64 << 20;                       // CSR, small arrays, slack
+  if (o.solver == PX_SOLVER_SHIFTED && model == PX_WFQ && mat) {
+    // shifted Krylov work space with the server's basis limit: double-FP32 planes of T
+    // (FP64 handles), basis and products T V, the per-system rotated triangular factors
+    const size_t ms = std::min<size_t>(nu, (size_t)o.shift_krylov_max);
+    if (o.precision == PX_FP64) t += np * np * 8;
+    t += 2 * (ms + 1) * nu * 4 * 8;                  // V, U (up to 4 directions)
+    t += (size_t)B * (ms * (ms + 1) / 2) * 16;       // R
+    t += ms * (ms + 2) * 4 * 8 + 5 * ms * (size_t)B * 16;   // Hessenberg, rotations, y
+  }
   return t;
 }
 
@@ -280,6 +289,9 @@ px_status px_server_create(px_server** out, const px_options* opt, int max_slots
   else px_options_default(&s->opt);
   // every slot shares the server's budget; a handle's own admission must not refuse
   s->opt.hbm_budget_bytes = 0;
+  // the shifted solver's basis limit is fixed for served requests, so that admission can
+  // account for its work space (a handle alone sizes it from the free memory)
+  if (s->opt.solver == PX_SOLVER_SHIFTED && s->opt.shift_krylov_max == 0) s->opt.shift_krylov_max = 1500;
   s->max_slots = max_slots;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;

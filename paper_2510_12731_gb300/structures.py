@@ -371,3 +371,71 @@ def alloy_sphere(radius=17.5, frac_au=0.5, seed=12731, nfreq=251, wmin=2.0, wmax
     return Workload(f"agau_sphere_r{radius:g}A_au{frac_au:g}_wfqfmu_hetero", "wfqfmu_hetero", xyz,
                     tidx, [ag.atom_type(), t_au], w, np.asarray(pols, dtype=np.float64), aib,
                     precision="fp32", tol=1e-7)
+
+
+# ----------------------------------------------------------------------------
+# Boundary-element inputs (Sec. 2.3): meshed particle surfaces and permittivities
+# ----------------------------------------------------------------------------
+
+def sphere_mesh(n, radius):
+    """n equal-area tesserae on a sphere of the given radius (Angstrom): the points of the
+    golden-angle spiral (a Fibonacci lattice) as barycentres, radial outward normals, area
+    4 pi R^2 / n each.  Returns (positions (n, 3), normals (n, 3), areas (n,))."""
+    i = np.arange(n) + 0.5
+    polar = np.arccos(1.0 - 2.0 * i / n)
+    azim = np.pi * (1.0 + math.sqrt(5.0)) * i
+    u = np.stack([np.cos(azim) * np.sin(polar), np.sin(azim) * np.sin(polar), np.cos(polar)], axis=1)
+    return radius * u, u, np.full(n, 4.0 * math.pi * radius * radius / n)
+
+
+def spheroid_mesh(n, a, b, c):
+    """The sphere mesh mapped onto the ellipsoid x^2/a^2 + y^2/b^2 + z^2/c^2 = 1: points
+    (a u_x, b u_y, c u_z), normals along (u_x/a, u_y/b, u_z/c), areas scaled by the map's
+    area factor a b c |(u_x/a, u_y/b, u_z/c)|."""
+    _, u, a0 = sphere_mesh(n, 1.0)
+    g = u / np.array([a, b, c])
+    gn = np.linalg.norm(g, axis=1)
+    return u * np.array([a, b, c]), g / gn[:, None], a0 * a * b * c * gn
+
+
+def drude_eps(omega_ev, wp_ev, gamma_ev, eps_inf=1.0):
+    """Drude permittivity e(w) = e_inf - wp^2 / (w^2 + i gamma w) (a stand-in for the
+    tabulated permittivities the paper reads)."""
+    w = np.asarray(omega_ev, dtype=np.float64)
+    return eps_inf - wp_ev ** 2 / (w * w + 1j * gamma_ev * w)
+
+
+@dataclass
+class MeshWorkload:
+    """A boundary-element problem: the meshed surface, the sweep and the permittivities."""
+
+    name: str
+    pos_ang: np.ndarray           # (n, 3) tessera barycentres
+    normals: np.ndarray           # (n, 3) outward unit normals
+    area_ang2: np.ndarray         # (n,) tessera areas
+    radius_ang: float             # radius of the sphere enclosing the mesh (F's diagonal)
+    omega_ev: np.ndarray          # (F,)
+    eps2: np.ndarray              # (F,) complex, the particle
+    eps1: np.ndarray              # (F,) complex, the medium
+    pol_dirs: np.ndarray          # (P, 3)
+    tol: float = 1e-7
+
+    @property
+    def ntess(self) -> int:
+        return int(self.pos_ang.shape[0])
+
+    @property
+    def ncols(self) -> int:
+        return int(self.omega_ev.size * self.pol_dirs.shape[0])
+
+
+def drude_sphere_mesh(n=3200, radius=20.0, nfreq=200, wmin=2.5, wmax=4.5, wp=6.0, gamma=0.1,
+                      eps1=1.0, pols=XYZ) -> MeshWorkload:
+    """DPCM stand-in workload: a Drude sphere (wp = 6 eV, gamma = 0.1 eV) of radius 20 A
+    meshed by n tesserae, in a medium of permittivity eps1, nfreq frequencies around its
+    dipolar (Froehlich) resonance wp / sqrt(3 eps1)."""
+    pos, nrm, area = sphere_mesh(n, radius)
+    w = np.linspace(wmin, wmax, nfreq)
+    return MeshWorkload(f"drude_sphere_r{radius:g}A_{n}tess", pos, nrm, area, float(radius), w,
+                        drude_eps(w, wp, gamma), np.full(nfreq, eps1, dtype=np.complex128),
+                        np.asarray(pols, dtype=np.float64))

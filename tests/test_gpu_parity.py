@@ -490,3 +490,46 @@ def test_wfqfmu_rod_converges_with_dipole_preconditioner():
     assert out["ok"]
     assert np.max(out["iters"]) < 3000
     assert _alpha_err(out, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_system_export_matches_the_oracle_and_solves(model):
+    """px_system_device: A0 = diag(Kbar, I) T and b against the oracle's dense assembly;
+    a direct LU of A0 - diag(z) in torch reproduces the oracle's alpha."""
+    import torch
+    w = S.small_cluster(element="Ag", radius=8.0, model=model, nfreq=2, wmin=3.0, wmax=4.0)
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    Kb = M.kbar(M.conductance_K(st))
+    N = w.natoms
+    nu = N if model == "wfq" else 4 * N
+    dev = torch.device("cuda", 0)
+    A0 = torch.zeros((nu, nu + 5), dtype=torch.float64, device=dev)    # ld > n_u
+    b = torch.zeros((nu, 3), dtype=torch.float64, device=dev)
+    with _solver(precision="fp64") as s:    # Morton-sorted inside; exported in caller order
+        s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        s.system_device(w.pol_dirs, 1.0, d_A0=A0, d_b=b)
+    if model == "wfq":
+        A_ref = Kb @ M.tqq(st)
+        b_ref = np.stack([M.rhs_wfq(Kb, st, e) for e in w.pol_dirs], axis=1)
+    else:
+        Pm = np.zeros((nu, nu))
+        Pm[:N, :N] = Kb
+        Pm[N:, N:] = np.eye(3 * N)
+        A_ref = Pm @ M.t_full(st)
+        b_ref = np.stack([M.rhs_wfqfmu(Kb, st, e) for e in w.pol_dirs], axis=1)
+    a = A0[:, :nu].cpu().numpy()
+    assert np.abs(a - A_ref).max() <= 1e-12 * np.abs(A_ref).max()
+    assert np.abs(b.cpu().numpy() - b_ref).max() <= 1e-12 * np.abs(b_ref).max()
+    ref = M.solve(st, w.model, w.omega_ev, w.pol_dirs, alpha_ib=w.alpha_ib)
+    om = w.omega_ev / M.HARTREE_EV
+    for f in range(2):
+        zq = M.z_q(om[f], st.n, st.tau)
+        shift = np.full(nu, zq, dtype=np.complex128)
+        if model == "wfqfmu":
+            shift[N:] = M.z_mu(w.alpha_ib[0, f])
+        A = A0[:, :nu].to(torch.complex128) - torch.diag(torch.from_numpy(shift).to(dev))
+        x = torch.linalg.solve(A, b.to(torch.complex128)).cpu().numpy()
+        q = x[:N]
+        mu = x[N:].reshape(N, 3, 3) if model == "wfqfmu" else None
+        alpha = M.dipole(st, q, mu)
+        assert np.abs(alpha - ref.alpha[f]).max() <= 1e-9 * np.abs(ref.alpha[f]).max()

@@ -120,14 +120,16 @@ def _golden(i, P):
     return fidx, a
 
 
-@pytest.mark.parametrize("precision", ["fp16split", "fp32"])
-def test_served_results_match_the_oracle(precision):
-    """Five requests (wFQ and wFQFmu, 893-5,287 atoms) submitted together to three slots;
+@pytest.mark.parametrize("precision,solver", [("fp16split", "batched"), ("fp32", "batched"),
+                                              ("fp32", "shifted")])
+def test_served_results_match_the_oracle(precision, solver):
+    """Five requests (wFQ and wFQFmu, 893-5,287 atoms) submitted together to three slots
+    (with the shifted solver, the wFQ requests run it and the wFQFmu ones stay batched);
     every served alpha within 1e-5 of the oracle (spectral route for wFQ, dense LU at three
     frequencies for wFQFmu), every column at its FP64-class tolerance."""
     from paper_2510_12731_gb300 import Server
     mix = S.serving_check_mix()
-    with Server(max_slots=3, precision=precision, tol_rel=1e-7) as srv:
+    with Server(max_slots=3, precision=precision, tol_rel=1e-7, solver=solver) as srv:
         ids = [srv.submit(w.model, w.xyz_ang, w.type_idx, w.types, w.omega_ev, w.pol_dirs,
                           w.alpha_ib) for w in mix]
         outs = [srv.wait(i, timeout_s=1800) for i in ids]
