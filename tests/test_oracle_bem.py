@@ -84,3 +84,77 @@ def test_f_rows_are_the_rows_of_f_matrix():
     rows = [0, 17, 299]
     full = BE.f_matrix(pos, nrm, area, 14.0)
     assert np.allclose(BE.f_rows(pos, nrm, area, 14.0, rows), full[rows], rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- IEFPCM (Eq. 12)
+def _ief_sphere(n, eps1):
+    pos, nrm, area = S.sphere_mesh(n, 20.0)
+    a, q, rel = BE.solve_iefpcm(pos, nrm, area, EPS2, eps1, np.eye(3), radius_ang=20.0)
+    rb = 20.0 / M.BOHR_ANG
+    assert rel.max() < 1e-12
+    return a, q, a[:, 0, 0] / (rb ** 3 * (EPS2 - eps1) / (EPS2 + 2 * eps1))
+
+
+@pytest.mark.parametrize("eps1", [1.0, 1.77])
+def test_iefpcm_sphere_converges_to_the_exact_quasistatic_polarisability(eps1):
+    _, _, r800 = _ief_sphere(800, eps1)
+    a, q, r3200 = _ief_sphere(3200, eps1)
+    e800, e3200 = np.abs(r800 - 1), np.abs(r3200 - 1)
+    assert np.all(e3200 < 0.6 * e800)            # first-order convergence in the mesh size
+    assert e3200.max() < 6e-3
+    assert np.abs(a[:, 1, 1] - a[:, 0, 0]).max() < 1e-5 * np.abs(a[:, 0, 0]).max()
+    assert np.abs(a[:, 0, 1]).max() < 1e-5 * np.abs(a[:, 0, 0]).max()
+    assert np.abs(q.sum(axis=2)).max() < 1e-4 * np.abs(q).sum(axis=2).max()
+
+
+def test_iefpcm_printed_diagonal_sign_converges_slowly():
+    """The reading's negative self term of F against the printed positive one."""
+    R = 20.0
+    pos, nrm, area = S.sphere_mesh(3200, R)
+    p, a_ = pos / M.BOHR_ANG, area / M.BOHR_ANG ** 2
+    F = BE.f_matrix_ief(p, nrm, a_, R / M.BOHR_ANG)
+    Fp = F.copy()
+    Fp[np.diag_indices_from(Fp)] *= -1.0
+    G = BE.g_matrix(p, a_)
+    e2 = -2.5 + 0.3j
+    lam = BE.lam(e2, 1.0)
+    V = -p[:, 0]
+    exact = (R / M.BOHR_ANG) ** 3 * (e2 - 1) / (e2 + 2)
+    errs = []
+    for FF in (F, Fp):
+        y = np.linalg.solve(lam * np.eye(len(V)) + FF, -(2 * np.pi * V + FF @ V).astype(complex))
+        errs.append(abs((p[:, 0] @ np.linalg.solve(G, y)) / exact - 1))
+    assert errs[0] < 5e-3 < 0.1 < errs[1]
+
+
+def test_iefpcm_weak_contrast_resonance_and_coulomb_matrix():
+    R = 20.0
+    pos, nrm, area = S.sphere_mesh(1600, R)
+    rb = R / M.BOHR_ANG
+    a, _, _ = BE.solve_iefpcm(pos, nrm, area, np.array([1.0 + 1e-6]), 1.0, np.eye(3)[:1],
+                              radius_ang=R)
+    assert a[0, 0, 0] / (rb ** 3 * 1e-6 / 3.0) == pytest.approx(1.0, abs=5e-3)
+    G = BE.g_matrix(pos / M.BOHR_ANG, area / M.BOHR_ANG ** 2)
+    assert np.array_equal(G, G.T) and np.linalg.eigvalsh(G).min() > 0   # Coulomb: SPD
+    w = S.drude_sphere_mesh(1600, nfreq=401, wmin=2.5, wmax=4.5, pols=np.eye(3)[:1])
+    a, _, _ = BE.solve_iefpcm(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1, w.pol_dirs,
+                              radius_ang=w.radius_ang)
+    assert w.omega_ev[np.argmax(a[:, 0, 0].imag)] == pytest.approx(6.0 / math.sqrt(3.0), abs=0.01)
+
+
+def test_iefpcm_spheroid_approaches_depolarisation_closed_form():
+    e2 = np.array([5.0 + 0.0j, -2.5 + 0.3j])
+    ab, cb = 10.0 / M.BOHR_ANG, 20.0 / M.BOHR_ANG
+    ecc = math.sqrt(1 - ab * ab / (cb * cb))
+    Lz = (1 - ecc * ecc) / (ecc * ecc) * (-1 + math.atanh(ecc) / ecc)
+    Lx = (1 - Lz) / 2
+    V = 4 * math.pi / 3 * ab * ab * cb
+    errs = []
+    for n in (1600, 3200):
+        pos, nrm, area = S.spheroid_mesh(n, 10.0, 10.0, 20.0)
+        a, _, _ = BE.solve_iefpcm(pos, nrm, area, e2, 1.0, np.eye(3))
+        az = V / (4 * math.pi) * (e2 - 1) / (1 + Lz * (e2 - 1))
+        ax = V / (4 * math.pi) * (e2 - 1) / (1 + Lx * (e2 - 1))
+        errs.append(np.concatenate([np.abs(a[:, 2, 2] / az - 1), np.abs(a[:, 0, 0] / ax - 1)]))
+    assert np.all(errs[1] < errs[0])
+    assert errs[1].max() < 0.12
