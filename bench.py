@@ -59,6 +59,14 @@ def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches, n_u=None):
         peaks, src = _measured_peaks()
         peak = float(peaks["bf16_tflops_sustained"])
         traffic = None
+        if mode == "matfree":
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": f"k_tc_mf (tcgen05 {prec} pair kernel: T tiles generated in shared "
+                              "memory, 3 MMAs per product)",
+                    "peak_source": f"bf16 dense sustained ({src}); algorithmic flops 4 n_u^2 B, "
+                                   "executed tensor flops are 3x",
+                    "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
         ratio = _profile_ratio("k_gemm_tc.cu", "k_tc_gemm_fp16split.md")
         if ratio is not None and n_u:
             # algorithmic bytes of the average launch: T hi + lo once, the hi/lo operand
@@ -728,7 +736,8 @@ def run_shifted_main(args, rank, world, local_rank):
 
 # ---------------------------------------------------------------- boundary elements
 def run_bem(args, rank, world, local_rank):
-    """Boundary-element (DPCM, Eq. 11) sweep: a Drude sphere meshed by --bem-tess tesserae,
+    """Boundary-element sweep (DPCM, Eq. 11, or IEFPCM, Eq. 12, by --bem-formulation): a
+    Drude sphere meshed by --bem-tess tesserae,
     200 frequencies x (x, y, z).  One step = px_set_mesh (Ft in FP64 and the solver's
     planes) + px_solve_bem of every column with the results copied to pinned host memory
     (the host-buffer call is the only one: value and e2e coincide except for the tesserae's
@@ -753,12 +762,12 @@ def run_bem(args, rank, world, local_rank):
                                       np.int32: torch.int32}[np.dtype(dtype).type], pin_memory=True)
         return t.numpy()
 
-    sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang)
+    sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang, args.bem_formulation)
     out_small = sv.alloc_outputs(F, P, want_q=False, want_mu=False, empty=pinned)
     out_full = sv.alloc_outputs(F, P, want_q=True, want_mu=False, empty=pinned)
 
     def step(out):
-        sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang)
+        sv.set_mesh(wl.pos_ang, wl.normals, wl.area_ang2, wl.radius_ang, args.bem_formulation)
         return sv.solve_bem(wl.omega_ev, wl.eps2, wl.eps1, wl.pol_dirs, out=out,
                             want_q=out is out_full)
 
@@ -828,14 +837,15 @@ def run_bem(args, rank, world, local_rank):
         4 * 8 * F + wl.pol_dirs.nbytes
     d2h = sum(v.nbytes for k, v in out_full.items() if isinstance(v, np.ndarray))
     if rank == 0:
-        line = {"metric": "BEM (DPCM) spectrum points/s", "value": whole_job_value(pts / args.steps, world, ms / args.steps),
+        line = {"metric": f"BEM ({args.bem_formulation.upper()}) spectrum points/s", "value": whole_job_value(pts / args.steps, world, ms / args.steps),
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warm,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": (DTYPES.get(prec, prec) if args.solver == "batched"
                           else "f32-pair (double-FP32) matvec, basis and orthogonalisation + f64 least squares"),
                 "data": "synthetic",
-                "config": {"workload": wl.name, "n_tesserae": n, "n_freq": F, "n_pol": P,
+                "config": {"workload": wl.name, "formulation": args.bem_formulation,
+                           "n_tesserae": n, "n_freq": F, "n_pol": P,
                            "columns": F * P, "tol_rel": wl.tol, "solver": args.solver,
                            "precision": prec,
                            "l2": "no flush: the operator planes are far larger than L2",
@@ -951,6 +961,8 @@ def main():
                     help="solver of the served wFQ requests (wFQFmu requests are batched)")
     ap.add_argument("--profile-run", dest="profile_run", action="store_true",
                     help="run one untimed step of the selected path and exit (for profilers)")
+    ap.add_argument("--bem-formulation", dest="bem_formulation", default="dpcm",
+                    choices=["dpcm", "iefpcm"], help="boundary-element formulation (Eq. 11 or 12)")
     ap.add_argument("--bem-tess", dest="bem_tess", type=int, default=20000,
                     help="tesserae of the boundary-element workload (--workload bem_sphere)")
     args = ap.parse_args()

@@ -353,38 +353,54 @@ px_status px_fields(px_handle* h, int n_points, const double* points_ang, int n_
 px_status px_system_device(px_handle* h, int n_pol, const double* pol_dir, double e0,
                            double* d_A0, size_t ld_A0, double* d_b, void* cuda_stream);
 
-/* Boundary-element (DPCM) surface of a dielectric or metal particle (Sec. 2.3, Eq. 11):
- * replaces any loaded structure.  Tessera i has barycentre s_i, outward unit normal n_i
- * and area A_i; the unknowns are the surface charge densities sigma_i.  The library
- * solves the normal-field form of Eq. 11,
+/* Boundary-element formulations (Sec. 2.3). */
+typedef enum {
+  PX_BEM_DPCM = 0,    /* Eq. 11 */
+  PX_BEM_IEFPCM = 1   /* Eq. 12 */
+} px_bem_formulation;
+
+/* Boundary-element surface of a dielectric or metal particle (Sec. 2.3): replaces any
+ * loaded structure.  Tessera i has barycentre s_i, outward unit normal n_i and area A_i.
+ * PX_BEM_DPCM solves the normal-field form of Eq. 11 for the surface charge densities,
  *   (Ft - Lambda(w) I) sigma = -E0 e . n,   Lambda(w) = 2 pi (e2 + e1)/(e2 - e1),
- *   Ft_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j),
- *   Ft_ii = 1.0694 sqrt(4 pi A_i) / (2 R),
+ *   Ft_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j),  Ft_ii = +1.0694 sqrt(4 pi A_i)/(2R),
  * which is the printed equation read dimensionally (the area matrix on the diagonal term
- * dropped, F taken with the receiving tessera's normal); on a sphere it converges to the
- * exact quasistatic polarisability R^3 (e2 - e1)/(e2 + 2 e1).  Ft is dense and
- * frequency-independent, so it is built once (FP64, plus the planes the selected
- * precision and solver read), and every frequency is a column shift Lambda(w), exactly
- * as z_q(w) in Eq. 1: both PX_SOLVER_BATCHED and PX_SOLVER_SHIFTED apply.
- *   pos_ang     host [n_tess][3] barycentres, Angstrom
- *   normals     host [n_tess][3] outward unit normals
- *   area_ang2   host [n_tess] areas, Angstrom^2 (> 0)
- *   radius_ang  R of the self term: the radius of the sphere enclosing the mesh, Angstrom
- * PX_EINVAL for NULL / non-finite inputs, non-unit normals, non-positive areas or R;
- * PX_ENOTIMPL in PX_MODE_MATFREE; PX_ENOMEM when the n_tess^2 operator planes do not fit.
- * Tesserae keep the caller's order.  px_fields, px_system_device and
- * px_relres_device_noalloc return PX_ENOTIMPL while a mesh is loaded. */
+ * dropped, F taken with the receiving tessera's normal).  PX_BEM_IEFPCM solves Eq. 12 for
+ * the tesserae's charges q in two steps,
+ *   (F + Lambda(w) I) y = -(2 pi I + F) V,   then   (S A^-1) q = y,
+ *   F_ij = A_j (s_i - s_j).n_j / |s_i - s_j|^3 (i != j),  F_ii = -1.0694 sqrt(4 pi A_i)/(2R),
+ *   (S A^-1)_ij = 1/|s_i - s_j| (i != j),  (S A^-1)_ii = 1.0694 sqrt(4 pi / A_i),
+ *   V_i = -E0 e . s_i,
+ * with the self term of F taken with the sign of the off-diagonal double-layer sum (with
+ * the printed positive sign a refined sphere converges only slowly).  Both converge on a
+ * sphere to the exact quasistatic polarisability R^3 (e2 - e1)/(e2 + 2 e1).  The operators
+ * are dense and frequency-independent, built once in FP64 (plus the planes the selected
+ * precision and solver read), and every frequency is a column shift, exactly as z_q(w) in
+ * Eq. 1: PX_SOLVER_BATCHED and PX_SOLVER_SHIFTED both apply to DPCM and to IEFPCM's first
+ * step; the second step (complex right-hand sides) runs batched.
+ *   pos_ang      host [n_tess][3] barycentres, Angstrom
+ *   normals      host [n_tess][3] outward unit normals
+ *   area_ang2    host [n_tess] areas, Angstrom^2 (> 0)
+ *   radius_ang   R of the self term: the radius of the sphere enclosing the mesh, Angstrom
+ *   formulation  PX_BEM_DPCM or PX_BEM_IEFPCM
+ * PX_EINVAL for NULL / non-finite inputs, non-unit normals, non-positive areas or R, or an
+ * unknown formulation; PX_ENOTIMPL in PX_MODE_MATFREE; PX_ECUDA when the n_tess^2 operator
+ * planes (two operators for IEFPCM) do not fit.  Tesserae keep the caller's order.
+ * px_fields, px_system_device and px_relres_device_noalloc return PX_ENOTIMPL while a
+ * mesh is loaded. */
 px_status px_set_mesh(px_handle* h, int n_tess, const double* pos_ang, const double* normals,
-                      const double* area_ang2, double radius_ang);
+                      const double* area_ang2, double radius_ang, int formulation);
 
 /* Solve the loaded mesh (px_set_mesh) for F frequencies x P field directions.
  *   omega_ev  host [F] frequencies, eV (> 0; they enter sigma_abs only)
  *   eps       host [F][4] doubles: Re e2, Im e2, Re e1, Im e1 -- the particle's and the
  *             medium's permittivities at each frequency (finite, e2 != e1)
- * Everything else is as in px_solve: out->q holds the tesserae's charges A_i sigma_i
- * (there are no dipoles: out->mu is left untouched), out->alpha the dipole
- * sum_i A_i sigma_i s_i / E0 (bohr^3), out->sigma_abs 4 pi w/(3c) Im Tr(alpha) for three
- * independent directions.  PX_EINVAL when no mesh is loaded. */
+ * Everything else is as in px_solve: out->q holds the tesserae's charges (A_i sigma_i for
+ * DPCM; there are no dipoles: out->mu is left untouched), out->alpha the dipole
+ * sum_i q_i s_i / E0 (bohr^3), out->sigma_abs 4 pi w/(3c) Im Tr(alpha) for three
+ * independent directions.  For IEFPCM rel_residual is the larger of the two steps'
+ * relative residuals, iters their sum, and the statistics cover both steps.
+ * PX_EINVAL when no mesh is loaded. */
 px_status px_solve_bem(px_handle* h, int n_freq, const double* omega_ev, const double* eps,
                        int n_pol, const double* pol_dir, double e0, px_result* out,
                        void* cuda_stream);

@@ -102,16 +102,18 @@ class Solver:
         self.model = m
         self.natoms = xyz.shape[0]
 
-    def set_mesh(self, pos_ang, normals, area_ang2, radius_ang):
-        """Boundary-element surface (Sec. 2.3, Eq. 11): barycentres (n, 3) Angstrom, outward
-        unit normals (n, 3), areas (n,) Angstrom^2, enclosing radius R (Angstrom)."""
+    def set_mesh(self, pos_ang, normals, area_ang2, radius_ang, formulation="dpcm"):
+        """Boundary-element surface (Sec. 2.3): barycentres (n, 3) Angstrom, outward unit
+        normals (n, 3), areas (n,) Angstrom^2, enclosing radius R (Angstrom);
+        formulation "dpcm" (Eq. 11) or "iefpcm" (Eq. 12)."""
         pos = np.ascontiguousarray(pos_ang, dtype=np.float64).reshape(-1, 3)
         nrm = np.ascontiguousarray(normals, dtype=np.float64).reshape(-1, 3)
         area = np.ascontiguousarray(area_ang2, dtype=np.float64).reshape(-1)
         if nrm.shape != pos.shape or area.size != pos.shape[0]:
             raise ValueError("pos_ang, normals and area_ang2 describe different meshes")
+        form = L.BEM_FORMULATIONS[formulation] if isinstance(formulation, str) else int(formulation)
         self._check(self._lib.px_set_mesh(self._h, pos.shape[0], L.dptr(pos), L.dptr(nrm),
-                                          L.dptr(area), float(radius_ang)))
+                                          L.dptr(area), float(radius_ang), form))
         self.model = L.PX_WFQ   # one scalar unknown per tessera, no dipoles
         self.natoms = pos.shape[0]
 

@@ -28,6 +28,8 @@ MODES = {"auto": PX_MODE_AUTO, "matfree": PX_MODE_MATFREE, "materialised": PX_MO
 BASES = {"auto": PX_BASIS_AUTO, "fp64": PX_BASIS_FP64, "ff32": PX_BASIS_FF32, "fp32": PX_BASIS_FP32}
 PX_SOLVER_BATCHED, PX_SOLVER_SHIFTED = 0, 1
 SOLVERS = {"batched": PX_SOLVER_BATCHED, "shifted": PX_SOLVER_SHIFTED}
+PX_BEM_DPCM, PX_BEM_IEFPCM = 0, 1
+BEM_FORMULATIONS = {"dpcm": PX_BEM_DPCM, "iefpcm": PX_BEM_IEFPCM}
 
 
 class AtomType(C.Structure):
@@ -112,7 +114,7 @@ SIGNATURES = {
                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "px_system_device": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_double, C.c_void_p, C.c_size_t,
                                    C.c_void_p, C.c_void_p]),
-    "px_set_mesh": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double]),
+    "px_set_mesh": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, C.c_double, C.c_int]),
     "px_solve_bem": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, C.c_int, _dp, C.c_double,
                                C.POINTER(Result), C.c_void_p]),
     "px_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),

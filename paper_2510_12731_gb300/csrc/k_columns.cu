@@ -228,9 +228,11 @@ __global__ void k_init_residual_c(const double2* bc, int nu, int B, const double
   }
 }
 
-// Boundary elements (Sec. 2.3): the scalar shift of every column, Lambda(w_f) =
-// 2 pi (e2 + e1) / (e2 - e1) (Eq. 11), and the right-hand side b_i = -E0 e_p . n_i.
-__global__ void k_bem_shifts(int F, int P, const double* eps, double2* zq) {
+// Boundary elements (Sec. 2.3): the scalar shift of every column from Lambda(w_f) =
+// 2 pi (e2 + e1) / (e2 - e1): z = +Lambda for DPCM, (Ft - Lambda I) sigma = -E0 e . n
+// (Eq. 11); z = -Lambda for the first IEFPCM step, (F + Lambda I) y = c (Eq. 12); z = 0 for
+// the second, (S A^-1) q = y.
+__global__ void k_bem_shifts(int F, int P, const double* eps, double sign, double2* zq) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= F * P) return;
   const int f = c / P;
@@ -239,9 +241,11 @@ __global__ void k_bem_shifts(int F, int P, const double* eps, double2* zq) {
   const double2 num = make_double2(e2.x + e1.x, e2.y + e1.y);
   const double2 den = make_double2(e2.x - e1.x, e2.y - e1.y);
   const double2 q = cdiv(num, den);
-  zq[c] = make_double2(2.0 * 3.141592653589793 * q.x, 2.0 * 3.141592653589793 * q.y);
+  const double k = sign * 2.0 * 3.141592653589793;
+  zq[c] = make_double2(k * q.x, k * q.y);
 }
 
+// DPCM right-hand side b_i = -E0 e_p . n_i
 __global__ void k_rhs_bem(int n, const double* nrm, const double* pol, int P, double e0, double* b) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * P) return;
@@ -249,13 +253,39 @@ __global__ void k_rhs_bem(int n, const double* nrm, const double* pol, int P, do
   b[idx] = -e0 * (pol[3 * p] * nrm[3 * i] + pol[3 * p + 1] * nrm[3 * i + 1] + pol[3 * p + 2] * nrm[3 * i + 2]);
 }
 
+// IEFPCM right-hand side c = -(2 pi I + F) V with V_j = -E0 e_p . s_j, i.e.
+// c_i = E0 (2 pi e_p . s_i + sum_j F_ij e_p . s_j); F is stored transposed (S[j][i] = F_ij),
+// so thread i walks column i of S (coalesced across the block's threads).
+__global__ void __launch_bounds__(128) k_rhs_ief(int n, int np, const double* __restrict__ S,
+                                                 const double* __restrict__ pos,
+                                                 const double* __restrict__ pol, int P, double e0,
+                                                 double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  const double ex = pol[3 * p], ey = pol[3 * p + 1], ez = pol[3 * p + 2];
+  double acc = 0.0;
+  if (i < n)
+    for (int j = 0; j < n; ++j)
+      acc = fma(S[(size_t)j * np + i], ex * pos[3 * j] + ey * pos[3 * j + 1] + ez * pos[3 * j + 2], acc);
+  if (i < n)
+    b[(size_t)i * P + p] =
+        e0 * (2.0 * 3.141592653589793 * (ex * pos[3 * i] + ey * pos[3 * i + 1] + ez * pos[3 * i + 2]) + acc);
+}
+
 }  // namespace
 
-cudaError_t launch_bem_setup(int F, int P, int n, const double* eps, const double* nrm,
+cudaError_t launch_bem_setup(int F, int P, int n, int np, int stage, const double* eps,
+                             const double* nrm, const double* S, const double* pos,
                              const double* pol, double e0, double2* zq, double* b, cudaStream_t s,
                              long long* nl) {
-  k_bem_shifts<<<(F * P + 127) / 128, 128, 0, s>>>(F, P, eps, zq);
-  k_rhs_bem<<<(n * P + 255) / 256, 256, 0, s>>>(n, nrm, pol, P, e0, b);
+  if (stage == 2) {
+    cudaError_t e = cudaMemsetAsync(zq, 0, sizeof(double2) * (size_t)F * P, s);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  k_bem_shifts<<<(F * P + 127) / 128, 128, 0, s>>>(F, P, eps, stage == 0 ? 1.0 : -1.0, zq);
+  if (stage == 0) k_rhs_bem<<<(n * P + 255) / 256, 256, 0, s>>>(n, nrm, pol, P, e0, b);
+  else k_rhs_ief<<<dim3((n + 127) / 128, P), 128, 0, s>>>(n, np, S, pos, pol, P, e0, b);
   *nl += 2;
   return cudaGetLastError();
 }

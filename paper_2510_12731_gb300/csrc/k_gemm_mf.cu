@@ -14,8 +14,9 @@ namespace px {
 
 namespace {
 
-constexpr float kSqrt2OverPiF = 0.79788456080286536f;
 constexpr double kSqrt2OverPiD = 0.7978845608028654;
+using radial::kSqrt2OverPiF;
+using radial::tqq_f;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -23,19 +24,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n"); }
-
-// pos: x, y, z (bohr, FP32) and R_q^2
-__device__ __forceinline__ float tqq_f(float4 a, float4 b, bool same) {
-  if (same) return kSqrt2OverPiF * rsqrtf(a.w);
-  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float R2 = a.w + b.w;
-  if (r2 < 16.0f * R2) {
-    const float r = sqrtf(r2);
-    return erff(r * rsqrtf(R2)) / r;
-  }
-  return rsqrtf(r2);
-}
 
 __global__ void __launch_bounds__(256, 2)
 k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, int ldx,

@@ -491,3 +491,275 @@ int tc_tuned_variant(int np, int ncols, bool f16) {
 }
 
 }  // namespace px
+
+#include "px_radial.cuh"
+
+namespace px {
+
+// ---------------------------------------------------------------- on-the-fly pair kernel
+// Matrix-free wFQ block matvec Y = T X on the tensor cores: the T tile of every 64-atom K
+// step is generated from the atom positions (Eq. 5, radial::tqq_f in FP32) by eight
+// generator warps straight into shared memory, as the hi / lo planes of the split (the
+// layout a 128-byte-swizzled TMA load would produce), and contracted with the X tiles
+// (TMA) by tcgen05.mma exactly as in k_tc_gemm; nothing of T is stored.
+//   warp 0        TMA producer of the X hi / lo tiles (BN x 64 per K step)
+//   warp 1        MMA issuer (one elected thread, 4 x 3 MMAs per K step)
+//   warp 2        TMEM allocation
+//   warps 4-11    generators: 128 rows x 64 atoms per K step, 8 consecutive atoms (one
+//                 16-byte chunk of each plane) per thread and row, 4 rows per thread;
+//                 then warps 4-7 run the epilogue
+// A stage is full when the TMA bytes landed and all eight generator warps arrived (each
+// after a proxy fence, so the tensor core sees the generic-proxy stores).
+// FP16 split: T' = 2^e T (2^e max|T| <= 2^14, max|T| = sqrt(2/pi)/min R_q), hi = RN(T'),
+// lo = RN((T' - hi) 2^11); the epilogue returns Y = D1 2^-(e+8) + D2 2^-(e+19) (X' = 2^8 X).
+// BF16 split: hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
+// Atoms beyond n generate 0.
+namespace {
+
+template <int F16, int TC_BN, int TC_STAGES>
+__global__ void __launch_bounds__(384, 1)
+k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
+        const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+        float* __restrict__ Y, int ldy, int K, float s1, float s2, int* err) {
+  using Cfg = TcCfg<TC_BN, TC_STAGES>;
+  constexpr int B_TILE = Cfg::B_TILE, STAGE = Cfg::STAGE, TC_TMEM_COLS = Cfg::TMEM_COLS;
+  constexpr uint32_t kIdescF16 = idesc<TC_BN>(true), kIdescBF16 = idesc<TC_BN>(false);
+  constexpr int kGenWarps = 8;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE);
+  uint64_t* full = bars;                    // [TC_STAGES]: TMA + 8 generator warps
+  uint64_t* empty = bars + TC_STAGES;       // [TC_STAGES]: MMA commit
+  uint64_t* accum = bars + 2 * TC_STAGES;   // [1]
+  __shared__ uint32_t tmem_slot;
+  __shared__ int cta_abort;
+  __shared__ int n_issued, n_consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * TC_BM, c0 = blockIdx.x * TC_BN;
+  const int nk = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1 + kGenWarps);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    cta_abort = 0;
+    n_issued = 0;
+    n_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_flag = &cta_abort;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (operand tiles)
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      unsigned char* st = base + s * STAGE;
+      mbar_expect_tx(&full[s], 2 * B_TILE);
+      const int kx = kt * TC_BK;
+      tma_load_2d(st + 2 * A_TILE, &mXh, &full[s], kx, c0);
+      tma_load_2d(st + 2 * A_TILE + B_TILE, &mXl, &full[s], kx, c0);
+      n_issued = kt + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, err, abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = su32(base + s * STAGE);
+      const uint64_t ah = sdesc(st), al = sdesc(st + A_TILE);
+      const uint64_t bh = sdesc(st + 2 * A_TILE), bl = sdesc(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        const uint64_t dk = (uint64_t)(kk * 32) >> 4;
+        const uint32_t first = (kt | kk) ? 1u : 0u;
+        if (F16) {
+          mma_f16(tmem, ah + dk, bh + dk, kIdescF16, first);
+          mma_f16(tmem + TC_BN, ah + dk, bl + dk, kIdescF16, first);
+          mma_f16(tmem + TC_BN, al + dk, bh + dk, kIdescF16, 1u);
+        } else {
+          mma_f16(tmem, ah + dk, bh + dk, kIdescBF16, first);
+          mma_f16(tmem, ah + dk, bl + dk, kIdescBF16, 1u);
+          mma_f16(tmem, al + dk, bh + dk, kIdescBF16, 1u);
+        }
+      }
+      mma_commit(&empty[s]);
+      n_consumed = kt + 1;
+    }
+    mma_commit(accum);
+  } else if (warp >= 4) {
+    // ---------------- generators: T tiles in the swizzled K-major layout
+    const int gt = threadIdx.x - 128;            // 0 .. 255
+    const int c = gt & 7;                        // 16-byte chunk (8 atoms) of the 64-atom step
+    const int rb = gt >> 3;                      // rows rb, rb + 32, rb + 64, rb + 96
+    float4 pi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + rb + 32 * u;
+      pi[u] = i < n ? pos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+    const uint32_t sw = (uint32_t)((c ^ (rb & 7)) << 4);   // (row & 7) == (rb & 7) for all 4 rows
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      unsigned char* sth = base + s * STAGE;
+      unsigned char* stl = sth + A_TILE;
+      const int kb = kt * TC_BK + c * 8;
+      float4 pk[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        pk[e] = kb + e < n ? __ldg(pos + kb + e) : make_float4(0.f, 0.f, 0.f, 1.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = rb + 32 * u;
+        const int i = i0 + r;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          float t[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int k = kb + e + q;
+            t[q] = (i < n && k < n) ? radial::tqq_f(pi[u], pk[e + q], i == k) : 0.f;
+          }
+          uint16_t h[2], l[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (F16) {
+              const float v = t[q] * tscale;
+              const __half hh = __float2half_rn(v);
+              h[q] = __half_as_ushort(hh);
+              l[q] = __half_as_ushort(__float2half_rn((v - __half2float(hh)) * 2048.0f));
+            } else {
+              const __nv_bfloat16 hh = __float2bfloat16_rn(t[q]);
+              h[q] = __bfloat16_as_ushort(hh);
+              l[q] = __bfloat16_as_ushort(__float2bfloat16_rn(t[q] - __bfloat162float(hh)));
+            }
+          }
+          hw[e / 2] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+          lw[e / 2] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+        }
+        const uint32_t off = (uint32_t)r * 128u + sw;
+        *reinterpret_cast<uint4*>(sth + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(stl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      // make the generic-proxy stores visible to the tensor core, then one arrival per warp
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
+    }
+    if (warp < 8) {
+      // ---------------- epilogue: TMEM -> registers -> Y
+      const bool ok = mbar_wait(accum, 0, err, abort_flag);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int wq = warp & 3;
+      const int row = i0 + wq * 32 + lane;
+      if (ok && !*abort_flag) {
+        float* yr = Y + (size_t)row * ldy + c0;
+#pragma unroll 1
+        for (int cc = 0; cc < TC_BN; cc += 32) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)cc;
+          TMEM_LD32(taddr, v);
+          if (F16) {
+            uint32_t v2[32];
+            TMEM_LD32(taddr + TC_BN, v2);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              v[q] = __float_as_uint(fmaf(__uint_as_float(v2[q]), s2, __uint_as_float(v[q]) * s1));
+          } else {
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(yr + cc + 4 * q) =
+                make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (cta_abort && threadIdx.x == 0) {
+    // after a time-out: wait (bounded) for operand loads that were issued but never consumed
+    for (int kt = n_consumed; kt < n_issued; ++kt) {
+      const long long t0 = clock64();
+      while (!mbar_try(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS));
+  }
+}
+
+template <int F16, int BN, int ST>
+cudaError_t launch_mf_variant(const float4* pos, int n, float tscale, const CUtensorMap& mXh,
+                              const CUtensorMap& mXl, int np, int ncols, float* Y, int ldy,
+                              float s1, float s2, int* err, cudaStream_t s) {
+  static bool attr = false;   // per process: every device uses the same attribute
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<BN, ST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grd(ncols / BN, np / TC_BM);
+  k_tc_mf<F16, BN, ST><<<grd, 384, TcCfg<BN, ST>::SMEM, s>>>(pos, n, tscale, mXh, mXl, Y, ldy, np,
+                                                             s1, s2, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_mf(const float4* pos, int n, int np, const uint16_t* Xh, const uint16_t* Xl,
+                         int ncols, float* Y, int ldy, bool f16, int scale_exp, int* err,
+                         cudaStream_t s, long long* nl) {
+  // shape contract as launch_tc_gemm: 128-row output tiles and 64-atom K steps (np % 128),
+  // 128- or 256-column operand tiles, 16-byte aligned operand rows
+  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols || n > np) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
+    return cudaErrorMisalignedAddress;
+  const int bn = ncols % 256 == 0 ? 256 : 128;
+  CUtensorMap mXh, mXl;
+  if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
+    return cudaErrorInvalidValue;
+  const float tscale = std::ldexp(1.0f, scale_exp);
+  const float s1 = std::ldexp(1.0f, -(scale_exp + 8)), s2 = std::ldexp(1.0f, -(scale_exp + 19));
+  cudaError_t e;
+  if (f16)
+    e = bn == 256 ? launch_mf_variant<1, 256, 2>(pos, n, tscale, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                  : launch_mf_variant<1, 128, 3>(pos, n, tscale, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+  else
+    e = bn == 256 ? launch_mf_variant<0, 256, 2>(pos, n, 1.0f, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
+                  : launch_mf_variant<0, 128, 3>(pos, n, 1.0f, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
+  ++*nl;
+  return e;
+}
+
+}  // namespace px

@@ -949,6 +949,13 @@ cudaError_t launch_rhs_hetero(int N, int F, int P, const int* rowptr, const int*
   return cudaGetLastError();
 }
 
+cudaError_t launch_col_norms_c(const double2* bc, int nu, int B, double* bn, cudaStream_t s,
+                               long long* nl) {
+  k_col_norms_c<<<B, 256, 0, s>>>(bc, nu, B, bn);
+  ++*nl;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dots(const KrylovArgs& a, int j, int pass, cudaStream_t s, long long* nl) {
   with_basis(a.basis, [&](auto e) {
     k_dots<decltype(e)><<<col_grid(a.Bact, a.nblk), dim3(32, 8), 0, s>>>(a, j);

@@ -172,6 +172,103 @@ __global__ void k_sk_combine(int n, int np, int NP, int S, const float2* __restr
   U[idx] = make_float2(h, l);
 }
 
+// The same product for an operator stored transposed (planes hold S = T^T, so
+// U[i][p] = sum_k S[k][i] v[k][p]): part[sg][i][p] sums the rows k of row segment sg, for
+// work items (128-column block, row segment).  Each stage holds 32 rows x 128 columns of both
+// planes and the operand's 32 rows; warp w takes rows 4w .. 4w+3 of the stage, lane l the
+// columns 4l .. 4l+3 (coalesced along the stored rows); the eight warps' double-FP32 sums
+// are added through shared memory at the end of the item.
+template <int NP>
+__global__ void __launch_bounds__(256, 2)
+k_sk_matvec_t(const float* __restrict__ Th, const float* __restrict__ Tl, int np, int St,
+              int seg_rows, const float* __restrict__ vp, float2* __restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int kSt = mv_stage_floats<NP>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ncb = np / kMvCols;
+  const int items = ncb * St;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int cb = item % ncb, sg = item / ncb;
+    const int r_begin = sg * seg_rows;
+    const int r_end = min(np, r_begin + seg_rows);
+    const int nch = (r_end - r_begin) / 32;
+    auto issue = [&](int ch) {
+      float* st = smem + (ch % kMvStages) * kSt;
+      const int r0 = r_begin + ch * 32;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int id = threadIdx.x + 256 * q;
+        const int pl = id >> 10, row = (id >> 5) & 31, c16 = id & 31;
+        const float* src = (pl ? Tl : Th) + (size_t)(r0 + row) * np + cb * kMvCols + c16 * 4;
+        cp_async16(st + (pl * 32 + row) * kMvCols + c16 * 4, src);
+      }
+      // operand rows r0 .. r0+31: 2 NP planes x 8 chunks of 16 bytes
+      if ((int)threadIdx.x < 2 * NP * 8) {
+        const int pl = threadIdx.x >> 3, c16 = threadIdx.x & 7;
+        cp_async16(st + 2 * 32 * kMvCols + pl * 32 + c16 * 4, vp + (size_t)pl * np + r0 + c16 * 4);
+      }
+    };
+    float ah[4][NP], al[4][NP];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int p = 0; p < NP; ++p) ah[c][p] = al[c][p] = 0.f;
+#pragma unroll
+    for (int c = 0; c < kMvStages - 1; ++c) {
+      if (c < nch) issue(c);
+      cp_async_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+      if (c + kMvStages - 1 < nch) issue(c + kMvStages - 1);
+      cp_async_commit();
+      cp_async_wait<kMvStages - 1>();
+      __syncthreads();
+      const float* st = smem + (c % kMvStages) * kSt;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int k = warp * 4 + rr;
+        const float4 th = *reinterpret_cast<const float4*>(st + k * kMvCols + lane * 4);
+        const float4 tl = *reinterpret_cast<const float4*>(st + (32 + k) * kMvCols + lane * 4);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float xh = st[2 * 32 * kMvCols + (2 * p) * 32 + k];
+          const float xl = st[2 * 32 * kMvCols + (2 * p + 1) * 32 + k];
+          ff::mac(ah[0][p], al[0][p], th.x, tl.x, xh, xl);
+          ff::mac(ah[1][p], al[1][p], th.y, tl.y, xh, xl);
+          ff::mac(ah[2][p], al[2][p], th.z, tl.z, xh, xl);
+          ff::mac(ah[3][p], al[3][p], th.w, tl.w, xh, xl);
+        }
+      }
+      if ((c & 7) == 7)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+          for (int p = 0; p < NP; ++p) ff::renorm(ah[cc][p], al[cc][p]);
+      __syncthreads();
+    }
+    // add the eight warps' sums: red[w][column][p] (hi, lo) in the ring's space
+    cp_async_wait<0>();
+    __syncthreads();
+    float2* red = reinterpret_cast<float2*>(smem);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        red[((size_t)warp * kMvCols + lane * 4 + cc) * NP + p] = make_float2(ah[cc][p], al[cc][p]);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kMvCols * NP; t += blockDim.x) {
+      float h = 0.f, l = 0.f;
+      for (int w = 0; w < 8; ++w) {
+        const float2 a = red[(size_t)w * kMvCols * NP + t];
+        ff::add(h, l, a.x, a.y);
+      }
+      const int col = t / NP, p = t - col * NP;
+      part[((size_t)sg * np + cb * kMvCols + col) * NP + p] = make_float2(h, l);
+    }
+    __syncthreads();
+  }
+}
+
 // W[i][p] = (Kbar U)_i = sum_j K_ij (U_j - U_i)  (Eq. 2) in double-FP32: the differences by
 // TwoSum, K_ij = val32 + its FP32 remainder, products by TwoProduct (the FP64 pipe is
 // 1/64 of the FP32 rate).  Eight lanes share a row (each takes every eighth neighbour),
@@ -706,26 +803,39 @@ SkMatvecPlan sk_matvec_plan(int np) {
   const int seg_tiles = (tiles + S - 1) / S;
   pl.seg_cols = seg_tiles * 128;
   pl.S = (tiles + seg_tiles - 1) / seg_tiles;
+  // transposed operator: (128-column block, row segment) items, segments >= 128 rows
+  const int ncb = np / 128;
+  int St = (16 * pl.grid + ncb - 1) / ncb;
+  St = std::max(1, std::min(St, np / 128));
+  const int rblocks = np / 32;
+  const int seg_rb = (rblocks + St - 1) / St;
+  pl.seg_rows = seg_rb * 32;
+  pl.St = (rblocks + seg_rb - 1) / seg_rb;
   return pl;
 }
 
 cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, int NP,
-                             const SkMatvecPlan& pl, const float* vp, float2* part, float2* U,
-                             cudaStream_t s, long long* nl) {
+                             const SkMatvecPlan& pl, bool trans, const float* vp, float2* part,
+                             float2* U, cudaStream_t s, long long* nl) {
   if (np % 128 || NP < 1 || NP > 4) return cudaErrorInvalidValue;
   cudaError_t err = cudaSuccess;
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
     const int shm = kMvStages * mv_stage_floats<K>() * (int)sizeof(float);
-    static bool attr_set[5] = {false, false, false, false, false};
-    if (!attr_set[K]) {
-      err = cudaFuncSetAttribute(k_sk_matvec<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-      attr_set[K] = err == cudaSuccess;
+    static bool attr_set[2][5] = {{false, false, false, false, false},
+                                  {false, false, false, false, false}};
+    const int t = trans ? 1 : 0;
+    if (!attr_set[t][K]) {
+      err = trans ? cudaFuncSetAttribute(k_sk_matvec_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm)
+                  : cudaFuncSetAttribute(k_sk_matvec<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+      attr_set[t][K] = err == cudaSuccess;
     }
-    if (err == cudaSuccess) k_sk_matvec<K><<<pl.grid, 256, shm, s>>>(Th, Tl, np, pl.S, pl.seg_cols, vp, part);
+    if (err != cudaSuccess) return;
+    if (trans) k_sk_matvec_t<K><<<pl.grid, 256, shm, s>>>(Th, Tl, np, pl.St, pl.seg_rows, vp, part);
+    else k_sk_matvec<K><<<pl.grid, 256, shm, s>>>(Th, Tl, np, pl.S, pl.seg_cols, vp, part);
   });
   if (err != cudaSuccess) return err;
-  k_sk_combine<<<(n * NP + 255) / 256, 256, 0, s>>>(n, np, NP, pl.S, part, U);
+  k_sk_combine<<<(n * NP + 255) / 256, 256, 0, s>>>(n, np, NP, trans ? pl.St : pl.S, part, U);
   *nl += 2;
   return cudaGetLastError();
 }

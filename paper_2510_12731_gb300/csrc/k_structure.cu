@@ -444,33 +444,104 @@ cudaError_t launch_unpermute_system(const double* M, int np, int nu, int N, cons
 }
 
 namespace {
-// DPCM operator of a meshed surface (Sec. 2.3, Eq. 11, normal-field form):
-// Ft_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j), Ft_ii = 1.0694 sqrt(4 pi A_i) / (2R).
+// Boundary-element operators of a meshed surface (Sec. 2.3).  Ft is not symmetric, and
+// the FP32 / FP64 / double-FP32 block matvecs read row k of the stored operator as column
+// k of the applied one (exact for the symmetric T of Eqs. 1 and 7), so these operators are
+// stored transposed: S[j][i] = Op[i][j].
+//   DPCM (Eq. 11, normal-field form): Op_ij = A_j (s_i - s_j).n_i / |s_i - s_j|^3 (i != j),
+//     Op_ii = +1.0694 sqrt(4 pi A_i) / (2R);
+//   IEFPCM (Eq. 12): Op_ij = A_j (s_i - s_j).n_j / |s_i - s_j|^3 (i != j),
+//     Op_ii = -1.0694 sqrt(4 pi A_i) / (2R)  (the sign of the off-diagonal double-layer sum).
 __global__ void k_build_F(const double* __restrict__ pos, const double* __restrict__ nrm,
-                          const double* __restrict__ area, double R, int n, int ld, double* F) {
+                          const double* __restrict__ area, double R, int n, int ld, int ief,
+                          double* S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // row of Op, column of S
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  double v;
+  if (i == j) {
+    v = 1.0694 * sqrt(4.0 * 3.141592653589793 * area[i]) / (2.0 * R);
+    if (ief) v = -v;
+  } else {
+    const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                 dz = pos[3 * i + 2] - pos[3 * j + 2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const int t = ief ? j : i;
+    const double dn = dx * nrm[3 * t] + dy * nrm[3 * t + 1] + dz * nrm[3 * t + 2];
+    v = area[j] * dn / (r2 * sqrt(r2));
+  }
+  S[(size_t)j * ld + i] = v;
+}
+
+// S A^-1 of Eq. 12 (the Coulomb matrix of the tesserae, symmetric): 1/|s_i - s_j| off the
+// diagonal, 1.0694 sqrt(4 pi / A_i) on it.
+__global__ void k_build_G(const double* __restrict__ pos, const double* __restrict__ area, int n,
+                          int ld, double* G) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
   double v;
   if (i == j) {
-    v = 1.0694 * sqrt(4.0 * 3.141592653589793 * area[i]) / (2.0 * R);
+    v = 1.0694 * sqrt(4.0 * 3.141592653589793 / area[i]);
   } else {
     const double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
                  dz = pos[3 * i + 2] - pos[3 * j + 2];
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    const double dn = dx * nrm[3 * i] + dy * nrm[3 * i + 1] + dz * nrm[3 * i + 2];
-    v = area[j] * dn / (r2 * sqrt(r2));
+    v = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
   }
-  F[(size_t)i * ld + j] = v;
+  G[(size_t)i * ld + j] = v;
+}
+
+// M = S^T through 32 x 32 shared-memory tiles, and max |M| (integer atomicMax on the bits
+// of the non-negative double).
+__global__ void __launch_bounds__(256) k_transpose_absmax(const double* __restrict__ S, int np,
+                                                          double* M, unsigned long long* absmax_bits) {
+  __shared__ double tile[32][33];
+  __shared__ double sh[8];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double amax = 0.0;
+  for (int r = ty; r < 32; r += 8) tile[r][tx] = S[(size_t)(by + r) * np + bx + tx];
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const double v = tile[tx][r];
+    M[(size_t)(bx + r) * np + by + tx] = v;
+    amax = fmax(amax, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (tx == 0) sh[ty] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < 8; ++w) m = fmax(m, sh[w]);
+    atomicMax(absmax_bits, (unsigned long long)__double_as_longlong(m));
+  }
 }
 }  // namespace
 
 cudaError_t launch_build_F(const double* pos, const double* nrm, const double* area, double R,
-                           int n, int np, double* F, cudaStream_t s, long long* nl) {
-  cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * (size_t)np * np, s);
+                           int n, int np, bool ief, double* S, cudaStream_t s, long long* nl) {
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * (size_t)np * np, s);
   if (e != cudaSuccess) return e;
   dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
-  k_build_F<<<grd, blk, 0, s>>>(pos, nrm, area, R, n, np, F);
+  k_build_F<<<grd, blk, 0, s>>>(pos, nrm, area, R, n, np, ief ? 1 : 0, S);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_G(const double* pos, const double* area, int n, int np, double* G,
+                           cudaStream_t s, long long* nl) {
+  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)np * np, s);
+  if (e != cudaSuccess) return e;
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  k_build_G<<<grd, blk, 0, s>>>(pos, area, n, np, G);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_absmax(const double* S, int np, double* M,
+                                    unsigned long long* absmax_bits, cudaStream_t s, long long* nl) {
+  if (np % 32) return cudaErrorInvalidValue;
+  k_transpose_absmax<<<dim3(np / 32, np / 32), 256, 0, s>>>(S, np, M, absmax_bits);
   ++*nl;
   return cudaGetLastError();
 }

@@ -79,6 +79,10 @@ struct px_handle {
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
   DevBuf b_rm2;    // matrix-free wFQFmu: R_mu^2 in FP32 and FP64
   DevBuf b_mesh;   // boundary elements: normals [N][3], areas [N]
+  // IEFPCM (Eq. 12): the operator S A^-1 of the second step and its planes, and the first
+  // step's solution y (the second step's right-hand side)
+  px::DevStructure ds_g;
+  DevBuf g_T64, g_T32, g_Thi, g_Tlo, g_Tffh, g_Tffl, b_yief;
   DevBuf b_M64;    // FP64 M = diag(Kbar, I) T while its split planes are built
   // solve buffers
   DevBuf b_pol, b_b, b_x, b_r, b_rnorm, b_bnorm, b_iters, b_act, b_zq, b_zmu;
@@ -124,7 +128,8 @@ void free_all(px_handle* h) {
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
                     &h->b_X32, &h->b_Y32, &h->b_X64, &h->b_Y64, &h->b_Xth, &h->b_Xtl, &h->b_dpart,
-                    &h->b_alpha, &h->b_q, &h->b_mu, &h->b_sk, &h->b_het, &h->b_hstruct};
+                    &h->b_alpha, &h->b_q, &h->b_mu, &h->b_sk, &h->b_het, &h->b_hstruct,
+                    &h->g_T64, &h->g_T32, &h->g_Thi, &h->g_Tlo, &h->g_Tffh, &h->g_Tffl, &h->b_yief};
   for (DevBuf* b : bufs) b->release();
 }
 
@@ -390,7 +395,16 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.rm2f = nullptr;
   d.rm2d = nullptr;
   if (d.matfree) {
-    if (split) throw PxError{PX_ENOTIMPL, "matrix-free mode runs PX_FP32 or PX_FP64 matvecs"};
+    // split precisions run the tensor-core pair kernel (wFQ): T scaled by 2^e before the
+    // fp16 split, 2^e max|T| <= 2^14 with max|T| = sqrt(2/pi) / min R_q (the diagonal)
+    if (split && model != PX_WFQ)
+      throw PxError{PX_ENOTIMPL, "matrix-free wFQFmu runs PX_FP32 or PX_FP64 matvecs"};
+    if (split) {
+      double rq_min = types[0].Rq_bohr;
+      for (int t = 1; t < ntypes; ++t) rq_min = std::min(rq_min, types[t].Rq_bohr);
+      const double tmax = 0.7978845608028654 / rq_min;
+      d.op_scale_exp = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / tmax))));
+    }
     CU(h->b_pos4f.ensure(sizeof(float4) * N));
     CU(h->b_pos4d.ensure(sizeof(double) * 4 * N));
     d.pos4f = h->b_pos4f.as<float4>();
@@ -462,13 +476,65 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
 
 
 // ------------------------------------------------------------------ boundary elements
-// A meshed surface (Sec. 2.3): tesserae with barycentres, outward normals and areas; the
-// dense DPCM operator Ft (Eq. 11, normal-field form) takes the place of Kbar T, so both
-// solvers apply unchanged with the column shift Lambda(w) = 2 pi (e2 + e1)/(e2 - e1).
+// The precision planes of a dense boundary-element operator whose FP64 form d.T64 holds it
+// transposed (S = Op^T, see launch_build_F): FP32 and double-FP32 copies of S (the block
+// matvecs and the shifted matvec read S as the transposed operator), and for the
+// tensor-core modes hi/lo planes of Op itself (row-major, as that GEMM reads them).
+void bem_planes(px_handle* h, px::DevStructure& d, DevBuf& bT32, DevBuf& bThi, DevBuf& bTlo,
+                DevBuf& bTffh, DevBuf& bTffl, cudaStream_t s) {
+  const int prec = h->opt.precision;
+  const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
+  const size_t np2 = (size_t)d.np * d.np;
+  d.op_has_kbar = split;
+  d.op_scale_exp = 12;
+  d.t_f16 = prec == PX_FP16SPLIT;
+  if (prec == PX_FP32) {
+    CU(bT32.ensure(np2 * sizeof(float)));
+    d.T32 = bT32.as<float>();
+    CU(px::launch_convert_T(d, s, &h->nl));
+  }
+  if (split) {
+    CU(bThi.ensure(np2 * sizeof(uint16_t)));
+    CU(bTlo.ensure(np2 * sizeof(uint16_t)));
+    d.Thi = bThi.as<uint16_t>();
+    d.Tlo = bTlo.as<uint16_t>();
+    CU(h->b_M64.ensure(np2 * sizeof(double) + 256));
+    double* M64 = h->b_M64.as<double>();
+    unsigned long long* d_amax = reinterpret_cast<unsigned long long*>(M64 + np2);
+    CU(cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s));
+    CU(px::launch_transpose_absmax(d.T64, d.np, M64, d_amax, s, &h->nl));
+    unsigned long long amax_bits = 0;
+    CU(cudaMemcpyAsync(&amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double amax = 0.0;
+    std::memcpy(&amax, &amax_bits, sizeof(amax));
+    if (!std::isfinite(amax)) throw PxError{PX_EINVAL, "non-finite operator entries"};
+    int e = 12;
+    if (amax > 0.0) e = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / amax))));
+    d.op_scale_exp = e;
+    CU(px::launch_split_op(M64, np2, d.Thi, d.Tlo, d.t_f16, e, s, &h->nl));
+    CU(cudaStreamSynchronize(s));
+    h->b_M64.release();
+  }
+  if (prec != PX_FP64 || h->opt.solver == PX_SOLVER_SHIFTED) {
+    CU(bTffh.ensure(np2 * sizeof(float)));
+    CU(bTffl.ensure(np2 * sizeof(float)));
+    d.Tffh = bTffh.as<float>();
+    d.Tffl = bTffl.as<float>();
+    CU(px::launch_split_ff(d.T64, np2, d.Tffh, d.Tffl, s, &h->nl));
+  }
+}
+
+// A meshed surface (Sec. 2.3): tesserae with barycentres, outward normals and areas.  DPCM
+// (Eq. 11, normal-field form): one dense operator Ft in place of Kbar T, every frequency a
+// column shift Lambda(w).  IEFPCM (Eq. 12): the operator F of the first step (column shift
+// -Lambda(w)) and the Coulomb matrix S A^-1 of the second.
 void set_mesh(px_handle* h, int n, const double* pos_ang, const double* nrm,
-              const double* area_ang2, double radius_ang) {
+              const double* area_ang2, double radius_ang, int formulation) {
   if (!pos_ang || !nrm || !area_ang2) throw PxError{PX_EINVAL, "NULL input"};
   if (n < 1) throw PxError{PX_EINVAL, "n_tess must be >= 1"};
+  if (formulation != PX_BEM_DPCM && formulation != PX_BEM_IEFPCM)
+    throw PxError{PX_EINVAL, "formulation must be PX_BEM_DPCM or PX_BEM_IEFPCM"};
   if (!std::isfinite(radius_ang) || !(radius_ang > 0.0)) throw PxError{PX_EINVAL, "radius must be finite and > 0"};
   std::vector<double> pos(3 * (size_t)n), area(n);
   for (int i = 0; i < n; ++i) {
@@ -483,15 +549,16 @@ void set_mesh(px_handle* h, int n, const double* pos_ang, const double* nrm,
     if (!std::isfinite(area_ang2[i]) || !(area_ang2[i] > 0.0)) throw PxError{PX_EINVAL, "areas must be > 0"};
     area[i] = area_ang2[i] / (kBohrAng * kBohrAng);
   }
-  const int prec = h->opt.precision;
-  const bool split = prec == PX_BF16SPLIT || prec == PX_FP16SPLIT;
   if (h->opt.mode == PX_MODE_MATFREE) throw PxError{PX_ENOTIMPL, "meshes need the materialised operator"};
+  const bool ief = formulation == PX_BEM_IEFPCM;
   cudaStream_t s = h->own_stream;
   px::DevStructure& d = h->ds;
   h->have_structure = false;
   d = px::DevStructure{};
+  h->ds_g = px::DevStructure{};
   d.model = PX_WFQ;   // one unknown per element, one scalar shift per column
   d.bem = true;
+  d.bem_stage = ief ? 1 : 0;
   d.N = n;
   d.nu = n;
   d.np = (int)round_up(n, px::kTile);
@@ -517,46 +584,22 @@ void set_mesh(px_handle* h, int n, const double* pos_ang, const double* nrm,
   const size_t np2 = (size_t)d.np * d.np;
   CU(h->b_T64.ensure(np2 * sizeof(double)));
   d.T64 = h->b_T64.as<double>();
-  CU(px::launch_build_F(d.pos64, d.nrm, d.tarea, radius_ang / kBohrAng, n, d.np, d.T64, s, &h->nl));
-  if (prec == PX_FP32) {
-    CU(h->b_T32.ensure(np2 * sizeof(float)));
-    d.T32 = h->b_T32.as<float>();
-    CU(px::launch_convert_T(d, s, &h->nl));
-  }
-  d.t_f16 = prec == PX_FP16SPLIT;
-  if (split) {
-    CU(h->b_Thi.ensure(np2 * sizeof(uint16_t)));
-    CU(h->b_Tlo.ensure(np2 * sizeof(uint16_t)));
-    d.Thi = h->b_Thi.as<uint16_t>();
-    d.Tlo = h->b_Tlo.as<uint16_t>();
-    // the planes hold the whole operator; max |Ft| from the row-copy pass (no charge rows)
-    CU(h->b_M64.ensure(np2 * sizeof(double) + 256));
-    double* M64 = h->b_M64.as<double>();
-    unsigned long long* d_amax = reinterpret_cast<unsigned long long*>(M64 + np2);
-    CU(cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s));
-    px::DevStructure dcopy = d;
-    dcopy.N = 0;
-    CU(px::launch_build_M64(dcopy, M64, d_amax, s, &h->nl));
-    unsigned long long amax_bits = 0;
-    CU(cudaMemcpyAsync(&amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    double amax = 0.0;
-    std::memcpy(&amax, &amax_bits, sizeof(amax));
-    if (!std::isfinite(amax)) throw PxError{PX_EINVAL, "non-finite operator entries"};
-    int e = 12;
-    if (amax > 0.0) e = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / amax))));
-    d.op_scale_exp = e;
-    d.op_has_kbar = true;
-    CU(px::launch_split_op(M64, np2, d.Thi, d.Tlo, d.t_f16, e, s, &h->nl));
-    CU(cudaStreamSynchronize(s));
-    h->b_M64.release();
-  }
-  if (prec != PX_FP64 || h->opt.solver == PX_SOLVER_SHIFTED) {
-    CU(h->b_Tffh.ensure(np2 * sizeof(float)));
-    CU(h->b_Tffl.ensure(np2 * sizeof(float)));
-    d.Tffh = h->b_Tffh.as<float>();
-    d.Tffl = h->b_Tffl.as<float>();
-    CU(px::launch_split_ff(d.T64, np2, d.Tffh, d.Tffl, s, &h->nl));
+  CU(px::launch_build_F(d.pos64, d.nrm, d.tarea, radius_ang / kBohrAng, n, d.np, ief, d.T64, s, &h->nl));
+  bem_planes(h, d, h->b_T32, h->b_Thi, h->b_Tlo, h->b_Tffh, h->b_Tffl, s);
+  if (ief) {
+    // second step: (S A^-1) q = y, a symmetric operator with charges as unknowns (no
+    // area weight in the observables)
+    px::DevStructure& g = h->ds_g;
+    g = d;
+    g.bem_stage = 2;
+    g.tarea = nullptr;
+    g.T32 = nullptr;
+    g.Thi = g.Tlo = nullptr;
+    g.Tffh = g.Tffl = nullptr;
+    CU(h->g_T64.ensure(np2 * sizeof(double)));
+    g.T64 = h->g_T64.as<double>();
+    CU(px::launch_build_G(d.pos64, d.tarea, n, d.np, g.T64, s, &h->nl));
+    bem_planes(h, g, h->g_T32, h->g_Thi, h->g_Tlo, h->g_Tffh, h->g_Tffl, s);
   }
   CU(cudaEventRecord(h->ev_b, s));
   wait_event(h, h->ev_b);
@@ -593,7 +636,7 @@ T* grow(DevBuf& b, size_t n) {
 
 px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha_ib, int P,
                 const double* pol, double e0, SolveOut* so, cudaStream_t s,
-                const double* eps = nullptr) {
+                const double* eps = nullptr, const double2* rhs_c = nullptr) {
   if (!h->have_structure) throw PxError{PX_EINVAL, "no structure loaded"};
   if (F < 1 || P < 1 || !omega_ev || !pol)
     throw PxError{PX_EINVAL, "need n_freq >= 1, n_pol >= 1, omega_ev and pol_dir"};
@@ -646,7 +689,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const bool lowp = o.precision != PX_FP64;
   const bool tc = o.precision == PX_BF16SPLIT || o.precision == PX_FP16SPLIT;
   const bool tc_f16 = o.precision == PX_FP16SPLIT;
-  if (tc && d.Thi == nullptr) throw PxError{PX_EINVAL, "precision changed since px_set_structure"};
+  if (tc && d.Thi == nullptr && !d.matfree)
+    throw PxError{PX_EINVAL, "precision changed since px_set_structure"};
   const size_t colpad = px::kTile;   // operand column padding of every matvec kernel
   // stopping targets of the inner (low-precision) iteration:
   //   max(inner_tol * ||r_outer||, tol_frac * tol * ||b||)
@@ -669,7 +713,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   st.graph_launches = 0;
   st.graphs_built = 0;
   // the shifted solver applies to Eq. 1 (one scalar shift); wFQFmu solves stay batched
-  const bool shifted = o.solver == PX_SOLVER_SHIFTED && model == PX_WFQ;
+  const bool shifted = o.solver == PX_SOLVER_SHIFTED && model == PX_WFQ && !rhs_c;
   st.solver_used = shifted ? PX_SOLVER_SHIFTED : PX_SOLVER_BATCHED;
   st.shift_steps = st.shift_matvec_launches = 0;
   st.shift_matvec_ms = st.shift_matvec_bytes = st.shift_ms = 0.0;
@@ -732,9 +776,18 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
                              d_pol, e0, bc, bn, s, &nl));
     CU(px::launch_init_residual_c(bc, nu, B, bn, inner_tol, tol_abs_frac, r, rnorm, beta, target_all,
                                   s, &nl));
+  } else if (rhs_c) {
+    // second IEFPCM step (Eq. 12): (S A^-1) q = y, one complex right-hand side per column
+    CU(px::launch_bem_setup(F, P, nu, np, d.bem_stage, d_eps, d.nrm, d.T64, d.pos64, d_pol, e0,
+                            zq_all, b, s, &nl));
+    bc = const_cast<double2*>(rhs_c);
+    CU(px::launch_col_norms_c(bc, nu, B, bn, s, &nl));
+    CU(px::launch_init_residual_c(bc, nu, B, bn, inner_tol, tol_abs_frac, r, rnorm, beta, target_all,
+                                  s, &nl));
   } else {
-    if (d.bem)   // Eq. 11: Lambda(w) per column (overwrites z_q) and b = -E0 e . n
-      CU(px::launch_bem_setup(F, P, nu, d_eps, d.nrm, d_pol, e0, zq_all, b, s, &nl));
+    if (d.bem)   // Eqs. 11, 12: the shift of every column (overwrites z_q) and b
+      CU(px::launch_bem_setup(F, P, nu, np, d.bem_stage, d_eps, d.nrm, d.T64, d.pos64, d_pol, e0,
+                              zq_all, b, s, &nl));
     else
       CU(px::launch_rhs(nu, N, model, d.rowptr, d.col, d.val64, d.pos64, d_pol, P, e0, b, s, &nl));
     CU(px::launch_col_norms(b, nu, P, bnorm, s, &nl));
@@ -847,7 +900,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           8 * (m + 1) * nu * NPmax,                          // V
           8 * m * nu * NPmax,                                // U = T V
           8 * (size_t)nu * NPmax,                            // W
-          8 * (size_t)plan.S * np * NPmax,                   // matvec partials
+          8 * (size_t)plan.parts() * np * NPmax,             // matvec partials
           8 * (size_t)nrb * (m + 1) * NPmax,                 // projection partials
           8 * 2 * (m + 1) * NPmax,                           // projections
           8 * (size_t)px::sk_update_chunks((int)m) * nu * NPmax,  // update partials
@@ -931,7 +984,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           e1v = pool_event(h, prof_k++);
           CU(cudaEventRecord(e0v, s));
         }
-        CU(px::launch_sk_matvec(d.Tffh, d.Tffl, nu, np, NP, plan, G.vp, skPart, Uj, s, &nl));
+        // boundary-element operators are stored transposed
+        CU(px::launch_sk_matvec(d.Tffh, d.Tffl, nu, np, NP, plan, d.bem, G.vp, skPart, Uj, s, &nl));
         if (o.profile) {
           CU(cudaEventRecord(e1v, s));
           sk_events.push_back({e0v, e1v});
@@ -1058,6 +1112,11 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
         if (d.matfree && model == PX_WFQFMU) {
           if (lowp) CU(px::launch_sgemm_mf4(d.pos4f, d.rm2f, N, d.mu_self, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
+        } else if (d.matfree && tc) {
+          // tensor-core pair kernel: T tiles generated in shared memory as split planes
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt));
+          CU(px::launch_tc_mf(d.pos4f, N, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, d.op_scale_exp,
+                              h->d_err, q, cnt));
         } else if (d.matfree) {
           if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
@@ -1069,7 +1128,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           if (st.gemm_tiles_used == 0) st.gemm_tiles_used = used + 1;
         } else if (lowp) {
           CU(px::launch_sgemm(d.T32, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
-        } else if (2 * Bact <= 8) {
+        } else if (2 * Bact <= 8 && !d.bem) {   // the GEMV reads rows: symmetric T only
           CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, q, cnt));
         } else {
           CU(px::launch_dgemm_splitk(d.T64, np, X64, ldxa, Y64, ldxa, ldxa, dpart, dpart_elems, q,
@@ -1098,7 +1157,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       if (use_graphs) {
         // the whole restart cycle is one graph launch: a device-side while loop runs
         // Krylov steps until every column stopped or the basis is full
-        if (tc && o.gemm_tiles == 0 && px::tc_tuned_variant(np, ldxa, tc_f16) < 0) {
+        if (tc && !d.matfree && o.gemm_tiles == 0 && px::tc_tuned_variant(np, ldxa, tc_f16) < 0) {
           // tune the tensor-core tile shape on this cycle's operands before capture
           CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
@@ -1122,7 +1181,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
             (uint64_t)(uintptr_t)d.Tlo, (uint64_t)(uintptr_t)d.rowptr, (uint64_t)(uintptr_t)d.col,
             (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
             (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d,
-            (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp,
+            (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp, (uint64_t)d.bem,
             (uint64_t)(uintptr_t)dpart, (uint64_t)dpart_elems};
         CycleGraph* cg = nullptr;
         for (size_t k = 0; k < h->graphs.size(); ++k) {
@@ -1226,7 +1285,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
     } else if (d.matfree) {
       CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
-    } else if (2 * Bact <= 8) {
+    } else if (2 * Bact <= 8 && !d.bem) {   // the GEMV reads rows: symmetric T only
       CU(px::launch_dgemv(d.T64, np, X64, ldxa, Y64, ldxa, 2 * Bact, s, &nl));
     } else if (d.Tffh) {
       // double-FP32 residual matvec; X32 / Y32 are free between cycles
@@ -1437,10 +1496,10 @@ px_status px_solve(px_handle* h, int n_freq, const double* omega_ev, const doubl
 }
 
 px_status px_set_mesh(px_handle* h, int n_tess, const double* pos_ang, const double* normals,
-                      const double* area_ang2, double radius_ang) {
+                      const double* area_ang2, double radius_ang, int formulation) {
   if (!h) return fail(nullptr, PX_EINVAL, "NULL handle");
   try {
-    set_mesh(h, n_tess, pos_ang, normals, area_ang2, radius_ang);
+    set_mesh(h, n_tess, pos_ang, normals, area_ang2, radius_ang, formulation);
   } catch (const PxError& e) {
     h->have_structure = false;
     return fail(h, e.st, e.msg);
@@ -1474,17 +1533,69 @@ px_status solve_host(px_handle* h, int n_freq, const double* omega_ev, const dou
     if (out->q) so.d_q = grow<double2>(h->b_q, B * N);
     if (out->mu && h->ds.model == PX_WFQFMU) so.d_mu = grow<double2>(h->b_mu, B * N * 3);
     so.sigma_required = out->sigma_abs != nullptr;
-    px_status r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s, eps);
+    px_status r = PX_OK;
+    SolveOut so1;
+    const bool ief = h->ds.bem && h->ds.bem_stage == 1;
+    if (ief) {
+      // IEFPCM (Eq. 12): y from the shifted system of F, then q from (S A^-1) q = y
+      so1 = so;
+      so1.d_q = nullptr;
+      so1.sigma_required = false;
+      const px_status r1 = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so1, s, eps);
+      const px_stats st1 = h->stats;
+      double2* y = grow<double2>(h->b_yief, (size_t)N * B);
+      CU(cudaMemcpyAsync(y, h->b_x.as<double2>(), sizeof(double2) * N * B, cudaMemcpyDeviceToDevice, s));
+      std::swap(h->ds, h->ds_g);
+      try {
+        r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s, eps, y);
+      } catch (...) {
+        std::swap(h->ds, h->ds_g);
+        throw;
+      }
+      std::swap(h->ds, h->ds_g);
+      px_stats& st = h->stats;
+      st.solve_ms += st1.solve_ms;
+      st.matvec_ms += st1.matvec_ms;
+      st.matvec_launches += st1.matvec_launches;
+      st.matvec_flops += st1.matvec_flops;
+      st.matvec_bytes += st1.matvec_bytes;
+      st.resid_ms += st1.resid_ms;
+      st.resid_launches += st1.resid_launches;
+      st.resid_flops += st1.resid_flops;
+      st.kernel_launches += st1.kernel_launches;
+      st.cycles += st1.cycles;
+      st.total_iters += st1.total_iters;
+      st.graph_launches += st1.graph_launches;
+      st.graphs_built += st1.graphs_built;
+      st.solver_used = st1.solver_used;
+      st.shift_steps = st1.shift_steps;
+      st.shift_matvec_launches = st1.shift_matvec_launches;
+      st.shift_matvec_ms = st1.shift_matvec_ms;
+      st.shift_matvec_bytes = st1.shift_matvec_bytes;
+      st.shift_ms = st1.shift_ms;
+      for (size_t c = 0; c < B; ++c) {
+        so.relres[c] = std::max(so.relres[c], so1.relres[c]);
+        so.iters[c] += so1.iters[c];
+        if (so1.status[c] != PX_OK) so.status[c] = so1.status[c];
+      }
+      if (r1 != PX_OK && r == PX_OK) {
+        r = r1;
+        h->err = "some columns did not reach tol_rel; see status[]";
+      }
+    } else {
+      r = solve(h, n_freq, omega_ev, alpha_ib, n_pol, pol_dir, e0, &so, s, eps);
+    }
     if (out->alpha) CU(cudaMemcpyAsync(out->alpha, so.d_alpha, sizeof(double2) * F * 3 * P, cudaMemcpyDeviceToHost, s));
     if (out->sigma_abs_pol) CU(cudaMemcpyAsync(out->sigma_abs_pol, so.d_sigma_pol, sizeof(double) * F * P, cudaMemcpyDeviceToHost, s));
     if (out->sigma_abs && P == 3) CU(cudaMemcpyAsync(out->sigma_abs, so.d_sigma, sizeof(double) * F, cudaMemcpyDeviceToHost, s));
-    if (out->rel_residual) CU(cudaMemcpyAsync(out->rel_residual, so.d_relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    if (out->rel_residual && !ief) CU(cudaMemcpyAsync(out->rel_residual, so.d_relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     if (so.d_q) CU(cudaMemcpyAsync(out->q, so.d_q, sizeof(double2) * B * N, cudaMemcpyDeviceToHost, s));
     if (so.d_mu) CU(cudaMemcpyAsync(out->mu, so.d_mu, sizeof(double2) * B * N * 3, cudaMemcpyDeviceToHost, s));
     sync_stream(h, s);
     for (size_t c = 0; c < B; ++c) {
       if (out->iters) out->iters[c] = so.iters[c];
       if (out->status) out->status[c] = so.status[c];
+      if (out->rel_residual && ief) out->rel_residual[c] = so.relres[c];
     }
     return r == PX_OK ? PX_OK : fail(h, r, h->err);
   } catch (const PxError& e) {

@@ -72,6 +72,7 @@ struct DevStructure {
   int* ident = nullptr;        // [N] 0..N-1: per-atom indexing of the dipole shifts
   // boundary elements (Sec. 2.3): the "atoms" are tesserae; T holds the DPCM operator Ft
   bool bem = false;
+  int bem_stage = 0;           // 0 DPCM; 1, 2 the two steps of IEFPCM (Eq. 12)
   double* nrm = nullptr;       // [N][3] outward normals
   double* tarea = nullptr;     // [N] tessera areas (bohr^2)
 };
@@ -171,6 +172,14 @@ cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const
                            cudaStream_t s, long long* nl, int variant, int* used);
 // The autotuner's cached variant for a shape on the current device, or -1.
 int tc_tuned_variant(int np, int ncols, bool f16);
+// Matrix-free wFQ block matvec Y = T X on the tensor cores: T^qq tiles generated from pos
+// [n] (x, y, z, R_q^2 in FP32, bohr) into shared memory as split planes and contracted with
+// the split operand (Xh / Xl as for launch_tc_gemm).  f16: T scaled by 2^scale_exp before the
+// split (2^scale_exp max|T| <= 2^14); Y is returned unscaled.  128 x 256 tiles when
+// ncols % 256 == 0, else 128 x 128.  *err as for launch_tc_gemm.
+cudaError_t launch_tc_mf(const float4* pos, int n, int np, const uint16_t* Xh, const uint16_t* Xl,
+                         int ncols, float* Y, int ldy, bool f16, int scale_exp, int* err,
+                         cudaStream_t s, long long* nl);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
 cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
                             uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);
@@ -266,14 +275,24 @@ struct ResidArgs {
 };
 cudaError_t launch_resid(const ResidArgs& a, cudaStream_t s, long long* nl);
 
-// ---- boundary elements (Sec. 2.3, Eq. 11 in the normal-field DPCM form)
-// Ft [np][np] (zero padded) of a mesh: pos, nrm [n][3] (bohr, unit), area [n] (bohr^2),
-// R the radius of the enclosing sphere.
+// ---- boundary elements (Sec. 2.3; Eq. 11 in the normal-field DPCM form, Eq. 12)
+// Operators [np][np] (zero padded) of a mesh: pos, nrm [n][3] (bohr, unit), area [n]
+// (bohr^2), R the radius of the enclosing sphere.  Stored transposed (S[j][i] = Op[i][j]);
+// ief selects Eq. 12's F instead of Eq. 11's Ft.
 cudaError_t launch_build_F(const double* pos, const double* nrm, const double* area, double R,
-                           int n, int np, double* F, cudaStream_t s, long long* nl);
+                           int n, int np, bool ief, double* S, cudaStream_t s, long long* nl);
+// S A^-1 of Eq. 12 (symmetric)
+cudaError_t launch_build_G(const double* pos, const double* area, int n, int np, double* G,
+                           cudaStream_t s, long long* nl);
+// M = S^T and max |M| (bits of the double, atomicMax)
+cudaError_t launch_transpose_absmax(const double* S, int np, double* M,
+                                    unsigned long long* absmax_bits, cudaStream_t s, long long* nl);
 // zq[c] = Lambda(w_f) = 2 pi (e2 + e1)/(e2 - e1) from eps [F][4] = (Re e2, Im e2, Re e1, Im e1),
 // and b[i][p] = -e0 e_p . n_i: the system (Ft - Lambda I) sigma = -E . n.
-cudaError_t launch_bem_setup(int F, int P, int n, const double* eps, const double* nrm,
+// stage 0: DPCM (z = Lambda, b = -E0 e . n); 1: first IEFPCM step (z = -Lambda, b = c from
+// the transposed operator S); 2: second IEFPCM step (z = 0, b unused)
+cudaError_t launch_bem_setup(int F, int P, int n, int np, int stage, const double* eps,
+                             const double* nrm, const double* S, const double* pos,
                              const double* pol, double e0, double2* zq, double* b, cudaStream_t s,
                              long long* nl);
 
@@ -353,6 +372,9 @@ cudaError_t launch_gather_shifts(const double2* zq, const double2* zmu, int ntyp
                                  const int* act, int Bact, double2* zq_act, double2* zmu_act,
                                  double2* amu_act, cudaStream_t s, long long* nl);
 // bnorm[p] = ||b[., p]||_2
+// ||bc_c|| of complex right-hand sides bc [nu][B]
+cudaError_t launch_col_norms_c(const double2* bc, int nu, int B, double* bn, cudaStream_t s,
+                               long long* nl);
 cudaError_t launch_col_norms(const double* b, int nu, int P, double* bnorm, cudaStream_t s,
                              long long* nl);
 // x = 0: r[i][c] = b[i][c % P], rnorm[c] = beta[c] = bnorm[c % P],
@@ -397,6 +419,9 @@ struct SkMatvecPlan {
   int grid = 0;      // persistent blocks (2 per SM)
   int S = 1;         // column segments; partial products part [S][np][NP]
   int seg_cols = 128;
+  int St = 1;        // transposed operator: row segments, partials part [St][np][NP]
+  int seg_rows = 32;
+  int parts() const { return S > St ? S : St; }
 };
 SkMatvecPlan sk_matvec_plan(int np);
 struct SkGroup {
@@ -417,10 +442,11 @@ struct SkGroup {
 };
 // U = T v in double-FP32 (T = Th + Tl planes [np][np]; v as planar hi / lo rows vp [2 NP][np],
 // zero beyond n; U [n][NP] float2), via partial products over column segments
-// (part [S][np][NP]).
+// (part [S][np][NP]).  trans: the planes hold T transposed (U = planes^T v, partial products
+// over row segments, part [St][np][NP]).
 cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, int NP,
-                             const SkMatvecPlan& pl, const float* vp, float2* part, float2* U,
-                             cudaStream_t s, long long* nl);
+                             const SkMatvecPlan& pl, bool trans, const float* vp, float2* part,
+                             float2* U, cudaStream_t s, long long* nl);
 // W = Kbar U (Eq. 2), double-FP32 arithmetic (K = val64 split as val32 + remainder).
 cudaError_t launch_sk_kbar(int n, int NP, const int* rowptr, const int* col, const double* val,
                            const float* val32, const float2* U, float2* W, cudaStream_t s,

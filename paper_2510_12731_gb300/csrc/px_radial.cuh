@@ -39,5 +39,21 @@ __device__ __forceinline__ void eval_f(float r, float R, float& G, float& G1r, f
   }
 }
 
+// wFQ charge-charge kernel (Eq. 5) in FP32 from (x, y, z, R_q^2) of two atoms (bohr):
+// erf(r/R)/r with R^2 = R_q,a^2 + R_q,b^2, the r -> 0 limit sqrt(2/pi)/R_q on the diagonal;
+// erf(r/R) = 1 to FP32 precision beyond r/R = 4, where one reciprocal square root remains.
+constexpr float kSqrt2OverPiF = 0.79788456080286536f;
+__device__ __forceinline__ float tqq_f(float4 a, float4 b, bool same) {
+  if (same) return kSqrt2OverPiF * rsqrtf(a.w);
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float R2 = a.w + b.w;
+  if (r2 < 16.0f * R2) {
+    const float r = sqrtf(r2);
+    return erff(r * rsqrtf(R2)) / r;
+  }
+  return rsqrtf(r2);
+}
+
 }  // namespace radial
 }  // namespace px

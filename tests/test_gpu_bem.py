@@ -24,10 +24,10 @@ def _alpha_err(a, ref):
     return np.max(np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1))
 
 
-def _solve(w, **opts):
+def _solve(w, formulation="dpcm", **opts):
     from paper_2510_12731_gb300 import Solver
     with Solver(**opts) as s:
-        s.set_mesh(w.pos_ang, w.normals, w.area_ang2, w.radius_ang)
+        s.set_mesh(w.pos_ang, w.normals, w.area_ang2, w.radius_ang, formulation)
         out = s.solve_bem(w.omega_ev, w.eps2, w.eps1, w.pol_dirs)
         st = s.stats()
     return out, st
@@ -54,20 +54,49 @@ def test_bem_sphere_parity(precision, solver):
     assert np.allclose(out["sigma_abs"], sig, rtol=1e-6)
 
 
-@pytest.mark.parametrize("solver", ["batched", "shifted"])
-def test_bem_spheroid_in_a_medium_parity(solver):
-    """Prolate spheroid 8 x 8 x 16 A, 700 tesserae, eps1 = 1.77 (water), oblique fields."""
+def _spheroid():
     pos, nrm, area = S.spheroid_mesh(700, 8.0, 8.0, 16.0)
     wv = np.linspace(2.0, 4.0, 9)
     pols = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8], [0.0, 0.0, 1.0], [0.48, 0.6, 0.64]])
-    w = S.MeshWorkload("spheroid", pos, nrm, area, 16.0, wv, S.drude_eps(wv, 6.0, 0.15),
-                       np.full(wv.size, 1.77 + 0j), pols)
-    ref_a, ref_q, _ = BE.solve(pos, nrm, area, w.eps2, w.eps1, pols, radius_ang=16.0)
-    out, _ = _solve(w, precision="fp32", solver=solver, tol_rel=1e-10)
+    return S.MeshWorkload("spheroid", pos, nrm, area, 16.0, wv, S.drude_eps(wv, 6.0, 0.15),
+                          np.full(wv.size, 1.77 + 0j), pols)
+
+
+@pytest.mark.parametrize("precision,solver", CASES)
+def test_bem_spheroid_in_a_medium_parity(precision, solver):
+    """Prolate spheroid 8 x 8 x 16 A, 700 tesserae, eps1 = 1.77 (water), oblique fields.
+    Unlike the sphere's, the spheroid's operator is not symmetric: a matvec that applied
+    its transpose would converge to a wrong answer with a small residual."""
+    w = _spheroid()
+    ref_a, ref_q, _ = BE.solve(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1, w.pol_dirs,
+                               radius_ang=16.0)
+    out, _ = _solve(w, precision=precision, solver=solver, tol_rel=1e-10)
     assert out["ok"]
     assert _alpha_err(out["alpha"], ref_a) <= 1e-7
     assert np.abs(out["q"] - ref_q).max() <= 1e-6 * np.abs(ref_q).max()
     assert "sigma_abs" not in out   # P = 4: no trace from four directions
+
+
+@pytest.mark.parametrize("precision,solver", CASES)
+def test_iefpcm_parity(precision, solver):
+    """IEFPCM (Eq. 12) in two steps on the spheroid (4 oblique directions) and on the Drude
+    sphere (x, y, z, sigma_abs), against the oracle's two dense LUs."""
+    w = _spheroid()
+    ref_a, ref_q, _ = BE.solve_iefpcm(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1,
+                                      w.pol_dirs, radius_ang=16.0)
+    out, st = _solve(w, "iefpcm", precision=precision, solver=solver, tol_rel=1e-10)
+    assert out["ok"] and np.all(out["rel_residual"] <= 1e-10)
+    assert _alpha_err(out["alpha"], ref_a) <= 1e-7
+    assert np.abs(out["q"] - ref_q).max() <= 1e-6 * np.abs(ref_q).max()
+    assert st["solver_used"] == (1 if solver == "shifted" else 0)
+    w = S.drude_sphere_mesh(600, nfreq=8, wmin=2.5, wmax=4.5)
+    ref_a, ref_q, _ = BE.solve_iefpcm(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1,
+                                      w.pol_dirs, radius_ang=w.radius_ang)
+    out, _ = _solve(w, "iefpcm", precision=precision, solver=solver, tol_rel=1e-10)
+    assert out["ok"]
+    assert _alpha_err(out["alpha"], ref_a) <= 1e-7
+    sig = M.sigma_abs(w.omega_ev / M.HARTREE_EV, np.einsum("fkk->f", ref_a).imag)
+    assert np.allclose(out["sigma_abs"], sig, rtol=1e-6)
 
 
 def test_bem_sphere_closed_form():
@@ -97,6 +126,14 @@ def test_bem_degenerate_meshes(n):
         scale = np.abs(ref_q).max()
         assert np.abs(out["q"] - ref_q).max() <= 1e-8 * scale
         assert np.abs(out["alpha"] - ref_a).max() <= 1e-8 * np.abs(ref_a).max()
+    # FP64 with at most four real operand columns (the narrowest block matvec)
+    w1 = S.MeshWorkload("tiny", pos, nrm, area, 5.0, wv[:2], w.eps2[:2], w.eps1[:2], np.eye(3)[:1])
+    out, _ = _solve(w1, precision="fp64", tol_rel=1e-12)
+    assert np.abs(out["q"] - ref_q[:2, :1]).max() <= 1e-10 * np.abs(ref_q).max()
+    ref_a, ref_q, _ = BE.solve_iefpcm(pos, nrm, area, w.eps2, w.eps1, w.pol_dirs, radius_ang=5.0)
+    for solver in ("batched", "shifted"):
+        out, _ = _solve(w, "iefpcm", precision="fp32", solver=solver, tol_rel=1e-10)
+        assert np.abs(out["q"] - ref_q).max() <= 1e-8 * np.abs(ref_q).max()
 
 
 def test_bem_large_mesh_sampled_residuals():
@@ -120,6 +157,13 @@ def test_bem_large_mesh_sampled_residuals():
     # the row residuals are bounded by the global one times sqrt(n / rows) in the mean
     rel = np.linalg.norm(r, axis=2) / np.linalg.norm(b[rows], axis=0)[None]
     assert rel.max() <= 10 * tol
+    # IEFPCM on the same mesh: both solvers for the first step agree
+    i_s, st = _solve(w, "iefpcm", precision="fp32", solver="shifted", tol_rel=tol)
+    i_b, _ = _solve(w, "iefpcm", precision="bf16split", solver="batched", tol_rel=tol)
+    assert i_s["ok"] and i_b["ok"] and st["solver_used"] == 1
+    assert _alpha_err(i_s["alpha"], i_b["alpha"]) <= 1e-6
+    # DPCM and IEFPCM discretise the same continuum problem: close on a fine sphere
+    assert _alpha_err(i_s["alpha"], out_s["alpha"]) <= 5e-3
 
 
 def test_bem_error_paths():
@@ -138,6 +182,8 @@ def test_bem_error_paths():
             s.set_mesh(pos, nrm, -area, 10.0)
         with pytest.raises(PxError):
             s.set_mesh(pos, nrm, area, 0.0)
+        with pytest.raises(PxError):                       # unknown formulation
+            s.set_mesh(pos, nrm, area, 10.0, 7)
         s.set_mesh(pos, nrm, area, 10.0)
         with pytest.raises(PxError):                       # e2 == e1
             s.solve_bem(w, [1.0 + 0j], 1.0, np.eye(3))

@@ -57,6 +57,18 @@ def test_graphene_disk_20nm_all_300_columns():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16split"])
+def test_na_icosahedron_19931_matrix_free_all_600_columns(precision):
+    """Config 2 as specified: T never stored, the pair kernel generating it inside every
+    matvec (FP32 CUDA-core kernel, or the tensor-core kernel with FP16-split tiles), block
+    GMRES with FP64 refinement (FP64 on-the-fly residual)."""
+    w = S.na_icosahedron_19931()
+    w.precision = precision
+    w.mode = "matfree"
+    fidx, ref = _golden("na_icosahedron_19931", w.omega_ev.size, 3)
+    _check(_solve(w), fidx, ref, w.tol)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
 def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies(precision):
     """The rod as configured (FP32 matvec; all 150 frequencies x 3 directions solved),
     and with the tensor-core FP16-split matvec, against oracle LU at three frequencies."""

@@ -411,7 +411,9 @@ def test_fp32_basis_single_round_is_limited_by_fp32_not_by_the_matvec():
 
 # ------------------------------------------------------------------ matrix-free (on the fly)
 
-@pytest.mark.parametrize("precision,tol,alpha_tol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-7)])
+@pytest.mark.parametrize("precision,tol,alpha_tol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-7),
+                                                     ("fp16split", 1e-9, 1e-7),
+                                                     ("bf16split", 1e-9, 1e-7)])
 def test_matfree_parity_small(precision, tol, alpha_tol):
     w = S.small_cluster(element="Ag", radius=9.0, model="wfq", nfreq=9, wmin=2.0, wmax=5.5)
     ref, _ = _oracle(w)
@@ -430,7 +432,10 @@ def test_matfree_matches_materialised_on_multi_tile_sphere():
     a_ref = SP.alpha(st, SP.modes(st), w.omega_ev, w.pol_dirs)
     out_mf, _ = _run(w, precision="fp32", tol_rel=1e-8, mode="matfree")
     out_m, _ = _run(w, precision="fp32", tol_rel=1e-8, mode="materialised")
-    for out in (out_mf, out_m):
+    # the tensor-core pair kernel (T tiles generated in shared memory as fp16 / bf16 planes)
+    out_tc, _ = _run(w, precision="fp16split", tol_rel=1e-8, mode="matfree")
+    out_tb, _ = _run(w, precision="bf16split", tol_rel=1e-8, mode="matfree")
+    for out in (out_mf, out_m, out_tc, out_tb):
         assert out["ok"]
         num = np.linalg.norm(out["alpha"] - a_ref, axis=1)
         assert np.max(num / np.linalg.norm(a_ref, axis=1)) <= 1e-5
@@ -533,3 +538,28 @@ def test_system_export_matches_the_oracle_and_solves(model):
         mu = x[N:].reshape(N, 3, 3) if model == "wfqfmu" else None
         alpha = M.dipole(st, q, mu)
         assert np.abs(alpha - ref.alpha[f]).max() <= 1e-9 * np.abs(ref.alpha[f]).max()
+
+
+def test_matfree_tensor_core_matvec_against_the_oracle_operator():
+    """One tensor-core pair-kernel step before refinement: with max_refine = 0 and a
+    tight inner tolerance, the FP16-split on-the-fly solve reaches the oracle to about the
+    split's ~22 bits times the condition number (1e-4), and the BF16 split (~16 bits) to
+    1e-2; a wrong swizzle, scale or transposition of the generated tile fails both."""
+    w = S.small_cluster(element="Na", radius=17.0, model="wfq", nfreq=6, wmin=2.0, wmax=4.5)
+    ref, _ = _oracle(w)
+    out16, _ = _run(w, precision="fp16split", tol_rel=1e-9, inner_tol=1e-9, max_refine=0,
+                    mode="matfree", restart_m=300)
+    assert _alpha_err(out16, ref) <= 1e-4
+    outb, _ = _run(w, precision="bf16split", tol_rel=1e-9, inner_tol=1e-9, max_refine=0,
+                   mode="matfree", restart_m=300)
+    assert _alpha_err(outb, ref) <= 1e-2
+
+
+def test_matfree_tensor_core_wfqfmu_not_implemented():
+    from paper_2510_12731_gb300 import PxError, Solver
+    from paper_2510_12731_gb300 import _lib as L
+    w = S.small_cluster(element="Ag", radius=6.0, model="wfqfmu", nfreq=2)
+    with Solver(precision="fp16split", mode="matfree") as s:
+        with pytest.raises(PxError) as e:
+            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
+        assert e.value.status == L.PX_ENOTIMPL
