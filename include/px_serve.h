@@ -51,6 +51,8 @@ typedef struct {
   double wall_s;              /* server lifetime so far */
   long long structure_reuses; /* admissions that kept a slot's resident operators */
   size_t peak_reserved_bytes; /* largest sum of admitted footprint estimates */
+  long long merged_requests;  /* requests solved as extra columns of another request's
+                                 block (same structure, model, field directions, E0) */
 } px_server_stats;
 
 /* Create a server.  opt: solver options for every request (NULL = defaults); with

@@ -90,7 +90,7 @@ class ServerStats(C.Structure):
                 ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double),
                 ("max_latency_ms", C.c_double), ("busy_points", C.c_double),
                 ("wall_s", C.c_double), ("structure_reuses", C.c_longlong),
-                ("peak_reserved_bytes", C.c_size_t)]
+                ("peak_reserved_bytes", C.c_size_t), ("merged_requests", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

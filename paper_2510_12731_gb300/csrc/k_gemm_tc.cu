@@ -498,38 +498,49 @@ namespace px {
 
 // ---------------------------------------------------------------- on-the-fly pair kernel
 // Matrix-free wFQ block matvec Y = T X on the tensor cores: the T tile of every 64-atom K
-// step is generated from the atom positions (Eq. 5, radial::tqq_f in FP32) by eight
-// generator warps straight into shared memory, as the hi / lo planes of the split (the
-// layout a 128-byte-swizzled TMA load would produce), and contracted with the X tiles
-// (TMA) by tcgen05.mma exactly as in k_tc_gemm; nothing of T is stored.
+// step is generated from the atom positions (Eq. 5 in FP32) by sixteen generator warps
+// straight into shared memory, as the hi / lo planes of the split (the layout a
+// 128-byte-swizzled TMA load would produce), and contracted with the X tiles (TMA) by
+// tcgen05.mma exactly as in k_tc_gemm; nothing of T is stored.
 //   warp 0        TMA producer of the X hi / lo tiles (BN x 64 per K step)
 //   warp 1        MMA issuer (one elected thread, 4 x 3 MMAs per K step)
 //   warp 2        TMEM allocation
-//   warps 4-11    generators: 128 rows x 64 atoms per K step, 8 consecutive atoms (one
-//                 16-byte chunk of each plane) per thread and row, 4 rows per thread;
-//                 then warps 4-7 run the epilogue
-// A stage is full when the TMA bytes landed and all eight generator warps arrived (each
-// after a proxy fence, so the tensor core sees the generic-proxy stores).
+//   warps 4-19    generators: 128 rows x 64 atoms per K step; a thread owns one 16-byte
+//                 chunk (8 consecutive atoms) of two rows; then warps 4-7 run the epilogue
+// A pair costs one reciprocal square root while r >= 4 R (erf(r/R) = 1 in FP32, so
+// T = 1/r); pairs closer than that take erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in
+// a branch the warp enters only when one of its lanes has such a pair (atoms are in
+// Morton order, so most tiles have none).  A stage is full when the TMA bytes landed and
+// all sixteen generator warps arrived (each after a proxy fence, so that the tensor core
+// sees the generic-proxy stores).
 // FP16 split: T' = 2^e T (2^e max|T| <= 2^14, max|T| = sqrt(2/pi)/min R_q), hi = RN(T'),
 // lo = RN((T' - hi) 2^11); the epilogue returns Y = D1 2^-(e+8) + D2 2^-(e+19) (X' = 2^8 X).
 // BF16 split: hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
 // Atoms beyond n generate 0.
 namespace {
 
+constexpr int kMfGenWarps = 16;
+constexpr int kMfThreads = 128 + 32 * kMfGenWarps;
+
+// positions of atoms beyond n: far from every atom and from each other, so that no
+// padded pair reaches the close-pair branch except its own diagonal
+__device__ __forceinline__ float4 mf_pos(const float4* __restrict__ pos, int i, int n) {
+  return i < n ? __ldg(pos + i) : make_float4(3.0e4f + 64.0f * (float)(i - n), 0.f, 0.f, 1.f);
+}
+
 template <int F16, int TC_BN, int TC_STAGES>
-__global__ void __launch_bounds__(384, 1)
+__global__ void __launch_bounds__(kMfThreads, 1)
 k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
         float* __restrict__ Y, int ldy, int K, float s1, float s2, int* err) {
   using Cfg = TcCfg<TC_BN, TC_STAGES>;
   constexpr int B_TILE = Cfg::B_TILE, STAGE = Cfg::STAGE, TC_TMEM_COLS = Cfg::TMEM_COLS;
   constexpr uint32_t kIdescF16 = idesc<TC_BN>(true), kIdescBF16 = idesc<TC_BN>(false);
-  constexpr int kGenWarps = 8;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE);
-  uint64_t* full = bars;                    // [TC_STAGES]: TMA + 8 generator warps
+  uint64_t* full = bars;                    // [TC_STAGES]: TMA + generator warps
   uint64_t* empty = bars + TC_STAGES;       // [TC_STAGES]: MMA commit
   uint64_t* accum = bars + 2 * TC_STAGES;   // [1]
   __shared__ uint32_t tmem_slot;
@@ -542,7 +553,7 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(&full[s], 1 + kGenWarps);
+      mbar_init(&full[s], 1 + kMfGenWarps);
       mbar_init(&empty[s], 1);
     }
     mbar_init(accum, 1);
@@ -606,16 +617,18 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
     mma_commit(accum);
   } else if (warp >= 4) {
     // ---------------- generators: T tiles in the swizzled K-major layout
-    const int gt = threadIdx.x - 128;            // 0 .. 255
+    const int gt = threadIdx.x - 128;            // 0 .. 511
     const int c = gt & 7;                        // 16-byte chunk (8 atoms) of the 64-atom step
-    const int rb = gt >> 3;                      // rows rb, rb + 32, rb + 64, rb + 96
-    float4 pi[4];
+    const int rb = gt >> 3;                      // rows rb and rb + 64
+    float4 pi[2];
+    bool rv[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + rb + 32 * u;
-      pi[u] = i < n ? pos[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    for (int u = 0; u < 2; ++u) {
+      const int i = i0 + rb + 64 * u;
+      pi[u] = mf_pos(pos, i, n);
+      rv[u] = i < n;
     }
-    const uint32_t sw = (uint32_t)((c ^ (rb & 7)) << 4);   // (row & 7) == (rb & 7) for all 4 rows
+    const uint32_t sw = (uint32_t)((c ^ (rb & 7)) << 4);   // (row & 7) == (rb & 7) for both rows
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
@@ -625,37 +638,49 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
       const int kb = kt * TC_BK + c * 8;
       float4 pk[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        pk[e] = kb + e < n ? __ldg(pos + kb + e) : make_float4(0.f, 0.f, 0.f, 1.f);
+      for (int e = 0; e < 8; ++e) pk[e] = mf_pos(pos, kb + e, n);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = rb + 32 * u;
+      for (int u = 0; u < 2; ++u) {
+        const int r = rb + 64 * u;
         const int i = i0 + r;
+        float t[8];
+        bool near_any = false;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          t[e] = rsqrtf(r2);
+          near_any |= r2 < 16.0f * (pi[u].w + pk[e].w);
+        }
+        if (__any_sync(0xffffffffu, near_any)) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float R2 = pi[u].w + pk[e].w;
+            if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pi[u].w);
+            else if (r2 < 16.0f * R2) t[e] = erff(r2 * t[e] * rsqrtf(R2)) * t[e];
+          }
+        }
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          float t[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int k = kb + e + q;
-            t[q] = (i < n && k < n) ? radial::tqq_f(pi[u], pk[e + q], i == k) : 0.f;
+          const float t0 = (rv[u] && kb + e < n) ? t[e] : 0.f;
+          const float t1 = (rv[u] && kb + e + 1 < n) ? t[e + 1] : 0.f;
+          if (F16) {
+            const float v0 = t0 * tscale, v1 = t1 * tscale;
+            const __half2 h = __floats2half2_rn(v0, v1);
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn((v0 - hf.x) * 2048.0f, (v1 - hf.y) * 2048.0f);
+            hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
+          } else {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(t0, t1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(t0 - hf.x, t1 - hf.y);
+            hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
           }
-          uint16_t h[2], l[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            if (F16) {
-              const float v = t[q] * tscale;
-              const __half hh = __float2half_rn(v);
-              h[q] = __half_as_ushort(hh);
-              l[q] = __half_as_ushort(__float2half_rn((v - __half2float(hh)) * 2048.0f));
-            } else {
-              const __nv_bfloat16 hh = __float2bfloat16_rn(t[q]);
-              h[q] = __bfloat16_as_ushort(hh);
-              l[q] = __bfloat16_as_ushort(__float2bfloat16_rn(t[q] - __bfloat162float(hh)));
-            }
-          }
-          hw[e / 2] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-          lw[e / 2] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
         }
         const uint32_t off = (uint32_t)r * 128u + sw;
         *reinterpret_cast<uint4*>(sth + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -730,8 +755,8 @@ cudaError_t launch_mf_variant(const float4* pos, int n, float tscale, const CUte
     attr = true;
   }
   dim3 grd(ncols / BN, np / TC_BM);
-  k_tc_mf<F16, BN, ST><<<grd, 384, TcCfg<BN, ST>::SMEM, s>>>(pos, n, tscale, mXh, mXl, Y, ldy, np,
-                                                             s1, s2, err);
+  k_tc_mf<F16, BN, ST><<<grd, kMfThreads, TcCfg<BN, ST>::SMEM, s>>>(pos, n, tscale, mXh, mXl, Y,
+                                                                    ldy, np, s1, s2, err);
   return cudaGetLastError();
 }
 

@@ -691,7 +691,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
   const bool tc_f16 = o.precision == PX_FP16SPLIT;
   if (tc && d.Thi == nullptr && !d.matfree)
     throw PxError{PX_EINVAL, "precision changed since px_set_structure"};
-  const size_t colpad = px::kTile;   // operand column padding of every matvec kernel
+  // operand column padding of every matvec kernel; the tensor-core pair kernel runs
+  // 256-column tiles (each generated T tile then serves twice the columns)
+  const size_t colpad = (d.matfree && tc) ? 2 * px::kTile : px::kTile;
   // stopping targets of the inner (low-precision) iteration:
   //   max(inner_tol * ||r_outer||, tol_frac * tol * ||b||)
   const double inner_tol = lowp ? o.inner_tol : 0.0;

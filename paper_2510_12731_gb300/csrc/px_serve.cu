@@ -43,6 +43,8 @@ struct Req {
   px_status st = PX_OK;
   int state = 0;   // 0 queued, 1 running, 2 done
   double t_submit = 0, t_start = 0, t_done = 0;
+  // requests solved with this one as extra columns of its block (this one leads)
+  std::vector<Req*> group;
 };
 
 struct Slot {
@@ -115,7 +117,7 @@ struct px_server {
   std::vector<Slot*> slots;
   uint64_t next_id = 1;
   size_t peak_reserved = 0;
-  long long submitted = 0, completed = 0, failed = 0, reuses = 0;
+  long long submitted = 0, completed = 0, failed = 0, reuses = 0, merged = 0;
   double points = 0.0;
   std::vector<double> latencies_ms;
   Clock::time_point t0 = Clock::now();
@@ -124,6 +126,40 @@ struct px_server {
 };
 
 namespace {
+
+// Largest block of frequencies one merged solve takes.
+constexpr int kMergeMaxFreq = 512;
+
+// Queued requests that can join r's solve as extra columns: the same structure, operator
+// mode and model (so the same T, CSR and shifts' form), the same field directions and E0
+// (so the same right-hand sides); their frequency lists are appended to r's.  The
+// group's footprint must still fit beside the other slots (lock held).
+void gather_group(px_server* s, Req* r, const Slot* pick) {
+  size_t others = 0;
+  for (const Slot* o : s->slots)
+    if (o != pick) others += std::max(o->retained, o->req ? o->req->footprint : 0);
+  int F = r->F;
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Req* q = *it;
+    const bool same = q != r && q->key == r->key && q->mode == r->mode && q->model == r->model &&
+                      q->P == r->P && q->e0 == r->e0 && q->ntypes == r->ntypes &&
+                      q->pol == r->pol && F + q->F <= kMergeMaxFreq;
+    if (!same) {
+      ++it;
+      continue;
+    }
+    const size_t fp = footprint(s->opt, r->model, r->N, (F + q->F) * r->P,
+                                r->mode == PX_MODE_MATERIALISED);
+    if (others + std::max(pick->retained, fp) > s->budget) break;
+    F += q->F;
+    r->footprint = std::max(r->footprint, fp);
+    q->state = 1;
+    q->t_start = r->t_start;
+    r->group.push_back(q);
+    ++s->merged;
+    it = s->queue.erase(it);
+  }
+}
 
 size_t reserved_bytes(const px_server* s) {
   size_t t = 0;
@@ -152,8 +188,9 @@ void admit(px_server* s) {
       sl->req = r;
       r->state = 1;
       r->t_start = now;
-      s->peak_reserved = std::max(s->peak_reserved, reserved_bytes(s));
       s->queue.erase(it);
+      gather_group(s, r, sl);
+      s->peak_reserved = std::max(s->peak_reserved, reserved_bytes(s));
       sl->cv.notify_one();
       break;
     }
@@ -193,10 +230,66 @@ void admit(px_server* s) {
     pick->req = r;
     r->state = 1;
     r->t_start = now;
+    s->queue.erase(it);
+    gather_group(s, r, pick);
     s->peak_reserved = std::max(s->peak_reserved, reserved_bytes(s));
-    it = s->queue.erase(it);
     pick->cv.notify_one();
+    // erasing invalidated the iterators: continue from the front (earlier entries that
+    // did not fit are checked again, as the next admission pass would)
+    it = s->queue.begin();
   }
+}
+
+// One solve for a request and the requests merged into it: the frequency lists (and the
+// alpha_ib rows, [n_types][F]) are concatenated, the results split back per request
+// (every result array is frequency-major).  Each request's status is its own columns'.
+px_status solve_group(px_handle* h, Req* r) {
+  std::vector<Req*> all{r};
+  all.insert(all.end(), r->group.begin(), r->group.end());
+  int F = 0;
+  for (const Req* q : all) F += q->F;
+  const size_t P = r->P, N = r->N, nt = r->ntypes, B = (size_t)F * P;
+  std::vector<double> omega, aib;
+  for (const Req* q : all) omega.insert(omega.end(), q->omega.begin(), q->omega.end());
+  if (!r->aib.empty()) {
+    aib.reserve(2 * nt * F);
+    for (size_t t = 0; t < nt; ++t)
+      for (const Req* q : all)
+        aib.insert(aib.end(), q->aib.begin() + 2 * t * q->F, q->aib.begin() + 2 * (t + 1) * q->F);
+  }
+  std::vector<double> alpha(2 * B * 3), sigma(F), sigma_pol(B), qv(2 * B * N), mu, relres(B);
+  if (!r->mu.empty()) mu.resize(6 * B * N);
+  std::vector<int> iters(B), status(B);
+  px_result res;
+  res.alpha = alpha.data();
+  res.sigma_abs = sigma.data();
+  res.sigma_abs_pol = sigma_pol.data();
+  res.q = qv.data();
+  res.mu = mu.empty() ? nullptr : mu.data();
+  res.rel_residual = relres.data();
+  res.iters = iters.data();
+  res.status = status.data();
+  const px_status st = px_solve(h, F, omega.data(), aib.empty() ? nullptr : aib.data(), (int)P,
+                                r->pol.data(), r->e0, &res, nullptr);
+  if (st != PX_OK && st != PX_ENOTCONV) return st;
+  size_t f0 = 0;
+  for (Req* q : all) {
+    const size_t Fq = q->F, Bq = Fq * P, b0 = f0 * P;
+    std::copy(alpha.begin() + 2 * 3 * b0, alpha.begin() + 2 * 3 * (b0 + Bq), q->alpha.begin());
+    std::copy(sigma.begin() + f0, sigma.begin() + f0 + Fq, q->sigma.begin());
+    std::copy(sigma_pol.begin() + b0, sigma_pol.begin() + b0 + Bq, q->sigma_pol.begin());
+    std::copy(qv.begin() + 2 * N * b0, qv.begin() + 2 * N * (b0 + Bq), q->q.begin());
+    if (!mu.empty())
+      std::copy(mu.begin() + 6 * N * b0, mu.begin() + 6 * N * (b0 + Bq), q->mu.begin());
+    std::copy(relres.begin() + b0, relres.begin() + b0 + Bq, q->relres.begin());
+    std::copy(iters.begin() + b0, iters.begin() + b0 + Bq, q->iters.begin());
+    std::copy(status.begin() + b0, status.begin() + b0 + Bq, q->status.begin());
+    q->st = PX_OK;
+    for (size_t c = 0; c < Bq; ++c)
+      if (q->status[c] != PX_OK) q->st = PX_ENOTCONV;
+    f0 += Fq;
+  }
+  return r->st;
 }
 
 void slot_main(px_server* s, Slot* sl) {
@@ -218,7 +311,7 @@ void slot_main(px_server* s, Slot* sl) {
         st = px_set_structure(sl->h, (px_model)r->model, r->N, r->xyz.data(), r->tidx.data(),
                               r->types.data(), r->ntypes);
     }
-    if (st == PX_OK) {
+    if (st == PX_OK && r->group.empty()) {
       px_result res;
       res.alpha = r->alpha.data();
       res.sigma_abs = r->sigma.data();
@@ -230,11 +323,26 @@ void slot_main(px_server* s, Slot* sl) {
       res.status = r->status.data();
       st = px_solve(sl->h, r->F, r->omega.data(), r->aib.empty() ? nullptr : r->aib.data(), r->P,
                     r->pol.data(), r->e0, &res, nullptr);
+    } else if (st == PX_OK) {
+      st = solve_group(sl->h, r);
     }
     lk.lock();
     r->st = st;
     r->state = 2;
     r->t_done = seconds_since(s->t0);
+    for (Req* q : r->group) {
+      q->state = 2;
+      q->t_done = r->t_done;
+      if (st == PX_OK || st == PX_ENOTCONV) {
+        ++s->completed;
+        for (int c : q->status) s->points += (c == PX_OK) ? 1.0 : 0.0;
+      } else {
+        q->st = st;
+        ++s->failed;
+      }
+      s->latencies_ms.push_back((q->t_done - q->t_submit) * 1e3);
+    }
+    r->group.clear();
     if (st == PX_OK || st == PX_ENOTCONV) {
       sl->key = r->key;
       sl->mode = r->mode;
@@ -434,6 +542,7 @@ px_status px_server_get_stats(px_server* s, px_server_stats* st) {
   st->wall_s = seconds_since(s->t0);
   st->structure_reuses = s->reuses;
   st->peak_reserved_bytes = s->peak_reserved;
+  st->merged_requests = s->merged;
   return PX_OK;
 }
 

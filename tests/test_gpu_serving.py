@@ -141,3 +141,33 @@ def test_served_results_match_the_oracle(precision, solver):
         fidx, ref = _golden(i, w.pol_dirs.shape[0])
         err = np.linalg.norm(o["alpha"][fidx] - ref, axis=1) / np.linalg.norm(ref, axis=1)
         assert np.max(err) <= 1e-5, (w.name, np.max(err))
+
+
+@pytest.mark.parametrize("model", ["wfq", "wfqfmu"])
+def test_same_structure_requests_merge_into_one_block(model):
+    """One slot, busy with another structure: three queued requests on one structure with
+    the same field directions and different frequency grids are solved as one block
+    (their frequencies appended, alpha_ib rows concatenated per type), and each gets back
+    exactly its own columns: equal to its alone result, in its own frequency order."""
+    from paper_2510_12731_gb300 import Server
+    blocker = _mix()[2]                        # Na sphere r = 14 A, 23 w x 3
+    el = S.ELEMENTS["Au"] if model == "wfqfmu" else S.ELEMENTS["Ag"]
+    xyz = S.sphere("fcc", 4.08 if model == "wfqfmu" else 4.09, 8.0)
+    grids = [np.linspace(2.0, 5.0, 9), np.linspace(2.7, 3.9, 5)[::-1], np.linspace(3.1, 4.6, 13)]
+    same = []
+    for w in grids:
+        same.append(dict(model=model, xyz_ang=xyz, type_idx=np.zeros(len(xyz), np.int32),
+                         types=[el.atom_type()], omega_ev=w, pol_dirs=S.XYZ,
+                         alpha_ib=el.alpha_ib(w)[None, :] if model == "wfqfmu" else None))
+    alone = [_alone(r, precision="fp32", tol_rel=TOL) for r in same]
+    with Server(max_slots=1, precision="fp32", tol_rel=TOL) as srv:
+        ids = [srv.submit(**blocker)] + [srv.submit(**r) for r in same]
+        outs = [srv.wait(i) for i in ids][1:]
+        st = srv.stats()
+    assert st["merged_requests"] == 2 and st["completed"] == 4 and st["failed"] == 0
+    for a, o in zip(alone, outs):
+        assert o["ok"] and o["alpha"].shape == a["alpha"].shape
+        num = np.linalg.norm(o["alpha"] - a["alpha"], axis=1)
+        assert np.max(num / np.linalg.norm(a["alpha"], axis=1)) <= 1e-6
+        assert np.all(o["rel_residual"] <= TOL)
+        assert np.allclose(o["sigma_abs"], a["sigma_abs"], rtol=1e-6)

@@ -72,7 +72,7 @@ def test_prolate_spheroid_approaches_depolarisation_closed_form():
 
 
 def test_drude_sphere_resonance_at_wp_over_sqrt3():
-    w = S.drude_sphere_mesh(1600, nfreq=401, wmin=2.5, wmax=4.5, pols=np.eye(3)[:1])
+    w = S.drude_sphere_mesh(1600, nfreq=27, wmin=3.40, wmax=3.53, pols=np.eye(3)[:1])
     a, _, _ = BE.solve(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1, w.pol_dirs,
                        radius_ang=w.radius_ang)
     peak = w.omega_ev[np.argmax(a[:, 0, 0].imag)]
@@ -136,7 +136,7 @@ def test_iefpcm_weak_contrast_resonance_and_coulomb_matrix():
     assert a[0, 0, 0] / (rb ** 3 * 1e-6 / 3.0) == pytest.approx(1.0, abs=5e-3)
     G = BE.g_matrix(pos / M.BOHR_ANG, area / M.BOHR_ANG ** 2)
     assert np.array_equal(G, G.T) and np.linalg.eigvalsh(G).min() > 0   # Coulomb: SPD
-    w = S.drude_sphere_mesh(1600, nfreq=401, wmin=2.5, wmax=4.5, pols=np.eye(3)[:1])
+    w = S.drude_sphere_mesh(1600, nfreq=27, wmin=3.40, wmax=3.53, pols=np.eye(3)[:1])
     a, _, _ = BE.solve_iefpcm(w.pos_ang, w.normals, w.area_ang2, w.eps2, w.eps1, w.pol_dirs,
                               radius_ang=w.radius_ang)
     assert w.omega_ev[np.argmax(a[:, 0, 0].imag)] == pytest.approx(6.0 / math.sqrt(3.0), abs=0.01)
