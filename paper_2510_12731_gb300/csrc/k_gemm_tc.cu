@@ -502,35 +502,34 @@ namespace px {
 // straight into shared memory, as the hi / lo planes of the split (the layout a
 // 128-byte-swizzled TMA load would produce), and contracted with the X tiles (TMA) by
 // tcgen05.mma exactly as in k_tc_gemm; nothing of T is stored.
-//   warp 0        TMA producer of the X hi / lo tiles (BN x 64 per K step)
+//   warp 0        TMA producer: per K step the 64 atoms' positions (1 KB, bulk copy) and
+//                 the X hi / lo tiles (BN x 64)
 //   warp 1        MMA issuer (one elected thread, 4 x 3 MMAs per K step)
 //   warp 2        TMEM allocation
-//   warps 4-19    generators: 128 rows x 64 atoms per K step; a thread owns one 16-byte
-//                 chunk (8 consecutive atoms) of two rows; then warps 4-7 run the epilogue
-// A pair costs one reciprocal square root while r >= 4 R (erf(r/R) = 1 in FP32, so
-// T = 1/r); pairs closer than that take erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in
-// a branch the warp enters only when one of its lanes has such a pair (atoms are in
-// Morton order, so most tiles have none).  A stage is full when the TMA bytes landed and
-// all sixteen generator warps arrived (each after a proxy fence, so that the tensor core
-// sees the generic-proxy stores).
-// FP16 split: T' = 2^e T (2^e max|T| <= 2^14, max|T| = sqrt(2/pi)/min R_q), hi = RN(T'),
-// lo = RN((T' - hi) 2^11); the epilogue returns Y = D1 2^-(e+8) + D2 2^-(e+19) (X' = 2^8 X).
-// BF16 split: hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
-// Atoms beyond n generate 0.
+//   warps 4-19    generators: warp w writes the 16-byte chunk c = w % 8 (atoms 8c .. 8c+7
+//                 of the step) of 64 rows (lane, lane + 32 of its half), so the warp reads
+//                 the same eight positions (a broadcast) and its stores cover eight swizzled
+//                 chunk positions (no bank conflicts); then warps 4-7 run the epilogue
+// Positions come pre-scaled by 2^-e (launch_tc_mf_positions), so 1/r and erf(r/R)/r are
+// generated as 2^e T directly, and padded to np atoms with distinct far-away dummies
+// (their columns meet zero operand rows; their rows are never read).  A pair costs one
+// reciprocal square root while r >= 4 R (erf(r/R) = 1 in FP32); closer pairs take
+// erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in a branch a warp enters only when one
+// of its lanes has such a pair (atoms are in Morton order, so most tiles have none).
+// Barriers per stage: pos_full (positions landed; the producer issues them only after the
+// MMA released the stage), full (X bytes + sixteen generator arrivals, each after a proxy
+// fence so the tensor core sees the generic-proxy stores), empty (MMA commit).
+// FP16 split: hi = RN(2^e T), lo = RN((2^e T - hi) 2^11), Y = D1 2^-(e+8) + D2 2^-(e+19)
+// (X' = 2^8 X).  BF16 split (e = 0): hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
 namespace {
 
 constexpr int kMfGenWarps = 16;
 constexpr int kMfThreads = 128 + 32 * kMfGenWarps;
-
-// positions of atoms beyond n: far from every atom and from each other, so that no
-// padded pair reaches the close-pair branch except its own diagonal
-__device__ __forceinline__ float4 mf_pos(const float4* __restrict__ pos, int i, int n) {
-  return i < n ? __ldg(pos + i) : make_float4(3.0e4f + 64.0f * (float)(i - n), 0.f, 0.f, 1.f);
-}
+constexpr int kMfPosBytes = TC_BK * 16;   // 64 float4 per K step
 
 template <int F16, int TC_BN, int TC_STAGES>
 __global__ void __launch_bounds__(kMfThreads, 1)
-k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
+k_tc_mf(const float4* __restrict__ pos, float wmax,
         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
         float* __restrict__ Y, int ldy, int K, float s1, float s2, int* err) {
   using Cfg = TcCfg<TC_BN, TC_STAGES>;
@@ -539,10 +538,12 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE);
-  uint64_t* full = bars;                    // [TC_STAGES]: TMA + generator warps
-  uint64_t* empty = bars + TC_STAGES;       // [TC_STAGES]: MMA commit
-  uint64_t* accum = bars + 2 * TC_STAGES;   // [1]
+  float4* spos = reinterpret_cast<float4*>(base + TC_STAGES * STAGE);   // [TC_STAGES][64]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE + TC_STAGES * kMfPosBytes);
+  uint64_t* full = bars;                      // [TC_STAGES]: X bytes + generator warps
+  uint64_t* empty = bars + TC_STAGES;         // [TC_STAGES]: MMA commit
+  uint64_t* pfull = bars + 2 * TC_STAGES;     // [TC_STAGES]: positions landed
+  uint64_t* accum = bars + 3 * TC_STAGES;     // [1]
   __shared__ uint32_t tmem_slot;
   __shared__ int cta_abort;
   __shared__ int n_issued, n_consumed;
@@ -555,6 +556,7 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1 + kMfGenWarps);
       mbar_init(&empty[s], 1);
+      mbar_init(&pfull[s], 1);
     }
     mbar_init(accum, 1);
     cta_abort = 0;
@@ -575,12 +577,18 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
   volatile int* abort_flag = &cta_abort;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer (operand tiles)
+    // ---------------- TMA producer (positions, operand tiles)
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
       if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
       unsigned char* st = base + s * STAGE;
+      mbar_expect_tx(&pfull[s], kMfPosBytes);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              su32(spos + s * TC_BK)),
+          "l"(reinterpret_cast<uint64_t>(pos + (size_t)kt * TC_BK)), "r"(kMfPosBytes), "r"(su32(&pfull[s]))
+          : "memory");
       mbar_expect_tx(&full[s], 2 * B_TILE);
       const int kx = kt * TC_BK;
       tma_load_2d(st + 2 * A_TILE, &mXh, &full[s], kx, c0);
@@ -617,32 +625,31 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
     mma_commit(accum);
   } else if (warp >= 4) {
     // ---------------- generators: T tiles in the swizzled K-major layout
-    const int gt = threadIdx.x - 128;            // 0 .. 511
-    const int c = gt & 7;                        // 16-byte chunk (8 atoms) of the 64-atom step
-    const int rb = gt >> 3;                      // rows rb and rb + 64
+    const int gw = warp - 4;                     // 0 .. 15
+    const int c = gw & 7;                        // 16-byte chunk (atoms 8c .. 8c+7 of the step)
+    const int r_lo = (gw >> 3) * 64 + lane;      // rows r_lo and r_lo + 32
     float4 pi[2];
-    bool rv[2];
+    float thr[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int i = i0 + rb + 64 * u;
-      pi[u] = mf_pos(pos, i, n);
-      rv[u] = i < n;
+      pi[u] = __ldg(pos + i0 + r_lo + 32 * u);
+      thr[u] = 16.0f * (pi[u].w + wmax);          // r^2 below this: a close pair is possible
     }
-    const uint32_t sw = (uint32_t)((c ^ (rb & 7)) << 4);   // (row & 7) == (rb & 7) for both rows
+    const uint32_t sw = (uint32_t)((c ^ (lane & 7)) << 4);   // row & 7 == lane & 7
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      // positions landed (issued after the MMA released this stage)
+      if (!mbar_wait(&pfull[s], ph, err, abort_flag)) break;
       unsigned char* sth = base + s * STAGE;
       unsigned char* stl = sth + A_TILE;
-      const int kb = kt * TC_BK + c * 8;
       float4 pk[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) pk[e] = mf_pos(pos, kb + e, n);
+      for (int e = 0; e < 8; ++e) pk[e] = spos[s * TC_BK + c * 8 + e];
+      const int kb = kt * TC_BK + c * 8;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int r = rb + 64 * u;
-        const int i = i0 + r;
+        const int r = r_lo + 32 * u;
         float t[8];
         bool near_any = false;
 #pragma unroll
@@ -650,9 +657,10 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
           const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           t[e] = rsqrtf(r2);
-          near_any |= r2 < 16.0f * (pi[u].w + pk[e].w);
+          near_any |= r2 < thr[u];
         }
         if (__any_sync(0xffffffffu, near_any)) {
+          const int i = i0 + r;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
@@ -665,19 +673,16 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          const float t0 = (rv[u] && kb + e < n) ? t[e] : 0.f;
-          const float t1 = (rv[u] && kb + e + 1 < n) ? t[e + 1] : 0.f;
           if (F16) {
-            const float v0 = t0 * tscale, v1 = t1 * tscale;
-            const __half2 h = __floats2half2_rn(v0, v1);
+            const __half2 h = __floats2half2_rn(t[e], t[e + 1]);
             const float2 hf = __half22float2(h);
-            const __half2 l = __floats2half2_rn((v0 - hf.x) * 2048.0f, (v1 - hf.y) * 2048.0f);
+            const __half2 l = __floats2half2_rn((t[e] - hf.x) * 2048.0f, (t[e + 1] - hf.y) * 2048.0f);
             hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
             lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
           } else {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(t0, t1);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(t[e], t[e + 1]);
             const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(t0 - hf.x, t1 - hf.y);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(t[e] - hf.x, t[e + 1] - hf.y);
             hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
             lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
           }
@@ -726,11 +731,14 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (cta_abort && threadIdx.x == 0) {
-    // after a time-out: wait (bounded) for operand loads that were issued but never consumed
+    // after a time-out: wait (bounded) for the copies that were issued but never consumed
     for (int kt = n_consumed; kt < n_issued; ++kt) {
-      const long long t0 = clock64();
-      while (!mbar_try(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u) &&
-             clock64() - t0 < kWaitCycles) {
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      long long t0 = clock64();
+      while (!mbar_try(&full[kt % TC_STAGES], ph) && clock64() - t0 < kWaitCycles) {
+      }
+      t0 = clock64();
+      while (!mbar_try(&pfull[kt % TC_STAGES], ph) && clock64() - t0 < kWaitCycles) {
       }
     }
   }
@@ -742,47 +750,67 @@ k_tc_mf(const float4* __restrict__ pos, int n, float tscale,
   }
 }
 
+// Positions for k_tc_mf: (x, y, z, R_q^2) scaled by 2^-e (2^-2e for R_q^2), padded to np
+// with distinct dummies 3e4 + 64 (i - n) bohr away along x.
+__global__ void k_tc_mf_positions(const double* __restrict__ pos, const double* __restrict__ Rq,
+                                  int n, int np, double sc, float4* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  if (i < n)
+    out[i] = make_float4((float)(pos[3 * i] * sc), (float)(pos[3 * i + 1] * sc),
+                         (float)(pos[3 * i + 2] * sc), (float)(Rq[i] * Rq[i] * sc * sc));
+  else
+    out[i] = make_float4((float)((3.0e4 + 64.0 * (i - n)) * sc), 0.f, 0.f, (float)(sc * sc));
+}
+
 template <int F16, int BN, int ST>
-cudaError_t launch_mf_variant(const float4* pos, int n, float tscale, const CUtensorMap& mXh,
+cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& mXh,
                               const CUtensorMap& mXl, int np, int ncols, float* Y, int ldy,
                               float s1, float s2, int* err, cudaStream_t s) {
+  constexpr int smem = TcCfg<BN, ST>::SMEM + ST * kMfPosBytes;
+  static_assert(smem <= 227 * 1024, "shared memory per CTA");
   static bool attr = false;   // per process: every device uses the same attribute
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcCfg<BN, ST>::SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grd(ncols / BN, np / TC_BM);
-  k_tc_mf<F16, BN, ST><<<grd, kMfThreads, TcCfg<BN, ST>::SMEM, s>>>(pos, n, tscale, mXh, mXl, Y,
-                                                                    ldy, np, s1, s2, err);
+  k_tc_mf<F16, BN, ST><<<grd, kMfThreads, smem, s>>>(pos, wmax, mXh, mXl, Y, ldy, np, s1, s2, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tc_mf(const float4* pos, int n, int np, const uint16_t* Xh, const uint16_t* Xl,
-                         int ncols, float* Y, int ldy, bool f16, int scale_exp, int* err,
-                         cudaStream_t s, long long* nl) {
+cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
+                                   int scale_exp, float4* out, cudaStream_t s, long long* nl) {
+  k_tc_mf_positions<<<(np + 255) / 256, 256, 0, s>>>(pos, Rq, n, np, std::ldexp(1.0, -scale_exp), out);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
+                         const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
+                         int* err, cudaStream_t s, long long* nl) {
   // shape contract as launch_tc_gemm: 128-row output tiles and 64-atom K steps (np % 128),
-  // 128- or 256-column operand tiles, 16-byte aligned operand rows
-  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols || n > np) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl)) & 15)
+  // 128- or 256-column operand tiles, 16-byte aligned operand rows and positions
+  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+       reinterpret_cast<uintptr_t>(pos)) & 15)
     return cudaErrorMisalignedAddress;
   const int bn = ncols % 256 == 0 ? 256 : 128;
   CUtensorMap mXh, mXl;
   if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
     return cudaErrorInvalidValue;
-  const float tscale = std::ldexp(1.0f, scale_exp);
   const float s1 = std::ldexp(1.0f, -(scale_exp + 8)), s2 = std::ldexp(1.0f, -(scale_exp + 19));
   cudaError_t e;
   if (f16)
-    e = bn == 256 ? launch_mf_variant<1, 256, 2>(pos, n, tscale, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
-                  : launch_mf_variant<1, 128, 3>(pos, n, tscale, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+    e = bn == 256 ? launch_mf_variant<1, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                  : launch_mf_variant<1, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
   else
-    e = bn == 256 ? launch_mf_variant<0, 256, 2>(pos, n, 1.0f, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
-                  : launch_mf_variant<0, 128, 3>(pos, n, 1.0f, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
+    e = bn == 256 ? launch_mf_variant<0, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
+                  : launch_mf_variant<0, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
   ++*nl;
   return e;
 }

@@ -764,7 +764,10 @@ __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, d
                                                  double2* r, int B) {
   using TT = Tr<E>;
   constexpr int kXChunk = 32, kRows = 4;
-  __shared__ double2 shy[kXChunk][32], shu[kXChunk][32];
+  using C = typename TT::Coef;
+  // y and u in the basis's own arithmetic (FP32 for the FP32 basis: GB300's FP64 pipe is
+  // 1/64 of its FP32 rate, and the correction needs no more than the basis carries)
+  __shared__ C shy[kXChunk][32], shu[kXChunk][32];
   __shared__ double sh[8][32];
   __shared__ int sh_jmax;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -790,18 +793,18 @@ __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, d
     const int kend = min(jmax + 1, k0 + kXChunk);   // uniform over the block
     if (k0 > 0) __syncthreads();                    // previous chunk consumed
     for (int k = k0 + ty; k < kend; k += 8) {
-      shy[k - k0][tx] = (valid && k < jc) ? a.y[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0);
-      shu[k - k0][tx] = (valid && k <= jc) ? a.u[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0);
+      shy[k - k0][tx] = TT::coef((valid && k < jc) ? a.y[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0));
+      shu[k - k0][tx] = TT::coef((valid && k <= jc) ? a.u[(size_t)k * a.Bact + col] : make_double2(0.0, 0.0));
     }
     __syncthreads();
     if (!valid) continue;
     const bool first = k0 == 0, last = kend == jmax + 1;
     for (int rb = 0; rb < nrows; rb += kRows) {
-      double2 dx[kRows], ar[kRows];
+      typename TT::Acc dxa[kRows], ara[kRows];
 #pragma unroll
-      for (int q = 0; q < kRows; ++q) dx[q] = ar[q] = make_double2(0.0, 0.0);
+      for (int q = 0; q < kRows; ++q) dxa[q] = ara[q] = TT::zero();
       for (int k = k0; k < kend; ++k) {
-        const double2 yk = shy[k - k0][tx], uk = shu[k - k0][tx];
+        const C yk = shy[k - k0][tx], uk = shu[k - k0][tx];
         E v[kRows];
 #pragma unroll
         for (int q = 0; q < kRows; ++q)
@@ -810,28 +813,25 @@ __global__ void __launch_bounds__(256) k_xupdate(KrylovArgs a, const int* act, d
 #pragma unroll
         for (int q = 0; q < kRows; ++q) {
           if (rb + q >= nrows) continue;
-          const double2 vc = TT::to_c(v[q]);
-          const double2 pu = cmul(vc, uk), py = cmul(vc, yk);
-          ar[q].x += pu.x;
-          ar[q].y += pu.y;
-          dx[q].x += py.x;
-          dx[q].y += py.y;
+          TT::mac(ara[q], v[q], uk);
+          TT::mac(dxa[q], v[q], yk);
         }
       }
 #pragma unroll
       for (int q = 0; q < kRows; ++q) {
         if (rb + q >= nrows) continue;
         const int i = r0 + ty + 8 * (rb + q);
+        const double2 arq = TT::to_d2(ara[q]);
         // x += M V y with M = alpha^IB on the dipole rows (right preconditioner)
-        double2 d = dx[q];
+        double2 d = TT::to_d2(dxa[q]);
         if (a.amu && i >= a.N) d = cmul(a.amu[(size_t)a.type[(i - a.N) / 3] * a.Bact + col], d);
         double2 ax = x[(size_t)i * B + gc];
         ax.x += d.x;
         ax.y += d.y;
         x[(size_t)i * B + gc] = ax;
         double2 rv = first ? make_double2(0.0, 0.0) : r[(size_t)i * B + gc];
-        rv.x += ar[q].x;
-        rv.y += ar[q].y;
+        rv.x += arq.x;
+        rv.y += arq.y;
         r[(size_t)i * B + gc] = rv;
         if (last) nrm += rv.x * rv.x + rv.y * rv.y;
       }

@@ -78,6 +78,7 @@ struct px_handle {
   DevBuf b_stage;  // staging inputs (caller order) and sort scratch
   DevBuf b_T64, b_T32, b_Thi, b_Tlo, b_pos4f, b_pos4d, b_Tffh, b_Tffl;
   DevBuf b_rm2;    // matrix-free wFQFmu: R_mu^2 in FP32 and FP64
+  DevBuf b_pos4tc; // matrix-free split precisions: scaled, padded positions
   DevBuf b_mesh;   // boundary elements: normals [N][3], areas [N]
   // IEFPCM (Eq. 12): the operator S A^-1 of the second step and its planes, and the first
   // step's solution y (the second step's right-hand side)
@@ -123,7 +124,7 @@ void drop_graphs(px_handle* h) {
 void free_all(px_handle* h) {
   DevBuf* bufs[] = {&h->b_M64, &h->b_perm, &h->b_stage, &h->b_pos, &h->b_Rq, &h->b_Rmu, &h->b_area, &h->b_type, &h->b_rowptr,
                     &h->b_col, &h->b_val64, &h->b_val32, &h->b_counts, &h->b_pair, &h->b_T64,
-                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_rm2, &h->b_mesh, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
+                    &h->b_T32, &h->b_Thi, &h->b_Tlo, &h->b_pos4f, &h->b_pos4d, &h->b_rm2, &h->b_pos4tc, &h->b_mesh, &h->b_Tffh, &h->b_Tffl, &h->b_pol, &h->b_b, &h->b_x, &h->b_r,
                     &h->b_rnorm, &h->b_bnorm, &h->b_iters, &h->b_act, &h->b_zq, &h->b_zmu,
                     &h->b_V, &h->b_W, &h->b_h, &h->b_part, &h->b_normpart, &h->b_R, &h->b_g,
                     &h->b_cs, &h->b_sn, &h->b_target, &h->b_jconv, &h->b_invh, &h->b_y,
@@ -394,16 +395,24 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.mu_self = h->opt.mu_self_term;
   d.rm2f = nullptr;
   d.rm2d = nullptr;
+  d.pos4tc = nullptr;
+  d.tc_wmax = 0.f;
   if (d.matfree) {
     // split precisions run the tensor-core pair kernel (wFQ): T scaled by 2^e before the
     // fp16 split, 2^e max|T| <= 2^14 with max|T| = sqrt(2/pi) / min R_q (the diagonal)
     if (split && model != PX_WFQ)
       throw PxError{PX_ENOTIMPL, "matrix-free wFQFmu runs PX_FP32 or PX_FP64 matvecs"};
     if (split) {
-      double rq_min = types[0].Rq_bohr;
-      for (int t = 1; t < ntypes; ++t) rq_min = std::min(rq_min, types[t].Rq_bohr);
+      double rq_min = types[0].Rq_bohr, rq_max = types[0].Rq_bohr;
+      for (int t = 1; t < ntypes; ++t) {
+        rq_min = std::min(rq_min, types[t].Rq_bohr);
+        rq_max = std::max(rq_max, types[t].Rq_bohr);
+      }
       const double tmax = 0.7978845608028654 / rq_min;
-      d.op_scale_exp = std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / tmax))));
+      d.op_scale_exp = prec == PX_FP16SPLIT
+                           ? std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / tmax))))
+                           : 0;
+      d.tc_wmax = (float)(rq_max * rq_max * std::ldexp(1.0, -2 * d.op_scale_exp));
     }
     CU(h->b_pos4f.ensure(sizeof(float4) * N));
     CU(h->b_pos4d.ensure(sizeof(double) * 4 * N));
@@ -415,6 +424,11 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
       d.rm2d = reinterpret_cast<double*>(h->b_rm2.as<unsigned char>() + round_up(sizeof(float) * N, 256));
     }
     CU(px::launch_stage_pos4(d, s, &h->nl));
+    if (split) {
+      CU(h->b_pos4tc.ensure(sizeof(float4) * (size_t)d.np));
+      d.pos4tc = h->b_pos4tc.as<float4>();
+      CU(px::launch_tc_mf_positions(d.pos64, d.Rq, N, d.np, d.op_scale_exp, d.pos4tc, s, &h->nl));
+    }
   } else {
     CU(h->b_T64.ensure(np2 * sizeof(double)));
     d.T64 = h->b_T64.as<double>();
@@ -1117,8 +1131,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
         } else if (d.matfree && tc) {
           // tensor-core pair kernel: T tiles generated in shared memory as split planes
           CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt));
-          CU(px::launch_tc_mf(d.pos4f, N, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, d.op_scale_exp,
-                              h->d_err, q, cnt));
+          CU(px::launch_tc_mf(d.pos4tc, np, d.tc_wmax, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
+                              d.op_scale_exp, h->d_err, q, cnt));
         } else if (d.matfree) {
           if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
@@ -1165,6 +1179,8 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
                                 &nl, -1, nullptr));
         }
+        uint32_t wmax_bits = 0;
+        std::memcpy(&wmax_bits, &d.tc_wmax, sizeof(wmax_bits));
         const std::vector<uint64_t> key = {
             (uint64_t)Bact, (uint64_t)mc, (uint64_t)ldxa, (uint64_t)passes, (uint64_t)A.basis,
             (uint64_t)o.precision, (uint64_t)d.matfree, (uint64_t)o.gemm_tiles,
@@ -1184,6 +1200,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
             (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
             (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d,
             (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp, (uint64_t)d.bem,
+            (uint64_t)(uintptr_t)d.pos4tc, wmax_bits,
             (uint64_t)(uintptr_t)dpart, (uint64_t)dpart_elems};
         CycleGraph* cg = nullptr;
         for (size_t k = 0; k < h->graphs.size(); ++k) {

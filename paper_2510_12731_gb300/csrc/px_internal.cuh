@@ -53,6 +53,9 @@ struct DevStructure {
   double* pos4d = nullptr;     // matrix-free: [N][4] x, y, z, R_q^2 (FP64)
   float* rm2f = nullptr;       // matrix-free wFQFmu: R_mu^2 (FP32)
   double* rm2d = nullptr;      // matrix-free wFQFmu: R_mu^2 (FP64)
+  float4* pos4tc = nullptr;    // matrix-free split (tensor-core pair kernel): positions and
+                               //   R_q^2 scaled by 2^-op_scale_exp, padded to np
+  float tc_wmax = 0.f;         //   the largest scaled R_q^2
   int mu_self = 0;             // Gaussian self term on the T^mumu diagonal (options at set-up)
   bool matfree = false;
   int* perm = nullptr;         // [N] caller's index of internal (Morton-sorted) atom i
@@ -172,14 +175,19 @@ cudaError_t launch_tc_gemm(const uint16_t* Th, const uint16_t* Tl, int np, const
                            cudaStream_t s, long long* nl, int variant, int* used);
 // The autotuner's cached variant for a shape on the current device, or -1.
 int tc_tuned_variant(int np, int ncols, bool f16);
-// Matrix-free wFQ block matvec Y = T X on the tensor cores: T^qq tiles generated from pos
-// [n] (x, y, z, R_q^2 in FP32, bohr) into shared memory as split planes and contracted with
-// the split operand (Xh / Xl as for launch_tc_gemm).  f16: T scaled by 2^scale_exp before the
-// split (2^scale_exp max|T| <= 2^14); Y is returned unscaled.  128 x 256 tiles when
-// ncols % 256 == 0, else 128 x 128.  *err as for launch_tc_gemm.
-cudaError_t launch_tc_mf(const float4* pos, int n, int np, const uint16_t* Xh, const uint16_t* Xl,
-                         int ncols, float* Y, int ldy, bool f16, int scale_exp, int* err,
-                         cudaStream_t s, long long* nl);
+// Matrix-free wFQ block matvec Y = T X on the tensor cores: T^qq tiles generated from the
+// scaled, padded positions of launch_tc_mf_positions (wmax: their largest R_q^2) into shared
+// memory as split planes and contracted with the split operand (Xh / Xl as for
+// launch_tc_gemm).  f16: the tiles hold 2^scale_exp T (2^scale_exp max|T| <= 2^14; bf16:
+// scale_exp = 0); Y is returned unscaled.  128 x 256 tiles when ncols % 256 == 0, else
+// 128 x 128.  *err as for launch_tc_gemm.
+cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
+                         const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
+                         int* err, cudaStream_t s, long long* nl);
+// Its positions: pos (bohr) and Rq in internal order -> out [np] (x, y, z, R_q^2) scaled by
+// 2^-scale_exp (R_q^2 by 2^-2 scale_exp), atoms n .. np-1 distinct far-away dummies.
+cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
+                                   int scale_exp, float4* out, cudaStream_t s, long long* nl);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
 cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
                             uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);

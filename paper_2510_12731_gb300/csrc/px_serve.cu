@@ -395,8 +395,7 @@ px_status px_server_create(px_server** out, const px_options* opt, int max_slots
   if (!s) return PX_ENOMEM;
   if (opt) s->opt = *opt;
   else px_options_default(&s->opt);
-  // every slot shares the server's budget; a handle's own admission must not refuse
-  s->opt.hbm_budget_bytes = 0;
+
   // the shifted solver's basis limit is fixed for served requests, so that admission can
   // account for its work space (a handle alone sizes it from the free memory)
   if (s->opt.solver == PX_SOLVER_SHIFTED && s->opt.shift_krylov_max == 0) s->opt.shift_krylov_max = 1500;
@@ -411,6 +410,10 @@ px_status px_server_create(px_server** out, const px_options* opt, int max_slots
     return PX_ECUDA;
   }
   s->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)fr);
+  // every slot shares the server's budget, which admission already enforces: a slot's
+  // handle checks its operators against the whole budget, not against the memory that
+  // happens to be free beside the other slots
+  s->opt.hbm_budget_bytes = s->budget;
   for (int i = 0; i < max_slots; ++i) {
     Slot* sl = new Slot();
     s->slots.push_back(sl);
@@ -444,9 +447,10 @@ px_status px_submit(px_server* s, const px_request* r, uint64_t* req_id) {
   // materialised operators when they fit a share of the budget, else on the fly (wFQ)
   const size_t fmat = footprint(s->opt, q->model, q->N, (int)B, true);
   const size_t ffree = footprint(s->opt, q->model, q->N, (int)B, false);
+  // (on the fly: every precision for wFQ, FP32 / FP64 for wFQFmu)
   const bool split = s->opt.precision == PX_BF16SPLIT || s->opt.precision == PX_FP16SPLIT;
   if (s->opt.mode == PX_MODE_MATFREE || (s->opt.mode == PX_MODE_AUTO && fmat > s->budget / 2 &&
-                                         q->model == PX_WFQ && !split)) {
+                                         (q->model == PX_WFQ || !split))) {
     q->mode = PX_MODE_MATFREE;
     q->footprint = ffree;
   } else {
