@@ -512,7 +512,9 @@ namespace px {
 //                 chunk positions (no bank conflicts); then warps 4-7 run the epilogue
 // Positions come pre-scaled by 2^-e (launch_tc_mf_positions), so 1/r and erf(r/R)/r are
 // generated as 2^e T directly, and padded to np atoms with distinct far-away dummies
-// (their columns meet zero operand rows; their rows are never read).  A pair costs one
+// (their columns meet zero operand rows; their rows are never read); they are stored as
+// atom pairs with negated coordinates, so the differences and r^2 run as packed FP32x2
+// operations (two pairs per instruction).  A pair costs one
 // reciprocal square root while r >= 4 R (erf(r/R) = 1 in FP32); closer pairs take
 // erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in a branch a warp enters only when one
 // of its lanes has such a pair (atoms are in Morton order, so most tiles have none).
@@ -625,17 +627,27 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
     mma_commit(accum);
   } else if (warp >= 4) {
     // ---------------- generators: T tiles in the swizzled K-major layout
+    // Positions arrive as atom pairs [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1] (w = R_q^2), so that the
+    // differences and r^2 of two atoms run as packed FP32x2 instructions.
     const int gw = warp - 4;                     // 0 .. 15
     const int c = gw & 7;                        // 16-byte chunk (atoms 8c .. 8c+7 of the step)
     const int r_lo = (gw >> 3) * 64 + lane;      // rows r_lo and r_lo + 32
-    float4 pi[2];
-    float thr[2];
+    const float* posf = reinterpret_cast<const float*>(pos);
+    float2 px[2], py[2], pz[2];
+    float pw[2], thr[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      pi[u] = __ldg(pos + i0 + r_lo + 32 * u);
-      thr[u] = 16.0f * (pi[u].w + wmax);          // r^2 below this: a close pair is possible
+      const int i = i0 + r_lo + 32 * u;
+      const float* pp = posf + (size_t)(i >> 1) * 8 + (i & 1);
+      const float x = -__ldg(pp), y = -__ldg(pp + 2), z = -__ldg(pp + 4);
+      px[u] = make_float2(x, x);
+      py[u] = make_float2(y, y);
+      pz[u] = make_float2(z, z);
+      pw[u] = __ldg(pp + 6);
+      thr[u] = 16.0f * (pw[u] + wmax);           // r^2 below this: a close pair is possible
     }
     const uint32_t sw = (uint32_t)((c ^ (lane & 7)) << 4);   // row & 7 == lane & 7
+    const float2 k2048 = make_float2(2048.0f, 2048.0f), km1 = make_float2(-1.0f, -1.0f);
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
@@ -643,48 +655,62 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
       if (!mbar_wait(&pfull[s], ph, err, abort_flag)) break;
       unsigned char* sth = base + s * STAGE;
       unsigned char* stl = sth + A_TILE;
-      float4 pk[8];
+      // atoms 8c .. 8c+7 = pairs 4c .. 4c+3
+      float2 kx[4], ky[4], kz[4], kw[4];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) pk[e] = spos[s * TC_BK + c * 8 + e];
+      for (int q = 0; q < 4; ++q) {
+        const float4 a = spos[s * TC_BK + (4 * c + q) * 2];
+        const float4 b = spos[s * TC_BK + (4 * c + q) * 2 + 1];
+        kx[q] = make_float2(a.x, a.y);
+        ky[q] = make_float2(a.z, a.w);
+        kz[q] = make_float2(b.x, b.y);
+        kw[q] = make_float2(b.z, b.w);
+      }
       const int kb = kt * TC_BK + c * 8;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int r = r_lo + 32 * u;
+        float2 r2[4];
         float t[8];
-        bool near_any = false;
+        float mn = 3.0e38f;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          t[e] = rsqrtf(r2);
-          near_any |= r2 < thr[u];
+        for (int q = 0; q < 4; ++q) {
+          // (x_i - x_k) for two atoms k: the pair holds -x_k
+          const float2 dx = __fadd2_rn(px[u], kx[q]), dy = __fadd2_rn(py[u], ky[q]),
+                       dz = __fadd2_rn(pz[u], kz[q]);
+          r2[q] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          t[2 * q] = rsqrtf(r2[q].x);
+          t[2 * q + 1] = rsqrtf(r2[q].y);
+          mn = fminf(mn, fminf(r2[q].x, r2[q].y));
         }
-        if (__any_sync(0xffffffffu, near_any)) {
+        if (__any_sync(0xffffffffu, mn < thr[u])) {
           const int i = i0 + r;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const float dx = pi[u].x - pk[e].x, dy = pi[u].y - pk[e].y, dz = pi[u].z - pk[e].z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float R2 = pi[u].w + pk[e].w;
-            if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pi[u].w);
-            else if (r2 < 16.0f * R2) t[e] = erff(r2 * t[e] * rsqrtf(R2)) * t[e];
+            const float rr = (e & 1) ? r2[e >> 1].y : r2[e >> 1].x;
+            const float wk = (e & 1) ? kw[e >> 1].y : kw[e >> 1].x;
+            const float R2 = pw[u] + wk;
+            if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pw[u]);
+            else if (rr < 16.0f * R2) t[e] = erff(rr * t[e] * rsqrtf(R2)) * t[e];
           }
         }
         uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int e = 0; e < 8; e += 2) {
+        for (int q = 0; q < 4; ++q) {
+          const float2 tv = make_float2(t[2 * q], t[2 * q + 1]);
           if (F16) {
-            const __half2 h = __floats2half2_rn(t[e], t[e + 1]);
+            const __half2 h = __float22half2_rn(tv);
             const float2 hf = __half22float2(h);
-            const __half2 l = __floats2half2_rn((t[e] - hf.x) * 2048.0f, (t[e + 1] - hf.y) * 2048.0f);
-            hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
-            lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
+            // lo = RN((t - hi) 2^11)
+            const __half2 l = __float22half2_rn(__fmul2_rn(__ffma2_rn(hf, km1, tv), k2048));
+            hw[q] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[q] = *reinterpret_cast<const uint32_t*>(&l);
           } else {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(t[e], t[e + 1]);
+            const __nv_bfloat162 h = __float22bfloat162_rn(tv);
             const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(t[e] - hf.x, t[e + 1] - hf.y);
-            hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
-            lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
+            const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(hf, km1, tv));
+            hw[q] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[q] = *reinterpret_cast<const uint32_t*>(&l);
           }
         }
         const uint32_t off = (uint32_t)r * 128u + sw;
@@ -750,17 +776,29 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
   }
 }
 
-// Positions for k_tc_mf: (x, y, z, R_q^2) scaled by 2^-e (2^-2e for R_q^2), padded to np
-// with distinct dummies 3e4 + 64 (i - n) bohr away along x.
+// Positions for k_tc_mf, scaled by 2^-e (R_q^2 by 2^-2e), as atom pairs
+// [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1] (w = R_q^2); np atoms, those beyond n distinct dummies
+// 3e4 + 64 (i - n) bohr away along x.
 __global__ void k_tc_mf_positions(const double* __restrict__ pos, const double* __restrict__ Rq,
-                                  int n, int np, double sc, float4* out) {
+                                  int n, int np, double sc, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  if (i < n)
-    out[i] = make_float4((float)(pos[3 * i] * sc), (float)(pos[3 * i + 1] * sc),
-                         (float)(pos[3 * i + 2] * sc), (float)(Rq[i] * Rq[i] * sc * sc));
-  else
-    out[i] = make_float4((float)((3.0e4 + 64.0 * (i - n)) * sc), 0.f, 0.f, (float)(sc * sc));
+  double x, y, z, w;
+  if (i < n) {
+    x = pos[3 * i];
+    y = pos[3 * i + 1];
+    z = pos[3 * i + 2];
+    w = Rq[i] * Rq[i];
+  } else {
+    x = 3.0e4 + 64.0 * (i - n);
+    y = z = 0.0;
+    w = 1.0;
+  }
+  float* o = out + (size_t)(i >> 1) * 8 + (i & 1);
+  o[0] = (float)(-x * sc);
+  o[2] = (float)(-y * sc);
+  o[4] = (float)(-z * sc);
+  o[6] = (float)(w * sc * sc);
 }
 
 template <int F16, int BN, int ST>
@@ -785,7 +823,8 @@ cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& 
 
 cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
                                    int scale_exp, float4* out, cudaStream_t s, long long* nl) {
-  k_tc_mf_positions<<<(np + 255) / 256, 256, 0, s>>>(pos, Rq, n, np, std::ldexp(1.0, -scale_exp), out);
+  k_tc_mf_positions<<<(np + 255) / 256, 256, 0, s>>>(pos, Rq, n, np, std::ldexp(1.0, -scale_exp),
+                                                    reinterpret_cast<float*>(out));
   ++*nl;
   return cudaGetLastError();
 }

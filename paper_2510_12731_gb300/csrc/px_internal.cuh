@@ -184,8 +184,9 @@ int tc_tuned_variant(int np, int ncols, bool f16);
 cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
                          int* err, cudaStream_t s, long long* nl);
-// Its positions: pos (bohr) and Rq in internal order -> out [np] (x, y, z, R_q^2) scaled by
-// 2^-scale_exp (R_q^2 by 2^-2 scale_exp), atoms n .. np-1 distinct far-away dummies.
+// Its positions: pos (bohr) and Rq in internal order -> out (np / 2 atom pairs of 8 floats,
+// [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1], w = R_q^2) scaled by 2^-scale_exp (w by 2^-2 scale_exp),
+// atoms n .. np-1 distinct far-away dummies.
 cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
                                    int scale_exp, float4* out, cudaStream_t s, long long* nl);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
