@@ -1302,6 +1302,10 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
     }
     if (d.matfree && model == PX_WFQFMU) {
       CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
+    } else if (d.matfree && lowp) {
+      // double-FP32 contraction of FP64 pair values; X32 / Y32 are free between cycles
+      CU(px::launch_split_ff(X64, (size_t)np * ldxa, X32, Y32, s, &nl));
+      CU(px::launch_ffgemm_mf(d.pos4d, N, np, X32, Y32, ldxa, Y64, ldxa, ldxa, s, &nl));
     } else if (d.matfree) {
       CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, s, &nl));
     } else if (2 * Bact <= 8 && !d.bem) {   // the GEMV reads rows: symmetric T only

@@ -147,6 +147,10 @@ cudaError_t launch_split_ff(const double* X, size_t n, float* Xh, float* Xl, cud
 // Matrix-free matvecs: T generated from the staged positions (wFQ, Eq. 5).
 cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, int ldx, float* Y,
                             int ldy, int ncols, cudaStream_t s, long long* nl);
+// FP64-class on-the-fly wFQ matvec for the true residual: T in FP64 per pair, the
+// contraction in double-FP32 with the operand as FP32 hi / lo planes [np][ldx].
+cudaError_t launch_ffgemm_mf(const double* pos4, int n, int np, const float* Xh, const float* Xl,
+                             int ldx, double* Y, int ldy, int ncols, cudaStream_t s, long long* nl);
 cudaError_t launch_dgemm_mf(const double* pos4, int n, int np, const double* X, int ldx,
                             double* Y, int ldy, int ncols, cudaStream_t s, long long* nl);
 // wFQFmu matrix-free matvecs: the 4 x 4 blocks of T (Sec. 2.2) generated per atom pair;
