@@ -96,7 +96,9 @@ def _roofline(prec, mode, flops_per_launch, avg_launch_s, launches, n_u=None):
             traffic = ratio * (4.0 * np_ * np_ + 16.0 * np_ * b_avg)
     return {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
-            "kernel": "k_sgemm (FP32 CUDA-core block matvec on the materialised T)",
+            "kernel": ("k_sgemm_mf (FP32 CUDA-core pair kernel: T tiles generated on the fly)"
+                       if mode == "matfree" else
+                       "k_sgemm (FP32 CUDA-core block matvec on the materialised T)"),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
             "avg_launch_ms": avg_launch_s * 1e3, "launches": launches}
 

@@ -502,8 +502,8 @@ namespace px {
 // straight into shared memory, as the hi / lo planes of the split (the layout a
 // 128-byte-swizzled TMA load would produce), and contracted with the X tiles (TMA) by
 // tcgen05.mma exactly as in k_tc_gemm; nothing of T is stored.
-//   warp 0        TMA producer: per K step the 64 atoms' positions (1 KB, bulk copy) and
-//                 the X hi / lo tiles (BN x 64)
+//   warp 0        TMA producer: the 64 atoms' positions of each K step (1 KB bulk copies,
+//                 running ahead) and the X hi / lo tiles (BN x 64)
 //   warp 1        MMA issuer (one elected thread, 4 x 3 MMAs per K step)
 //   warp 2        TMEM allocation
 //   warps 4-19    generators: warp w writes the 16-byte chunk c = w % 8 (atoms 8c .. 8c+7
@@ -518,9 +518,11 @@ namespace px {
 // reciprocal square root while r >= 4 R (erf(r/R) = 1 in FP32); closer pairs take
 // erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in a branch a warp enters only when one
 // of its lanes has such a pair (atoms are in Morton order, so most tiles have none).
-// Barriers per stage: pos_full (positions landed; the producer issues them only after the
-// MMA released the stage), full (X bytes + sixteen generator arrivals, each after a proxy
-// fence so the tensor core sees the generic-proxy stores), empty (MMA commit).
+// Barriers: per position slot (a 4-slot ring the producer keeps 3 K steps ahead) pos_full
+// (copy landed) and pos_empty (all generator warps read it); per stage full (X bytes +
+// sixteen generator arrivals, each after a proxy fence so the tensor core sees the
+// generic-proxy stores) and empty (MMA commit; the generators wait for it before writing
+// the stage's A tile again).  Close pairs use the branch-free erf of erf_as.
 // FP16 split: hi = RN(2^e T), lo = RN((2^e T - hi) 2^11), Y = D1 2^-(e+8) + D2 2^-(e+19)
 // (X' = 2^8 X).  BF16 split (e = 0): hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
 namespace {
@@ -528,6 +530,20 @@ namespace {
 constexpr int kMfGenWarps = 16;
 constexpr int kMfThreads = 128 + 32 * kMfGenWarps;
 constexpr int kMfPosBytes = TC_BK * 16;   // 64 float4 per K step
+constexpr int kMfPosSlots = 4;            // position ring: copies run 3 K steps ahead
+
+// erf for close pairs: Abramowitz & Stegun 7.1.26 (after Hastings), |error| <= 1.5e-7 for
+// x >= 0, below the 2^-22 resolution of the fp16 split for the x >= ~1 of distinct atoms;
+// branch-free: one reciprocal and one exponential on the SFU.
+__device__ __forceinline__ float erf_as(float x) {
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  float p = fmaf(1.061405429f, t, -1.453152027f);
+  p = fmaf(p, t, 1.421413741f);
+  p = fmaf(p, t, -0.284496736f);
+  p = fmaf(p, t, 0.254829592f);
+  p *= t;
+  return fmaf(-p, __expf(-x * x), 1.0f);
+}
 
 template <int F16, int TC_BN, int TC_STAGES>
 __global__ void __launch_bounds__(kMfThreads, 1)
@@ -540,25 +556,31 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float4* spos = reinterpret_cast<float4*>(base + TC_STAGES * STAGE);   // [TC_STAGES][64]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE + TC_STAGES * kMfPosBytes);
+  float4* spos = reinterpret_cast<float4*>(base + TC_STAGES * STAGE);   // [kMfPosSlots][64]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * STAGE + kMfPosSlots * kMfPosBytes);
   uint64_t* full = bars;                      // [TC_STAGES]: X bytes + generator warps
   uint64_t* empty = bars + TC_STAGES;         // [TC_STAGES]: MMA commit
-  uint64_t* pfull = bars + 2 * TC_STAGES;     // [TC_STAGES]: positions landed
-  uint64_t* accum = bars + 3 * TC_STAGES;     // [1]
+  uint64_t* pfull = bars + 2 * TC_STAGES;     // [kMfPosSlots]: positions landed
+  uint64_t* pempty = pfull + kMfPosSlots;     // [kMfPosSlots]: generator warps read them
+  uint64_t* accum = pempty + kMfPosSlots;     // [1]
   __shared__ uint32_t tmem_slot;
   __shared__ int cta_abort;
-  __shared__ int n_issued, n_consumed;
+  __shared__ int n_issued, n_consumed, p_issued, p_consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.y * TC_BM, c0 = blockIdx.x * TC_BN;
   const int nk = K / TC_BK;
 
   if (threadIdx.x == 0) {
+    p_issued = 0;
+    p_consumed = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1 + kMfGenWarps);
       mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < kMfPosSlots; ++s) {
       mbar_init(&pfull[s], 1);
+      mbar_init(&pempty[s], kMfGenWarps);
     }
     mbar_init(accum, 1);
     cta_abort = 0;
@@ -579,18 +601,29 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
   volatile int* abort_flag = &cta_abort;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer (positions, operand tiles)
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
-      unsigned char* st = base + s * STAGE;
-      mbar_expect_tx(&pfull[s], kMfPosBytes);
+    // ---------------- TMA producer: positions (a ring running ahead), operand tiles
+    auto issue_pos = [&](int kp) {   // positions of K step kp into slot kp % kMfPosSlots
+      const int ps = kp % kMfPosSlots;
+      if (kp >= kMfPosSlots &&
+          !mbar_wait(&pempty[ps], (uint32_t)((kp / kMfPosSlots) & 1) ^ 1u, err, abort_flag))
+        return false;
+      mbar_expect_tx(&pfull[ps], kMfPosBytes);
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              su32(spos + s * TC_BK)),
-          "l"(reinterpret_cast<uint64_t>(pos + (size_t)kt * TC_BK)), "r"(kMfPosBytes), "r"(su32(&pfull[s]))
+              su32(spos + ps * TC_BK)),
+          "l"(reinterpret_cast<uint64_t>(pos + (size_t)kp * TC_BK)), "r"(kMfPosBytes), "r"(su32(&pfull[ps]))
           : "memory");
+      p_issued = kp + 1;
+      return true;
+    };
+    bool ok = true;
+    for (int kp = 0; kp < kMfPosSlots - 1 && kp < nk && ok; ++kp) ok = issue_pos(kp);
+    for (int kt = 0; kt < nk && ok; ++kt) {
+      const int s = kt % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+      if (kt + kMfPosSlots - 1 < nk && !issue_pos(kt + kMfPosSlots - 1)) break;
+      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      unsigned char* st = base + s * STAGE;
       mbar_expect_tx(&full[s], 2 * B_TILE);
       const int kx = kt * TC_BK;
       tma_load_2d(st + 2 * A_TILE, &mXh, &full[s], kx, c0);
@@ -651,21 +684,29 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      // positions landed (issued after the MMA released this stage)
-      if (!mbar_wait(&pfull[s], ph, err, abort_flag)) break;
-      unsigned char* sth = base + s * STAGE;
-      unsigned char* stl = sth + A_TILE;
+      const int ps = kt % kMfPosSlots;
+      // this step's positions (copied ahead), then release their slot
+      if (!mbar_wait(&pfull[ps], (uint32_t)(kt / kMfPosSlots) & 1u, err, abort_flag)) break;
       // atoms 8c .. 8c+7 = pairs 4c .. 4c+3
       float2 kx[4], ky[4], kz[4], kw[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float4 a = spos[s * TC_BK + (4 * c + q) * 2];
-        const float4 b = spos[s * TC_BK + (4 * c + q) * 2 + 1];
+        const float4 a = spos[ps * TC_BK + (4 * c + q) * 2];
+        const float4 b = spos[ps * TC_BK + (4 * c + q) * 2 + 1];
         kx[q] = make_float2(a.x, a.y);
         ky[q] = make_float2(a.z, a.w);
         kz[q] = make_float2(b.x, b.y);
         kw[q] = make_float2(b.z, b.w);
       }
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
+        if (gw == 0) p_consumed = kt + 1;
+      }
+      // the A stage is free once the MMA of step kt - TC_STAGES completed
+      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+      unsigned char* sth = base + s * STAGE;
+      unsigned char* stl = sth + A_TILE;
       const int kb = kt * TC_BK + c * 8;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -691,7 +732,7 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
             const float wk = (e & 1) ? kw[e >> 1].y : kw[e >> 1].x;
             const float R2 = pw[u] + wk;
             if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pw[u]);
-            else if (rr < 16.0f * R2) t[e] = erff(rr * t[e] * rsqrtf(R2)) * t[e];
+            else if (rr < 16.0f * R2) t[e] = erf_as(rr * t[e] * rsqrtf(R2)) * t[e];
           }
         }
         uint32_t hw[4], lw[4];
@@ -759,12 +800,15 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
   if (cta_abort && threadIdx.x == 0) {
     // after a time-out: wait (bounded) for the copies that were issued but never consumed
     for (int kt = n_consumed; kt < n_issued; ++kt) {
-      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      long long t0 = clock64();
-      while (!mbar_try(&full[kt % TC_STAGES], ph) && clock64() - t0 < kWaitCycles) {
+      const long long t0 = clock64();
+      while (!mbar_try(&full[kt % TC_STAGES], (uint32_t)(kt / TC_STAGES) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
       }
-      t0 = clock64();
-      while (!mbar_try(&pfull[kt % TC_STAGES], ph) && clock64() - t0 < kWaitCycles) {
+    }
+    for (int kp = p_consumed; kp < p_issued; ++kp) {
+      const long long t0 = clock64();
+      while (!mbar_try(&pfull[kp % kMfPosSlots], (uint32_t)(kp / kMfPosSlots) & 1u) &&
+             clock64() - t0 < kWaitCycles) {
       }
     }
   }
@@ -805,7 +849,7 @@ template <int F16, int BN, int ST>
 cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& mXh,
                               const CUtensorMap& mXl, int np, int ncols, float* Y, int ldy,
                               float s1, float s2, int* err, cudaStream_t s) {
-  constexpr int smem = TcCfg<BN, ST>::SMEM + ST * kMfPosBytes;
+  constexpr int smem = TcCfg<BN, ST>::SMEM + kMfPosSlots * kMfPosBytes;
   static_assert(smem <= 227 * 1024, "shared memory per CTA");
   static bool attr = false;   // per process: every device uses the same attribute
   if (!attr) {
