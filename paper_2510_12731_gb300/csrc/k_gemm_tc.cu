@@ -519,7 +519,8 @@ namespace px {
 // erf(r/R)/r, or sqrt(2/pi)/R_q on the diagonal, in a branch a warp enters only when one
 // of its lanes has such a pair (atoms are in Morton order, so most tiles have none).
 // Barriers: per position slot (a 4-slot ring the producer keeps 3 K steps ahead) pos_full
-// (copy landed) and pos_empty (all generator warps read it); per stage full (X bytes +
+// (copy landed) and pos_empty (all generator warps finished the step that used it); per
+// stage full (X bytes +
 // sixteen generator arrivals, each after a proxy fence so the tensor core sees the
 // generic-proxy stores) and empty (MMA commit; the generators wait for it before writing
 // the stage's A tile again).  Close pairs use the branch-free erf of erf_as.
@@ -621,7 +622,6 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
     for (int kt = 0; kt < nk && ok; ++kt) {
       const int s = kt % TC_STAGES;
       const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      if (kt + kMfPosSlots - 1 < nk && !issue_pos(kt + kMfPosSlots - 1)) break;
       if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
       unsigned char* st = base + s * STAGE;
       mbar_expect_tx(&full[s], 2 * B_TILE);
@@ -629,6 +629,8 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
       tma_load_2d(st + 2 * A_TILE, &mXh, &full[s], kx, c0);
       tma_load_2d(st + 2 * A_TILE + B_TILE, &mXl, &full[s], kx, c0);
       n_issued = kt + 1;
+      // positions of step kt + 3 (their slot frees when the generators finish step kt - 1)
+      if (kt + kMfPosSlots - 1 < nk && !issue_pos(kt + kMfPosSlots - 1)) break;
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -698,11 +700,6 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
         kz[q] = make_float2(b.x, b.y);
         kw[q] = make_float2(b.z, b.w);
       }
-      __syncwarp();
-      if (lane == 0) {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
-        if (gw == 0) p_consumed = kt + 1;
-      }
       // the A stage is free once the MMA of step kt - TC_STAGES completed
       if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
       unsigned char* sth = base + s * STAGE;
@@ -759,9 +756,15 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
         *reinterpret_cast<uint4*>(stl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       // make the generic-proxy stores visible to the tensor core, then one arrival per warp
+      // on the stage (A tile written) and on the position slot (its values are consumed:
+      // releasing the slot any earlier let its next copy race the loads)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
+        if (gw == 0) p_consumed = kt + 1;
+      }
     }
     if (warp < 8) {
       // ---------------- epilogue: TMEM -> registers -> Y
