@@ -854,12 +854,20 @@ cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& 
                               float s1, float s2, int* err, cudaStream_t s) {
   constexpr int smem = TcCfg<BN, ST>::SMEM + kMfPosSlots * kMfPosBytes;
   static_assert(smem <= 227 * 1024, "shared memory per CTA");
-  static bool attr = false;   // per process: every device uses the same attribute
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    // the shared-memory opt-in, once per device (handles on several threads may race here)
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    attr = true;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.count(dev)) {
+      e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+      if (e != cudaSuccess) return e;
+      done.insert(dev);
+    }
   }
   dim3 grd(ncols / BN, np / TC_BM);
   k_tc_mf<F16, BN, ST><<<grd, kMfThreads, smem, s>>>(pos, wmax, mXh, mXl, Y, ldy, np, s1, s2, err);

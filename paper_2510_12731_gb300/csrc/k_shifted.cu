@@ -29,7 +29,10 @@
 #include "px_ff.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <type_traits>
+#include <utility>
 
 namespace px {
 
@@ -822,13 +825,21 @@ cudaError_t launch_sk_matvec(const float* Th, const float* Tl, int n, int np, in
   with_np(NP, [&](auto c) {
     constexpr int K = decltype(c)::value;
     const int shm = kMvStages * mv_stage_floats<K>() * (int)sizeof(float);
-    static bool attr_set[2][5] = {{false, false, false, false, false},
-                                  {false, false, false, false, false}};
-    const int t = trans ? 1 : 0;
-    if (!attr_set[t][K]) {
-      err = trans ? cudaFuncSetAttribute(k_sk_matvec_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm)
-                  : cudaFuncSetAttribute(k_sk_matvec<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
-      attr_set[t][K] = err == cudaSuccess;
+    // the shared-memory opt-in, once per device and kernel (handles on several threads
+    // may race here)
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return;
+    const int key = (trans ? 8 : 0) + K;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!done.count({dev, key})) {
+        err = trans ? cudaFuncSetAttribute(k_sk_matvec_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm)
+                    : cudaFuncSetAttribute(k_sk_matvec<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+        if (err == cudaSuccess) done.insert({dev, key});
+      }
     }
     if (err != cudaSuccess) return;
     if (trans) k_sk_matvec_t<K><<<pl.grid, 256, shm, s>>>(Th, Tl, np, pl.St, pl.seg_rows, vp, part);
