@@ -56,7 +56,7 @@ typedef enum {
   PX_ETIMEOUT = 4,   /* a bounded wait ran out */
   PX_ECUDA = 5,      /* a CUDA runtime call failed (message in px_last_error) */
   PX_EBUSY = 6,      /* the server queue is full */
-  PX_ENOTIMPL = 7,   /* valid request that this build does not support */
+  PX_ENOTIMPL = 7,   /* valid request that the library does not support */
   PX_ENOTFOUND = 8   /* unknown request id */
 } px_status;
 
