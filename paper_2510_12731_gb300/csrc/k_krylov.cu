@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(256) k_dots(KrylovArgs a, int j) {
         // issue every load of this row before any arithmetic
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          if (kk < nk) v[kk] = Vk[(size_t)kk * vstride + off];
+          if (kk < nk) v[kk] = __ldcs(Vk + (size_t)kk * vstride + off);   // streamed: keep W in L2
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
           if (kk < nk) TT::conj_mac(acc[kk], v[kk], w);
@@ -576,11 +576,11 @@ __global__ void __launch_bounds__(256) k_update(KrylovArgs a, int j, int pass, i
         for (; k + 8 <= kend; k += 8) {
           E v[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(k + q) * vstride + off];
+          for (int q = 0; q < 8; ++q) v[q] = __ldcs(V + (size_t)(k + q) * vstride + off);
 #pragma unroll
           for (int q = 0; q < 8; ++q) TT::mac(acc, v[q], shh[(k - k0 + q) * 32 + tx]);
         }
-        for (; k < kend; ++k) TT::mac(acc, V[(size_t)k * vstride + off], shh[(k - k0) * 32 + tx]);
+        for (; k < kend; ++k) TT::mac(acc, __ldcs(V + (size_t)k * vstride + off), shh[(k - k0) * 32 + tx]);
         const E w = TT::sub(w0, acc);
         W[off] = w;
         if (last && final_chunk) TT::norm_mac(nacc, w);

@@ -340,7 +340,7 @@ k_sk_dots(const float2* __restrict__ V, const float2* __restrict__ W, int n, int
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const float2 v = Vk[(size_t)i * NP + p];
+      const float2 v = __ldcs(Vk + (size_t)i * NP + p);   // streamed: W stays in L2
       const float2 w = W[(size_t)i * NP + p];
       ff::mac(ah[p], al[p], v.x, v.y, w.x, w.y);
     }
@@ -401,7 +401,7 @@ k_sk_update(const float2* __restrict__ V, int n, int j, const double* __restrict
   for (int k = k0; k < kend; ++k)
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const float2 vv = V[((size_t)k * n + i) * NP + p];
+      const float2 vv = __ldcs(V + ((size_t)k * n + i) * NP + p);
       const float2 c = sh[(k - k0) * NP + p];
       ff::mac(ah[p], al[p], vv.x, vv.y, c.x, c.y);
     }
