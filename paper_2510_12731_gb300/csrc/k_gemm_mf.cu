@@ -196,27 +196,27 @@ k_dgemm_mf(const double* __restrict__ pos /* [n][4]: x y z Rq^2 */, int n,
 // is evaluated in FP64 (tqq_d) and split into FP32 hi / lo parts in shared memory, the
 // contraction runs in double-FP32 (TwoProduct via FMA, TwoSum; ~48 bits per dot) on the
 // FP32 pipe, the result is rounded to FP64.  This replaces the FP64 contraction of
-// k_dgemm_mf (GB300's FP64 pipe is 1/64 of FP32); the FP64 pair evaluation is shared by
-// the 64 columns of the tile.  X comes as FP32 hi / lo planes [np][ldx].
-// Tiling as in k_gemm_ff.cu: 64 x 64 outputs per 256-thread block, 4 x 4 per thread, K
-// steps of 16 atoms; T symmetric, so the A tile's rows k are T[k][i0 .. i0+63].
+// k_dgemm_mf (GB300's FP64 pipe is 1/64 of FP32).  Output tiles of 32 rows x 256 columns
+// (256 threads, 8 x 4 outputs each), so each FP64 pair value serves 256 columns; K steps
+// of 16 atoms; T symmetric, so the A tile's rows k are T[k][i0 .. i0+31].  X comes as FP32
+// hi / lo planes [np][ldx].
 __global__ void __launch_bounds__(256)
 k_ffgemm_mf(const double* __restrict__ pos /* [n][4]: x y z Rq^2 */, int n,
-            const float* __restrict__ Xh, const float* __restrict__ Xl, int ldx,
+            const float* __restrict__ Xh, const float* __restrict__ Xl, int ldx, int ncols,
             double* __restrict__ Y, int ldy, int K) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BM = 32, BN = 256, BK = 16;
   __shared__ __align__(16) float Ah[BK][BM], Al[BK][BM], Bh[BK][BN], Bl[BK][BN];
   __shared__ double Pi[BM][4];
   __shared__ double Pk[BK][4];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;   // columns 4 tx .., rows 8 ty ..
   const int i0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
   if (tid < BM * 4) {
     const int ii = tid >> 2, q = tid & 3;
     Pi[ii][q] = (i0 + ii < n) ? pos[(size_t)(i0 + ii) * 4 + q] : (q == 3 ? 1.0 : 0.0);
   }
-  float s[4][4], c[4][4];
+  float s[8][4], c[8][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) s[r][q] = c[r][q] = 0.f;
   const int nk = K / BK;
@@ -226,59 +226,62 @@ k_ffgemm_mf(const double* __restrict__ pos /* [n][4]: x y z Rq^2 */, int n,
       const int kk = tid >> 2, q = tid & 3;
       Pk[kk][q] = (k0 + kk < n) ? pos[(size_t)(k0 + kk) * 4 + q] : (q == 3 ? 1.0 : 0.0);
     }
-    {
-      // operand: 16 x 64 floats per plane, one 16-byte chunk per thread and plane
-      const int kk = tid >> 4, cc = (tid & 15) * 4;
-      const size_t bx = (size_t)(k0 + kk) * ldx + c0 + cc;
-      *reinterpret_cast<float4*>(&Bh[kk][cc]) = *reinterpret_cast<const float4*>(Xh + bx);
-      *reinterpret_cast<float4*>(&Bl[kk][cc]) = *reinterpret_cast<const float4*>(Xl + bx);
-    }
-    __syncthreads();
-    {
-      const int kk = tid >> 4, ib = (tid & 15) * 4;
-      const int gk = k0 + kk;
+    // operand: 16 x 256 floats per plane, four 16-byte chunks per thread and plane
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int gi = i0 + ib + q;
-        const double v = (gi < n && gk < n) ? tqq_d(Pi[ib + q], Pk[kk], gi == gk) : 0.0;
-        const float h = __double2float_rn(v);
-        Ah[kk][ib + q] = h;
-        Al[kk][ib + q] = __double2float_rn(v - (double)h);
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int id = tid + 256 * u;
+      const int kk = id >> 6, cc = (id & 63) * 4;
+      const size_t bx = (size_t)(k0 + kk) * ldx + c0 + cc;
+      const bool in = c0 + cc < ncols;   // the last tile may be narrower (ncols % 128 == 0)
+      *reinterpret_cast<float4*>(&Bh[kk][cc]) =
+          in ? *reinterpret_cast<const float4*>(Xh + bx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(&Bl[kk][cc]) =
+          in ? *reinterpret_cast<const float4*>(Xl + bx) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-#pragma unroll 4
+    // T tile: 16 x 32 pair values in FP64, two per thread
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int id = tid + 256 * u;
+      const int kk = id >> 5, ii = id & 31;
+      const int gi = i0 + ii, gk = k0 + kk;
+      const double v = (gi < n && gk < n) ? tqq_d(Pi[ii], Pk[kk], gi == gk) : 0.0;
+      const float h = __double2float_rn(v);
+      Ah[kk][ii] = h;
+      Al[kk][ii] = __double2float_rn(v - (double)h);
+    }
+    __syncthreads();
+#pragma unroll 2
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 ah = *reinterpret_cast<const float4*>(&Ah[kk][ty * 4]);
-      const float4 al = *reinterpret_cast<const float4*>(&Al[kk][ty * 4]);
+      const float4 ah0 = *reinterpret_cast<const float4*>(&Ah[kk][ty * 8]);
+      const float4 ah1 = *reinterpret_cast<const float4*>(&Ah[kk][ty * 8 + 4]);
+      const float4 al0 = *reinterpret_cast<const float4*>(&Al[kk][ty * 8]);
+      const float4 al1 = *reinterpret_cast<const float4*>(&Al[kk][ty * 8 + 4]);
       const float4 bh = *reinterpret_cast<const float4*>(&Bh[kk][tx * 4]);
       const float4 bl = *reinterpret_cast<const float4*>(&Bl[kk][tx * 4]);
-      const float a_h[4] = {ah.x, ah.y, ah.z, ah.w}, a_l[4] = {al.x, al.y, al.z, al.w};
+      const float a_h[8] = {ah0.x, ah0.y, ah0.z, ah0.w, ah1.x, ah1.y, ah1.z, ah1.w};
+      const float a_l[8] = {al0.x, al0.y, al0.z, al0.w, al1.x, al1.y, al1.z, al1.w};
       const float b_h[4] = {bh.x, bh.y, bh.z, bh.w}, b_l[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) ff::mac(s[r][q], c[r][q], a_h[r], a_l[r], b_h[q], b_l[q]);
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
       for (int q = 0; q < 4; ++q) ff::renorm(s[r][q], c[r][q]);
     __syncthreads();
   }
+  if (c0 + tx * 4 >= ncols) return;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    double* yr = Y + (size_t)(i0 + ty * 4 + r) * ldy + c0 + tx * 4;
+  for (int r = 0; r < 8; ++r) {
+    double* yr = Y + (size_t)(i0 + ty * 8 + r) * ldy + c0 + tx * 4;
 #pragma unroll
     for (int q = 0; q < 4; ++q) yr[q] = (double)s[r][q] + (double)c[r][q];
   }
 }
 
-// Y = T X for wFQFmu with T generated tile by tile: 128 x 128 output tiles (32 atoms x 4
-// unknowns, charges-first order inside the tile), K steps of 4 atoms (16 unknowns).  The
-// 128 (row atom, K atom) pairs of a step are generated by threads 0..127, one 4 x 4 block
-// each, one stage ahead of the FMA loop; unknowns of atoms beyond N generate / load 0 and
-// are not stored.
 // ---------------------------------------------------------------- wFQFmu on the fly
 // The 4 x 4 block of the wFQFmu kernel (Sec. 2.2) of atoms a != b, unknowns (q, mu_x, mu_y,
 // mu_z) of each: blk[0][0] = T^qq, blk[0][1+l] = T^qmu_l = -T'(r; R_q,a mu,b) rhat_l,
@@ -614,8 +617,9 @@ cudaError_t launch_sgemm_mf(const float4* pos, int n, int np, const float* X, in
 
 cudaError_t launch_ffgemm_mf(const double* pos4, int n, int np, const float* Xh, const float* Xl,
                              int ldx, double* Y, int ldy, int ncols, cudaStream_t s, long long* nl) {
-  if (np % 64 || ncols % 64 || ldx % 4) return cudaErrorInvalidValue;
-  k_ffgemm_mf<<<dim3(ncols / 64, np / 64), 256, 0, s>>>(pos4, n, Xh, Xl, ldx, Y, ldy, np);
+  if (np % 32 || ncols % 4 || ldx % 4 || ldx < ncols) return cudaErrorInvalidValue;
+  k_ffgemm_mf<<<dim3((ncols + 255) / 256, np / 32), 256, 0, s>>>(pos4, n, Xh, Xl, ldx, ncols, Y, ldy,
+                                                                 np);
   ++*nl;
   return cudaGetLastError();
 }
