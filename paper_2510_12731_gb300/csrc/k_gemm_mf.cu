@@ -33,7 +33,7 @@ k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, i
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   __shared__ float4 Pi[BM];
-  __shared__ float4 Pk[2][BK];
+  __shared__ float4 Pk[3][BK];   // positions of K blocks kt, kt+1, kt+2 (one barrier per step)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
   const float* Bb = X + c0;
@@ -55,7 +55,7 @@ k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, i
   // K offsets kk = tid / 128 + 2 q
   const int gi_local = tid & (BM - 1);
   const int kk_base = tid >> 7;
-  auto gen = [&](int st, int k0) {
+  auto gen = [&](int st, int ps, int k0) {
     const float4 pi = Pi[gi_local];
     const int gi = i0 + gi_local;
 #pragma unroll
@@ -63,7 +63,7 @@ k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, i
       const int kk = kk_base + 2 * q;
       const int gk = k0 + kk;
       float v = 0.f;
-      if (gi < n && gk < n) v = tqq_f(pi, Pk[st][kk], gi == gk);
+      if (gi < n && gk < n) v = tqq_f(pi, Pk[ps][kk], gi == gk);
       As[st][kk][gi_local] = v;
     }
   };
@@ -78,15 +78,18 @@ k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, i
   load_pk(0, 0);
   load_x(0, 0);
   __syncthreads();
-  gen(0, 0);
+  gen(0, 0, 0);
   if (nk > 1) load_pk(1, BK);
   cp_async_wait_all();
   __syncthreads();
   for (int kt = 0; kt < nk; ++kt) {
     const int st = kt & 1, nx = st ^ 1;
+    // slot (kt + 2) % 3 was last read by the generation of block kt - 1, before the
+    // previous barrier
+    if (kt + 2 < nk) load_pk((kt + 2) % 3, (kt + 2) * BK);
     if (kt + 1 < nk) {
       load_x(nx, (kt + 1) * BK);
-      gen(nx, (kt + 1) * BK);
+      gen(nx, (kt + 1) % 3, (kt + 1) * BK);
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -102,9 +105,6 @@ k_sgemm_mf(const float4* __restrict__ pos, int n, const float* __restrict__ X, i
         for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
     }
     cp_async_wait_all();
-    __syncthreads();
-    // positions of the K block after next go into the stage just consumed
-    if (kt + 2 < nk) load_pk(st, (kt + 2) * BK);
     __syncthreads();
   }
 #pragma unroll

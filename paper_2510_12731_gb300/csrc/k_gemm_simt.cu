@@ -25,13 +25,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // FP32: BM = BN = 128, BK = 16, 256 threads, 8 x 8 outputs per thread arranged as
-// rows {ty*4 + r, 64 + ty*4 + r} and columns {tx*4 + c, 64 + tx*4 + c}.
+// rows {ty*4 + r, 64 + ty*4 + r} and columns {tx*4 + c, 64 + tx*4 + c}.  A 3-stage
+// cp.async ring (48 KB): the copy of K block kt + 2 goes into the stage consumed at step
+// kt - 1, so one barrier per K step suffices.
 __global__ void __launch_bounds__(256, 2)
 k_sgemm(const float* __restrict__ T, int ldt, const float* __restrict__ X, int ldx,
         float* __restrict__ Y, int ldy, int K) {
-  constexpr int BM = 128, BN = 128, BK = 16;
-  __shared__ __align__(16) float As[2][BK][BM];
-  __shared__ __align__(16) float Bs[2][BK][BN];
+  constexpr int BM = 128, BN = 128, BK = 16, ST = 3;
+  __shared__ __align__(16) float As[ST][BK][BM];
+  __shared__ __align__(16) float Bs[ST][BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
   const float* Ab = T + i0;
@@ -56,15 +58,13 @@ k_sgemm(const float* __restrict__ T, int ldt, const float* __restrict__ X, int l
 
   const int nk = K / BK;
   load(0, 0);
+  if (nk > 1) load(1, BK);
   for (int kt = 0; kt < nk; ++kt) {
-    if (kt + 1 < nk) {
-      load((kt + 1) & 1, (kt + 1) * BK);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const int st = kt & 1;
+    if (kt + 1 < nk) cp_async_wait<1>();   // block kt landed, kt + 1 may be in flight
+    else cp_async_wait<0>();
+    __syncthreads();                       // ... for every thread; stage (kt + 2) % 3 is free
+    if (kt + 2 < nk) load((kt + 2) % ST, (kt + 2) * BK);
+    const int st = kt % ST;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float4 a0 = *reinterpret_cast<const float4*>(&As[st][kk][ty * 4]);
@@ -78,7 +78,6 @@ k_sgemm(const float* __restrict__ T, int ldt, const float* __restrict__ X, int l
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
