@@ -884,6 +884,20 @@ cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, i
   return cudaGetLastError();
 }
 
+namespace {
+// tile-width cache of the pair kernel: (device, np, ncols, f16) -> 256 or 128
+std::mutex g_mf_mu;
+std::map<std::tuple<int, int, int, int>, int> g_mf_tune;
+}  // namespace
+
+int tc_mf_tuned_width(int np, int ncols, bool f16) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lock(g_mf_mu);
+  auto it = g_mf_tune.find(std::make_tuple(dev, np, ncols, f16 ? 1 : 0));
+  return it == g_mf_tune.end() ? -1 : it->second;
+}
+
 cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
                          int* err, cudaStream_t s, long long* nl) {
@@ -893,18 +907,56 @@ cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* 
   if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
        reinterpret_cast<uintptr_t>(pos)) & 15)
     return cudaErrorMisalignedAddress;
-  const int bn = ncols % 256 == 0 ? 256 : 128;
-  CUtensorMap mXh, mXl;
-  if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
-    return cudaErrorInvalidValue;
   const float s1 = std::ldexp(1.0f, -(scale_exp + 8)), s2 = std::ldexp(1.0f, -(scale_exp + 19));
-  cudaError_t e;
-  if (f16)
-    e = bn == 256 ? launch_mf_variant<1, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
-                  : launch_mf_variant<1, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
-  else
-    e = bn == 256 ? launch_mf_variant<0, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
-                  : launch_mf_variant<0, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
+  auto run = [&](int bn) -> cudaError_t {
+    CUtensorMap mXh, mXl;
+    if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
+      return cudaErrorInvalidValue;
+    if (f16)
+      return bn == 256 ? launch_mf_variant<1, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                       : launch_mf_variant<1, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+    return bn == 256 ? launch_mf_variant<0, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
+                     : launch_mf_variant<0, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
+  };
+  // tile width: 256-column tiles share each generated T tile between more columns, 128-column
+  // tiles give more CTAs (fewer idle SMs in the last wave); the first call of a shape outside
+  // a stream capture times both (each writes the same Y) and keeps the faster
+  int bn = tc_mf_tuned_width(np, ncols, f16);
+  cudaError_t e = cudaSuccess;
+  if (bn < 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (ncols % 256 != 0 || cs != cudaStreamCaptureStatusNone) {
+      bn = ncols % 256 == 0 ? 256 : 128;
+    } else {
+      cudaEvent_t ev[4];
+      for (auto& x : ev) {
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return e;
+      }
+      const int widths[2] = {256, 128};
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        e = run(widths[v]);   // warm
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * v], s);
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run(widths[v]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * v + 1], s);
+        *nl += 3;
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+      float t[2] = {0.f, 0.f};
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) e = cudaEventElapsedTime(&t[v], ev[2 * v], ev[2 * v + 1]);
+      for (auto& x : ev) cudaEventDestroy(x);
+      if (e != cudaSuccess) return e;
+      bn = t[1] < t[0] ? 128 : 256;
+      int dev = 0;
+      e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      std::lock_guard<std::mutex> lock(g_mf_mu);
+      g_mf_tune[std::make_tuple(dev, np, ncols, f16 ? 1 : 0)] = bn;
+    }
+  }
+  e = run(bn);
   ++*nl;
   return e;
 }

@@ -1179,6 +1179,12 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
                                 &nl, -1, nullptr));
         }
+        if (tc && d.matfree && px::tc_mf_tuned_width(np, ldxa, tc_f16) < 0) {
+          // likewise the pair kernel's tile width
+          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
+          CU(px::launch_tc_mf(d.pos4tc, np, d.tc_wmax, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
+                              d.op_scale_exp, h->d_err, s, &nl));
+        }
         uint32_t wmax_bits = 0;
         std::memcpy(&wmax_bits, &d.tc_wmax, sizeof(wmax_bits));
         const std::vector<uint64_t> key = {

@@ -183,11 +183,15 @@ int tc_tuned_variant(int np, int ncols, bool f16);
 // scaled, padded positions of launch_tc_mf_positions (wmax: their largest R_q^2) into shared
 // memory as split planes and contracted with the split operand (Xh / Xl as for
 // launch_tc_gemm).  f16: the tiles hold 2^scale_exp T (2^scale_exp max|T| <= 2^14; bf16:
-// scale_exp = 0); Y is returned unscaled.  128 x 256 tiles when ncols % 256 == 0, else
-// 128 x 128.  *err as for launch_tc_gemm.
+// scale_exp = 0); Y is returned unscaled.  128 x 256 or 128 x 128 tiles (only 128 when
+// ncols % 256 != 0; else the faster of the two for the shape, timed on its first call
+// outside a stream capture).  *err as for launch_tc_gemm.
 cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
                          int* err, cudaStream_t s, long long* nl);
+// The pair kernel's tile width chosen for a shape on the current device (256 or 128), or -1
+// before the first uncaptured call of that shape (which times both widths).
+int tc_mf_tuned_width(int np, int ncols, bool f16);
 // Its positions: pos (bohr) and Rq in internal order -> out (np / 2 atom pairs of 8 floats,
 // [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1], w = R_q^2) scaled by 2^-scale_exp (w by 2^-2 scale_exp),
 // atoms n .. np-1 distinct far-away dummies.
