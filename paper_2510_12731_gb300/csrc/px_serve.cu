@@ -127,8 +127,10 @@ struct px_server {
 
 namespace {
 
-// Largest block of frequencies one merged solve takes.
+// Largest block one merged solve takes: frequencies, and complex per-atom results
+// (frequencies x directions x unknowns) held on the host while the solve runs.
 constexpr int kMergeMaxFreq = 512;
+constexpr size_t kMergeMaxEntries = size_t(1) << 26;
 
 // Queued requests that can join r's solve as extra columns: the same structure, operator
 // mode and model (so the same T, CSR and shifts' form), the same field directions and E0
@@ -143,7 +145,8 @@ void gather_group(px_server* s, Req* r, const Slot* pick) {
     Req* q = *it;
     const bool same = q != r && q->key == r->key && q->mode == r->mode && q->model == r->model &&
                       q->P == r->P && q->e0 == r->e0 && q->ntypes == r->ntypes &&
-                      q->pol == r->pol && F + q->F <= kMergeMaxFreq;
+                      q->pol == r->pol && F + q->F <= kMergeMaxFreq &&
+                      (size_t)(F + q->F) * r->P * (r->model == PX_WFQ ? 1 : 4) * r->N <= kMergeMaxEntries;
     if (!same) {
       ++it;
       continue;
