@@ -196,7 +196,7 @@ class ClockSampler:
 # helper (tensor-core file), or the span from the file's namespace to the next kernel
 # (the FP32 GEMM shares its file with the FP64 kernels).  Code outside it does not change
 # what the profiled kernel executes.
-DEVICE_PART_END = {"k_gemm_tc.cu": b"PFN_cuTensorMapEncodeTiled_v12000 encode_fn()"}
+DEVICE_PART_END = {"k_gemm_tc.cu": b"// Xt_hi[c][k], Xt_lo[c][k] (K-major) from X[k][c]"}
 DEVICE_PART_SPAN = {"k_gemm_simt.cu": (b"namespace px {", b"// FP64: BM = BN = 64, BK = 16"),
                     "k_shifted.cu": (b"// ---------------------------------------------------------------- matvec",
                                      b"// U[i][p] = sum over segments")}

@@ -16,7 +16,6 @@ namespace px {
 namespace {
 
 constexpr double kSqrt2OverPiD = 0.7978845608028654;
-using radial::kSqrt2OverPiF;
 using radial::tqq_f;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -283,60 +282,6 @@ k_ffgemm_mf(const double* __restrict__ pos /* [n][4]: x y z Rq^2 */, int n,
 }
 
 // ---------------------------------------------------------------- wFQFmu on the fly
-// The 4 x 4 block of the wFQFmu kernel (Sec. 2.2) of atoms a != b, unknowns (q, mu_x, mu_y,
-// mu_z) of each: blk[0][0] = T^qq, blk[0][1+l] = T^qmu_l = -T'(r; R_q,a mu,b) rhat_l,
-// blk[1+k][0] = T^muq_k = +T'(r; R_mu,a q,b) rhat_k,
-// blk[1+k][1+l] = T^mumu_kl = -[T'' rhat_k rhat_l + (T'/r)(delta_kl - rhat_k rhat_l)],
-// rhat = (r_a - r_b)/r, pair widths sqrt(R_a^2 + R_b^2) of the two densities involved.
-// With T' rhat = (T'/r) (r_a - r_b), only G'/r and G'' enter.  Equal charge and dipole
-// widths (the usual case) need one radial evaluation instead of four.
-__device__ __forceinline__ void pair_block_f(float4 pa, float rma2, float4 pb, float rmb2,
-                                             float blk[4][4]) {
-  const float d[3] = {pa.x - pb.x, pa.y - pb.y, pa.z - pb.z};
-  const float r2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
-  const float r = sqrtf(r2), ir = 1.0f / r;
-  float Gqq, t1, t2, g;
-  float G1qm, G1mq, G1mm, G2mm;
-  radial::eval_f(r, sqrtf(pa.w + pb.w), Gqq, t1, t2, g);
-  if (pa.w == rma2 && pb.w == rmb2) {
-    G1qm = G1mq = G1mm = t1;
-    G2mm = t2;
-  } else {
-    float u0, u2;
-    radial::eval_f(r, sqrtf(pa.w + rmb2), u0, G1qm, u2, g);
-    radial::eval_f(r, sqrtf(rma2 + pb.w), u0, G1mq, u2, g);
-    radial::eval_f(r, sqrtf(rma2 + rmb2), u0, G1mm, G2mm, g);
-  }
-  blk[0][0] = Gqq;
-  const float rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
-#pragma unroll
-  for (int l = 0; l < 3; ++l) blk[0][1 + l] = -G1qm * d[l];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    blk[1 + k][0] = G1mq * d[k];
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const float rr = rh[k] * rh[l];
-      blk[1 + k][1 + l] = -(G2mm * rr + G1mm * ((k == l ? 1.0f : 0.0f) - rr));
-    }
-  }
-}
-
-// Diagonal 4 x 4 block of atom a: T^qq self limit, zero charge-dipole coupling, T^mumu = 0 or
-// the Gaussian self term 4/(3 sqrt(pi) R^3) I with R = sqrt(2) R_mu (mu_self_term).
-__device__ __forceinline__ void self_block_f(float rq2, float rm2, int mu_self, float blk[4][4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int l = 0; l < 4; ++l) blk[k][l] = 0.f;
-  blk[0][0] = kSqrt2OverPiF * rsqrtf(rq2);
-  if (mu_self) {
-    const float R2 = 2.0f * rm2;   // R = sqrt(2) R_mu
-    const float v = 4.0f / (3.0f * 1.7724538509055159f) * rsqrtf(R2) / R2;
-    blk[1][1] = blk[2][2] = blk[3][3] = v;
-  }
-}
-
 // Standard (charges first) row of unknown u of a tile whose atoms start at a0 and whose
 // first `na` unknowns are those atoms' charges, the next 3 na their dipole components.
 __device__ __forceinline__ int std_row(int N, int a0, int na, int u, int* atom) {
@@ -395,9 +340,9 @@ k_sgemm_mf4(const float4* __restrict__ pos, const float* __restrict__ rm2, int N
 #pragma unroll
           for (int l = 0; l < 4; ++l) blk[k][l] = 0.f;
       } else if (a == b) {
-        self_block_f(Pa[al].w, Ra[al], mu_self, blk);
+        radial::self_block_f(Pa[al].w, Ra[al], mu_self, blk);
       } else {
-        pair_block_f(Pa[al], Ra[al], Pb[st][bl], Rb[st][bl], blk);
+        radial::pair_block_f(Pa[al], Ra[al], Pb[st][bl], Rb[st][bl], blk);
       }
       // As[st][K unknown][row unknown]
       As[st][bl][al] = blk[0][0];

@@ -292,12 +292,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUten
 
 // Xt_hi[c][k], Xt_lo[c][k] (K-major) from X[k][c] (FP32, row-major); 32 x 32 tiles.
 // BF16: hi = RN(x), lo = RN(x - hi).  FP16: x' = 2^8 x, hi = RN(x'), lo = RN((x' - hi) 2^11).
-template <int F16>
-__global__ void k_split_xt(const float* __restrict__ X, int ldx, int K,
+// PERM (wFQFmu, N atoms): K index k is atom-blocked, groups of 16 atoms holding their 16
+// charges then their 48 dipole components (atom by atom), read from the charges-first row
+// of X; the unknowns of atoms beyond N are 0.
+template <int F16, int PERM>
+__global__ void k_split_xt(const float* __restrict__ X, int ldx, int K, int N,
                            uint16_t* __restrict__ Xh, uint16_t* __restrict__ Xl) {
   __shared__ float tile[32][33];
   const int k0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = X[(size_t)(k0 + r) * ldx + c0 + threadIdx.x];
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int row = k0 + r;
+    bool real = true;
+    if (PERM) {
+      const int g = row >> 6, w = row & 63, b0 = 16 * g;
+      const int atom = w < 16 ? b0 + w : b0 + (w - 16) / 3;
+      real = atom < N;
+      row = w < 16 ? atom : N + 3 * b0 + (w - 16);
+    }
+    tile[r][threadIdx.x] = real ? X[(size_t)row * ldx + c0 + threadIdx.x] : 0.0f;
+  }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const float v = tile[threadIdx.x][r];
@@ -351,8 +364,19 @@ cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t
                             uint16_t* Xl, bool f16, cudaStream_t s, long long* nl) {
   if (np % 32 || ncols % 32) return cudaErrorInvalidValue;
   dim3 grd(np / 32, ncols / 32), blk(32, 8);
-  if (f16) k_split_xt<1><<<grd, blk, 0, s>>>(X, ldx, np, Xh, Xl);
-  else k_split_xt<0><<<grd, blk, 0, s>>>(X, ldx, np, Xh, Xl);
+  if (f16) k_split_xt<1, 0><<<grd, blk, 0, s>>>(X, ldx, np, 0, Xh, Xl);
+  else k_split_xt<0, 0><<<grd, blk, 0, s>>>(X, ldx, np, 0, Xh, Xl);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_xt_mu(const float* X, int ldx, int np, int ncols, int N, uint16_t* Xh,
+                               uint16_t* Xl, bool f16, cudaStream_t s, long long* nl) {
+  // every K index maps to a row below 4 N <= np
+  if (np % 64 || ncols % 32 || N < 1 || 4 * (long long)N > np) return cudaErrorInvalidValue;
+  dim3 grd(np / 32, ncols / 32), blk(32, 8);
+  if (f16) k_split_xt<1, 1><<<grd, blk, 0, s>>>(X, ldx, np, N, Xh, Xl);
+  else k_split_xt<0, 1><<<grd, blk, 0, s>>>(X, ldx, np, N, Xh, Xl);
   ++*nl;
   return cudaGetLastError();
 }
@@ -526,6 +550,16 @@ namespace px {
 // the stage's A tile again).  Close pairs use the branch-free erf of erf_as.
 // FP16 split: hi = RN(2^e T), lo = RN((2^e T - hi) 2^11), Y = D1 2^-(e+8) + D2 2^-(e+19)
 // (X' = 2^8 X).  BF16 split (e = 0): hi = RN(T), lo = RN(T - hi), one accumulator, Y = D.
+// wFQFmu (MU = 1, Sec. 2.2): the unknowns are reordered atom-blocked, so that a 128-row tile
+// holds those of 32 atoms (their 32 charges, then their dipoles x, y, z atom by atom) and a
+// 64-unknown K step those of 16 atoms in the same order (launch_split_xt_mu permutes X
+// alike; the epilogue writes each row back to its place in the charges-first vector).
+// Generator thread (al, bl) evaluates the 4 x 4 block of T^qq / T^qmu / T^muq / T^mumu of
+// row atom al and column atom bl of the step (512 blocks, one per generator thread), in
+// FP32 from unscaled positions: the closed far-field forms (1/r, d/r^3, (I - 3 rhat rhat)/r^3)
+// when every pair of the warp has r >= 5 R for all four widths (erf = 1 and the Gaussian
+// terms below 1e-9 there), else the full radial functions; the block is multiplied by 2^e
+// (tscale) before the split, and blocks with an atom beyond N are zero.
 namespace {
 
 constexpr int kMfGenWarps = 16;
@@ -546,9 +580,9 @@ __device__ __forceinline__ float erf_as(float x) {
   return fmaf(-p, __expf(-x * x), 1.0f);
 }
 
-template <int F16, int TC_BN, int TC_STAGES>
+template <int F16, int TC_BN, int TC_STAGES, int MU>
 __global__ void __launch_bounds__(kMfThreads, 1)
-k_tc_mf(const float4* __restrict__ pos, float wmax,
+k_tc_mf(const float4* __restrict__ pos, float wmax, float tscale, int N, int mu_self,
         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
         float* __restrict__ Y, int ldy, int K, float s1, float s2, int* err) {
   using Cfg = TcCfg<TC_BN, TC_STAGES>;
@@ -603,16 +637,19 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer: positions (a ring running ahead), operand tiles
+    // one K step's positions: 64 atoms x 16 bytes (wFQ), 16 atoms x 32 bytes (wFQFmu)
+    constexpr int kStepPos = MU ? 32 : TC_BK;   // float4 per K step
+    constexpr int kStepBytes = kStepPos * 16;
     auto issue_pos = [&](int kp) {   // positions of K step kp into slot kp % kMfPosSlots
       const int ps = kp % kMfPosSlots;
       if (kp >= kMfPosSlots &&
           !mbar_wait(&pempty[ps], (uint32_t)((kp / kMfPosSlots) & 1) ^ 1u, err, abort_flag))
         return false;
-      mbar_expect_tx(&pfull[ps], kMfPosBytes);
+      mbar_expect_tx(&pfull[ps], kStepBytes);
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
               su32(spos + ps * TC_BK)),
-          "l"(reinterpret_cast<uint64_t>(pos + (size_t)kp * TC_BK)), "r"(kMfPosBytes), "r"(su32(&pfull[ps]))
+          "l"(reinterpret_cast<uint64_t>(pos + (size_t)kp * kStepPos)), "r"(kStepBytes), "r"(su32(&pfull[ps]))
           : "memory");
       p_issued = kp + 1;
       return true;
@@ -661,109 +698,187 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
     }
     mma_commit(accum);
   } else if (warp >= 4) {
-    // ---------------- generators: T tiles in the swizzled K-major layout
-    // Positions arrive as atom pairs [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1] (w = R_q^2), so that the
-    // differences and r^2 of two atoms run as packed FP32x2 instructions.
-    const int gw = warp - 4;                     // 0 .. 15
-    const int c = gw & 7;                        // 16-byte chunk (atoms 8c .. 8c+7 of the step)
-    const int r_lo = (gw >> 3) * 64 + lane;      // rows r_lo and r_lo + 32
-    const float* posf = reinterpret_cast<const float*>(pos);
-    float2 px[2], py[2], pz[2];
-    float pw[2], thr[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = i0 + r_lo + 32 * u;
-      const float* pp = posf + (size_t)(i >> 1) * 8 + (i & 1);
-      const float x = -__ldg(pp), y = -__ldg(pp + 2), z = -__ldg(pp + 4);
-      px[u] = make_float2(x, x);
-      py[u] = make_float2(y, y);
-      pz[u] = make_float2(z, z);
-      pw[u] = __ldg(pp + 6);
-      thr[u] = 16.0f * (pw[u] + wmax);           // r^2 below this: a close pair is possible
-    }
-    const uint32_t sw = (uint32_t)((c ^ (lane & 7)) << 4);   // row & 7 == lane & 7
-    const float2 k2048 = make_float2(2048.0f, 2048.0f), km1 = make_float2(-1.0f, -1.0f);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
-      const int ps = kt % kMfPosSlots;
-      // this step's positions (copied ahead), then release their slot
-      if (!mbar_wait(&pfull[ps], (uint32_t)(kt / kMfPosSlots) & 1u, err, abort_flag)) break;
-      // atoms 8c .. 8c+7 = pairs 4c .. 4c+3
-      float2 kx[4], ky[4], kz[4], kw[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 a = spos[ps * TC_BK + (4 * c + q) * 2];
-        const float4 b = spos[ps * TC_BK + (4 * c + q) * 2 + 1];
-        kx[q] = make_float2(a.x, a.y);
-        ky[q] = make_float2(a.z, a.w);
-        kz[q] = make_float2(b.x, b.y);
-        kw[q] = make_float2(b.z, b.w);
-      }
-      // the A stage is free once the MMA of step kt - TC_STAGES completed
-      if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
-      unsigned char* sth = base + s * STAGE;
-      unsigned char* stl = sth + A_TILE;
-      const int kb = kt * TC_BK + c * 8;
-#pragma unroll
+    if constexpr (MU == 0) {
+      // ---------------- generators: T tiles in the swizzled K-major layout
+      // Positions arrive as atom pairs [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1] (w = R_q^2), so that the
+      // differences and r^2 of two atoms run as packed FP32x2 instructions.
+      const int gw = warp - 4;                     // 0 .. 15
+      const int c = gw & 7;                        // 16-byte chunk (atoms 8c .. 8c+7 of the step)
+      const int r_lo = (gw >> 3) * 64 + lane;      // rows r_lo and r_lo + 32
+      const float* posf = reinterpret_cast<const float*>(pos);
+      float2 px[2], py[2], pz[2];
+      float pw[2], thr[2];
+  #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int r = r_lo + 32 * u;
-        float2 r2[4];
-        float t[8];
-        float mn = 3.0e38f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          // (x_i - x_k) for two atoms k: the pair holds -x_k
-          const float2 dx = __fadd2_rn(px[u], kx[q]), dy = __fadd2_rn(py[u], ky[q]),
-                       dz = __fadd2_rn(pz[u], kz[q]);
-          r2[q] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-          t[2 * q] = rsqrtf(r2[q].x);
-          t[2 * q + 1] = rsqrtf(r2[q].y);
-          mn = fminf(mn, fminf(r2[q].x, r2[q].y));
-        }
-        if (__any_sync(0xffffffffu, mn < thr[u])) {
-          const int i = i0 + r;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float rr = (e & 1) ? r2[e >> 1].y : r2[e >> 1].x;
-            const float wk = (e & 1) ? kw[e >> 1].y : kw[e >> 1].x;
-            const float R2 = pw[u] + wk;
-            if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pw[u]);
-            else if (rr < 16.0f * R2) t[e] = erf_as(rr * t[e] * rsqrtf(R2)) * t[e];
-          }
-        }
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 tv = make_float2(t[2 * q], t[2 * q + 1]);
-          if (F16) {
-            const __half2 h = __float22half2_rn(tv);
-            const float2 hf = __half22float2(h);
-            // lo = RN((t - hi) 2^11)
-            const __half2 l = __float22half2_rn(__fmul2_rn(__ffma2_rn(hf, km1, tv), k2048));
-            hw[q] = *reinterpret_cast<const uint32_t*>(&h);
-            lw[q] = *reinterpret_cast<const uint32_t*>(&l);
-          } else {
-            const __nv_bfloat162 h = __float22bfloat162_rn(tv);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(hf, km1, tv));
-            hw[q] = *reinterpret_cast<const uint32_t*>(&h);
-            lw[q] = *reinterpret_cast<const uint32_t*>(&l);
-          }
-        }
-        const uint32_t off = (uint32_t)r * 128u + sw;
-        *reinterpret_cast<uint4*>(sth + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(stl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        const int i = i0 + r_lo + 32 * u;
+        const float* pp = posf + (size_t)(i >> 1) * 8 + (i & 1);
+        const float x = -__ldg(pp), y = -__ldg(pp + 2), z = -__ldg(pp + 4);
+        px[u] = make_float2(x, x);
+        py[u] = make_float2(y, y);
+        pz[u] = make_float2(z, z);
+        pw[u] = __ldg(pp + 6);
+        thr[u] = 16.0f * (pw[u] + wmax);           // r^2 below this: a close pair is possible
       }
-      // make the generic-proxy stores visible to the tensor core, then one arrival per warp
-      // on the stage (A tile written) and on the position slot (its values are consumed:
-      // releasing the slot any earlier let its next copy race the loads)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
-        if (gw == 0) p_consumed = kt + 1;
+      const uint32_t sw = (uint32_t)((c ^ (lane & 7)) << 4);   // row & 7 == lane & 7
+      const float2 k2048 = make_float2(2048.0f, 2048.0f), km1 = make_float2(-1.0f, -1.0f);
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+        const int ps = kt % kMfPosSlots;
+        // this step's positions (copied ahead), then release their slot
+        if (!mbar_wait(&pfull[ps], (uint32_t)(kt / kMfPosSlots) & 1u, err, abort_flag)) break;
+        // atoms 8c .. 8c+7 = pairs 4c .. 4c+3
+        float2 kx[4], ky[4], kz[4], kw[4];
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 a = spos[ps * TC_BK + (4 * c + q) * 2];
+          const float4 b = spos[ps * TC_BK + (4 * c + q) * 2 + 1];
+          kx[q] = make_float2(a.x, a.y);
+          ky[q] = make_float2(a.z, a.w);
+          kz[q] = make_float2(b.x, b.y);
+          kw[q] = make_float2(b.z, b.w);
+        }
+        // the A stage is free once the MMA of step kt - TC_STAGES completed
+        if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+        unsigned char* sth = base + s * STAGE;
+        unsigned char* stl = sth + A_TILE;
+        const int kb = kt * TC_BK + c * 8;
+  #pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int r = r_lo + 32 * u;
+          float2 r2[4];
+          float t[8];
+          float mn = 3.0e38f;
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            // (x_i - x_k) for two atoms k: the pair holds -x_k
+            const float2 dx = __fadd2_rn(px[u], kx[q]), dy = __fadd2_rn(py[u], ky[q]),
+                         dz = __fadd2_rn(pz[u], kz[q]);
+            r2[q] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            t[2 * q] = rsqrtf(r2[q].x);
+            t[2 * q + 1] = rsqrtf(r2[q].y);
+            mn = fminf(mn, fminf(r2[q].x, r2[q].y));
+          }
+          if (__any_sync(0xffffffffu, mn < thr[u])) {
+            const int i = i0 + r;
+  #pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float rr = (e & 1) ? r2[e >> 1].y : r2[e >> 1].x;
+              const float wk = (e & 1) ? kw[e >> 1].y : kw[e >> 1].x;
+              const float R2 = pw[u] + wk;
+              if (i == kb + e) t[e] = radial::kSqrt2OverPiF * rsqrtf(pw[u]);
+              else if (rr < 16.0f * R2) t[e] = erf_as(rr * t[e] * rsqrtf(R2)) * t[e];
+            }
+          }
+          uint32_t hw[4], lw[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 tv = make_float2(t[2 * q], t[2 * q + 1]);
+            if (F16) {
+              const __half2 h = __float22half2_rn(tv);
+              const float2 hf = __half22float2(h);
+              // lo = RN((t - hi) 2^11)
+              const __half2 l = __float22half2_rn(__fmul2_rn(__ffma2_rn(hf, km1, tv), k2048));
+              hw[q] = *reinterpret_cast<const uint32_t*>(&h);
+              lw[q] = *reinterpret_cast<const uint32_t*>(&l);
+            } else {
+              const __nv_bfloat162 h = __float22bfloat162_rn(tv);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(hf, km1, tv));
+              hw[q] = *reinterpret_cast<const uint32_t*>(&h);
+              lw[q] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+          }
+          const uint32_t off = (uint32_t)r * 128u + sw;
+          *reinterpret_cast<uint4*>(sth + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(stl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        // make the generic-proxy stores visible to the tensor core, then one arrival per warp
+        // on the stage (A tile written) and on the position slot (its values are consumed:
+        // releasing the slot any earlier let its next copy race the loads)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
+          if (gw == 0) p_consumed = kt + 1;
+        }
+      }
+    } else {
+      // ---------------- wFQFmu generators: 4 x 4 blocks in the swizzled K-major layout
+      const int gw = warp - 4;                       // 0 .. 15
+      const int al = 8 * (gw & 3) + (lane & 7);      // row atom of the tile, 0 .. 31
+      const int bl = 4 * (gw >> 2) + (lane >> 3);    // column atom of the K step, 0 .. 15
+      const int a = blockIdx.y * 32 + al;
+      const float4 pa = __ldg(pos + 2 * a);
+      const float rma2 = __ldg(pos + 2 * a + 1).x;
+      const float wa = fmaxf(pa.w, rma2);
+      // rows: the charge of atom al, then its dipole components; K: likewise for atom bl
+      const int rows[4] = {al, 32 + 3 * al, 33 + 3 * al, 34 + 3 * al};
+      const int cols[4] = {bl, 16 + 3 * bl, 17 + 3 * bl, 18 + 3 * bl};
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
+        const int ps = kt % kMfPosSlots;
+        if (!mbar_wait(&pfull[ps], (uint32_t)(kt / kMfPosSlots) & 1u, err, abort_flag)) break;
+        const float4 pb = spos[ps * TC_BK + 2 * bl];
+        const float rmb2 = spos[ps * TC_BK + 2 * bl + 1].x;
+        const int b = kt * 16 + bl;
+        const float d[3] = {pa.x - pb.x, pa.y - pb.y, pa.z - pb.z};
+        const float r2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+        const bool close = a == b || r2 < 25.0f * (wa + fmaxf(pb.w, rmb2));
+        float blk[4][4];
+        if (__any_sync(0xffffffffu, close)) {
+          if (a == b) radial::self_block_f(pa.w, rma2, mu_self, blk);
+          else radial::pair_block_f(pa, rma2, pb, rmb2, blk);
+        } else {
+          // r >= 5 R: G = 1/r, G'/r = -1/r^3, G'' = 2/r^3
+          const float ir = rsqrtf(r2), ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+          blk[0][0] = ir;
+#pragma unroll
+          for (int l = 0; l < 3; ++l) blk[0][1 + l] = ir3 * d[l];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            blk[1 + k][0] = -ir3 * d[k];
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+              blk[1 + k][1 + l] = (k == l ? ir3 : 0.0f) - 3.0f * ir5 * d[k] * d[l];
+          }
+        }
+        const bool real = a < N && b < N;
+        // the A stage is free once the MMA of step kt - TC_STAGES completed
+        if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
+        unsigned char* sth = base + s * STAGE;
+        unsigned char* stl = sth + A_TILE;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float t = real ? blk[u][v] * tscale : 0.0f;
+            uint16_t hv, lv;
+            if (F16) {
+              const __half h = __float2half_rn(t);
+              hv = __half_as_ushort(h);
+              lv = __half_as_ushort(__float2half_rn((t - __half2float(h)) * 2048.0f));
+            } else {
+              const __nv_bfloat16 h = __float2bfloat16_rn(t);
+              hv = __bfloat16_as_ushort(h);
+              lv = __bfloat16_as_ushort(__float2bfloat16_rn(t - __bfloat162float(h)));
+            }
+            const int r = rows[u], k = cols[v];
+            const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) +
+                                 (uint32_t)(k & 7) * 2u;
+            *reinterpret_cast<uint16_t*>(sth + off) = hv;
+            *reinterpret_cast<uint16_t*>(stl + off) = lv;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&full[s])) : "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&pempty[ps])) : "memory");
+          if (gw == 0) p_consumed = kt + 1;
+        }
       }
     }
     if (warp < 8) {
@@ -771,7 +886,16 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
       const bool ok = mbar_wait(accum, 0, err, abort_flag);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int wq = warp & 3;
-      const int row = i0 + wq * 32 + lane;
+      int row = i0 + wq * 32 + lane;
+      bool store = true;
+      if constexpr (MU == 1) {
+        // atom-blocked tile row -> charges-first row (charge of atom a0 + u, or dipole
+        // component (u - 32) % 3 of atom a0 + (u - 32) / 3); rows of padding atoms are skipped
+        const int u = wq * 32 + lane, a0 = blockIdx.y * 32;
+        const int atom = u < 32 ? a0 + u : a0 + (u - 32) / 3;
+        row = u < 32 ? atom : N + 3 * a0 + (u - 32);
+        store = atom < N;
+      }
       if (ok && !*abort_flag) {
         float* yr = Y + (size_t)row * ldy + c0;
 #pragma unroll 1
@@ -789,11 +913,13 @@ k_tc_mf(const float4* __restrict__ pos, float wmax,
           } else {
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           }
+          if (store) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<float4*>(yr + cc + 4 * q) =
-                make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            for (int q = 0; q < 8; ++q)
+              *reinterpret_cast<float4*>(yr + cc + 4 * q) =
+                  make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+          }
         }
       }
     }
@@ -848,10 +974,27 @@ __global__ void k_tc_mf_positions(const double* __restrict__ pos, const double* 
   o[6] = (float)(w * sc * sc);
 }
 
-template <int F16, int BN, int ST>
-cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& mXh,
-                              const CUtensorMap& mXl, int np, int ncols, float* Y, int ldy,
-                              float s1, float s2, int* err, cudaStream_t s) {
+// Positions for the wFQFmu pair kernel: per atom two float4 (x, y, z, R_q^2) and
+// (R_mu^2, 0, 0, 0) in bohr, unscaled; na atoms, those beyond n distinct dummies 3e4 + 64 (i - n)
+// bohr away along x (their blocks are zeroed by the kernel).
+__global__ void k_tc_mf4_positions(const double* __restrict__ pos, const double* __restrict__ Rq,
+                                   const double* __restrict__ Rmu, int n, int na, float4* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= na) return;
+  if (i < n) {
+    out[2 * i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2],
+                             (float)(Rq[i] * Rq[i]));
+    out[2 * i + 1] = make_float4((float)(Rmu[i] * Rmu[i]), 0.f, 0.f, 0.f);
+  } else {
+    out[2 * i] = make_float4((float)(3.0e4 + 64.0 * (i - n)), 0.f, 0.f, 1.f);
+    out[2 * i + 1] = make_float4(1.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int F16, int BN, int ST, int MU>
+cudaError_t launch_mf_variant(const float4* pos, float wmax, float tscale, int N, int mu_self,
+                              const CUtensorMap& mXh, const CUtensorMap& mXl, int np, int ncols,
+                              float* Y, int ldy, float s1, float s2, int* err, cudaStream_t s) {
   constexpr int smem = TcCfg<BN, ST>::SMEM + kMfPosSlots * kMfPosBytes;
   static_assert(smem <= 227 * 1024, "shared memory per CTA");
   {
@@ -863,65 +1006,30 @@ cudaError_t launch_mf_variant(const float4* pos, float wmax, const CUtensorMap& 
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
     if (!done.count(dev)) {
-      e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
+      e = cudaFuncSetAttribute(k_tc_mf<F16, BN, ST, MU>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
       done.insert(dev);
     }
   }
   dim3 grd(ncols / BN, np / TC_BM);
-  k_tc_mf<F16, BN, ST><<<grd, kMfThreads, smem, s>>>(pos, wmax, mXh, mXl, Y, ldy, np, s1, s2, err);
+  k_tc_mf<F16, BN, ST, MU><<<grd, kMfThreads, smem, s>>>(pos, wmax, tscale, N, mu_self, mXh, mXl,
+                                                         Y, ldy, np, s1, s2, err);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
-                                   int scale_exp, float4* out, cudaStream_t s, long long* nl) {
-  k_tc_mf_positions<<<(np + 255) / 256, 256, 0, s>>>(pos, Rq, n, np, std::ldexp(1.0, -scale_exp),
-                                                    reinterpret_cast<float*>(out));
-  ++*nl;
-  return cudaGetLastError();
-}
-
-namespace {
-// tile-width cache of the pair kernel: (device, np, ncols, f16) -> 256 or 128
+// tile-width cache of the pair kernels: (device, np, ncols, f16, model) -> 256 or 128
 std::mutex g_mf_mu;
-std::map<std::tuple<int, int, int, int>, int> g_mf_tune;
-}  // namespace
+std::map<std::tuple<int, int, int, int, int>, int> g_mf_tune;
 
-int tc_mf_tuned_width(int np, int ncols, bool f16) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-  std::lock_guard<std::mutex> lock(g_mf_mu);
-  auto it = g_mf_tune.find(std::make_tuple(dev, np, ncols, f16 ? 1 : 0));
-  return it == g_mf_tune.end() ? -1 : it->second;
-}
-
-cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
-                         const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
-                         int* err, cudaStream_t s, long long* nl) {
-  // shape contract as launch_tc_gemm: 128-row output tiles and 64-atom K steps (np % 128),
-  // 128- or 256-column operand tiles, 16-byte aligned operand rows and positions
-  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
-       reinterpret_cast<uintptr_t>(pos)) & 15)
-    return cudaErrorMisalignedAddress;
-  const float s1 = std::ldexp(1.0f, -(scale_exp + 8)), s2 = std::ldexp(1.0f, -(scale_exp + 19));
-  auto run = [&](int bn) -> cudaError_t {
-    CUtensorMap mXh, mXl;
-    if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
-      return cudaErrorInvalidValue;
-    if (f16)
-      return bn == 256 ? launch_mf_variant<1, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
-                       : launch_mf_variant<1, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
-    return bn == 256 ? launch_mf_variant<0, 256, 2>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
-                     : launch_mf_variant<0, 128, 3>(pos, wmax, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
-  };
-  // tile width: 256-column tiles share each generated T tile between more columns, 128-column
-  // tiles give more CTAs (fewer idle SMs in the last wave); the first call of a shape outside
-  // a stream capture times both (each writes the same Y) and keeps the faster
-  int bn = tc_mf_tuned_width(np, ncols, f16);
+// Launch run(bn) at the cached tile width of the shape, or, on the first call of a shape
+// outside a stream capture, time both widths (each writes the same Y) and keep the faster:
+// 256-column tiles share each generated T tile between more columns, 128-column tiles give
+// more CTAs (fewer idle SMs in the last wave).
+template <class Run>
+cudaError_t launch_tuned_width(int np, int ncols, bool f16, int mu, cudaStream_t s,
+                               long long* nl, Run run) {
+  int bn = tc_mf_tuned_width(np, ncols, f16, mu != 0);
   cudaError_t e = cudaSuccess;
   if (bn < 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -953,12 +1061,87 @@ cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* 
       e = cudaGetDevice(&dev);
       if (e != cudaSuccess) return e;
       std::lock_guard<std::mutex> lock(g_mf_mu);
-      g_mf_tune[std::make_tuple(dev, np, ncols, f16 ? 1 : 0)] = bn;
+      g_mf_tune[std::make_tuple(dev, np, ncols, f16 ? 1 : 0, mu)] = bn;
     }
   }
   e = run(bn);
   ++*nl;
   return e;
+}
+
+}  // namespace
+
+cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
+                                   int scale_exp, float4* out, cudaStream_t s, long long* nl) {
+  k_tc_mf_positions<<<(np + 255) / 256, 256, 0, s>>>(pos, Rq, n, np, std::ldexp(1.0, -scale_exp),
+                                                    reinterpret_cast<float*>(out));
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_mf4_positions(const double* pos, const double* Rq, const double* Rmu, int n,
+                                    int np, float4* out, cudaStream_t s, long long* nl) {
+  if (np % TC_BM || n > np / 4) return cudaErrorInvalidValue;
+  const int na = np / 4;
+  k_tc_mf4_positions<<<(na + 255) / 256, 256, 0, s>>>(pos, Rq, Rmu, n, na, out);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+int tc_mf_tuned_width(int np, int ncols, bool f16, bool mu) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lock(g_mf_mu);
+  auto it = g_mf_tune.find(std::make_tuple(dev, np, ncols, f16 ? 1 : 0, mu ? 1 : 0));
+  return it == g_mf_tune.end() ? -1 : it->second;
+}
+
+cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
+                         const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
+                         int* err, cudaStream_t s, long long* nl) {
+  // shape contract as launch_tc_gemm: 128-row output tiles and 64-atom K steps (np % 128),
+  // 128- or 256-column operand tiles, 16-byte aligned operand rows and positions
+  if (np % TC_BM || ncols % 128 || ldy % 4 || ldy < ncols) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+       reinterpret_cast<uintptr_t>(pos)) & 15)
+    return cudaErrorMisalignedAddress;
+  const float s1 = std::ldexp(1.0f, -(scale_exp + 8)), s2 = std::ldexp(1.0f, -(scale_exp + 19));
+  auto run = [&](int bn) -> cudaError_t {
+    CUtensorMap mXh, mXl;
+    if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
+      return cudaErrorInvalidValue;
+    if (f16)
+      return bn == 256 ? launch_mf_variant<1, 256, 2, 0>(pos, wmax, 1.0f, 0, 0, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                       : launch_mf_variant<1, 128, 3, 0>(pos, wmax, 1.0f, 0, 0, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+    return bn == 256 ? launch_mf_variant<0, 256, 2, 0>(pos, wmax, 1.0f, 0, 0, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s)
+                     : launch_mf_variant<0, 128, 3, 0>(pos, wmax, 1.0f, 0, 0, mXh, mXl, np, ncols, Y, ldy, 1.0f, 1.0f, err, s);
+  };
+  return launch_tuned_width(np, ncols, f16, 0, s, nl, run);
+}
+
+cudaError_t launch_tc_mf4(const float4* pos, int np, int N, int mu_self, const uint16_t* Xh,
+                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
+                          int* err, cudaStream_t s, long long* nl) {
+  // 128-row tiles of 32 atoms, K steps of 16 atoms: np % 128 == 0 and N <= np / 4
+  if (np % TC_BM || N < 1 || N > np / 4 || ncols % 128 || ldy % 4 || ldy < ncols)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Xh) | reinterpret_cast<uintptr_t>(Xl) |
+       reinterpret_cast<uintptr_t>(pos)) & 15)
+    return cudaErrorMisalignedAddress;
+  const float tscale = f16 ? std::ldexp(1.0f, scale_exp) : 1.0f;
+  const float s1 = f16 ? std::ldexp(1.0f, -(scale_exp + 8)) : 1.0f;
+  const float s2 = f16 ? std::ldexp(1.0f, -(scale_exp + 19)) : 1.0f;
+  auto run = [&](int bn) -> cudaError_t {
+    CUtensorMap mXh, mXl;
+    if (!make_map(&mXh, Xh, ncols, np, bn, f16) || !make_map(&mXl, Xl, ncols, np, bn, f16))
+      return cudaErrorInvalidValue;
+    if (f16)
+      return bn == 256 ? launch_mf_variant<1, 256, 2, 1>(pos, 0.f, tscale, N, mu_self, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                       : launch_mf_variant<1, 128, 3, 1>(pos, 0.f, tscale, N, mu_self, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+    return bn == 256 ? launch_mf_variant<0, 256, 2, 1>(pos, 0.f, tscale, N, mu_self, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s)
+                     : launch_mf_variant<0, 128, 3, 1>(pos, 0.f, tscale, N, mu_self, mXh, mXl, np, ncols, Y, ldy, s1, s2, err, s);
+  };
+  return launch_tuned_width(np, ncols, f16, 1, s, nl, run);
 }
 
 }  // namespace px

@@ -398,17 +398,22 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
   d.pos4tc = nullptr;
   d.tc_wmax = 0.f;
   if (d.matfree) {
-    // split precisions run the tensor-core pair kernel (wFQ): T scaled by 2^e before the
-    // fp16 split, 2^e max|T| <= 2^14 with max|T| = sqrt(2/pi) / min R_q (the diagonal)
-    if (split && model != PX_WFQ)
-      throw PxError{PX_ENOTIMPL, "matrix-free wFQFmu runs PX_FP32 or PX_FP64 matvecs"};
+    // split precisions run the tensor-core pair kernels: T scaled by 2^e before the fp16
+    // split, 2^e max|T| <= 2^14 with max|T| bounded from the smallest widths: T^qq by its
+    // diagonal sqrt(2/pi) / R_q; wFQFmu also |T^qmu| <= 0.43 / R^2 (R^2 = R_q^2 + R_mu^2)
+    // and |T^mumu| <= 0.76 / R^3 (R^2 = 2 R_mu^2; the self term 0.75 / R^3), both taken with
+    // margin (0.5, 1.0)
     if (split) {
-      double rq_min = types[0].Rq_bohr, rq_max = types[0].Rq_bohr;
+      double rq_min = types[0].Rq_bohr, rq_max = types[0].Rq_bohr, rm_min = types[0].Rmu_bohr;
       for (int t = 1; t < ntypes; ++t) {
         rq_min = std::min(rq_min, types[t].Rq_bohr);
         rq_max = std::max(rq_max, types[t].Rq_bohr);
+        rm_min = std::min(rm_min, types[t].Rmu_bohr);
       }
-      const double tmax = 0.7978845608028654 / rq_min;
+      double tmax = 0.7978845608028654 / rq_min;
+      if (model == PX_WFQFMU)
+        tmax = std::max({tmax, 0.5 / (rq_min * rq_min + rm_min * rm_min),
+                         1.0 / std::pow(2.0 * rm_min * rm_min, 1.5)});
       d.op_scale_exp = prec == PX_FP16SPLIT
                            ? std::max(-60, std::min(60, (int)std::floor(std::log2(16384.0 / tmax))))
                            : 0;
@@ -425,9 +430,13 @@ void set_structure(px_handle* h, int model, int N, const double* xyz, const int*
     }
     CU(px::launch_stage_pos4(d, s, &h->nl));
     if (split) {
+      // wFQ: np atoms of one float4; wFQFmu: np / 4 atoms of two
       CU(h->b_pos4tc.ensure(sizeof(float4) * (size_t)d.np));
       d.pos4tc = h->b_pos4tc.as<float4>();
-      CU(px::launch_tc_mf_positions(d.pos64, d.Rq, N, d.np, d.op_scale_exp, d.pos4tc, s, &h->nl));
+      if (model == PX_WFQFMU)
+        CU(px::launch_tc_mf4_positions(d.pos64, d.Rq, d.Rmu, N, d.np, d.pos4tc, s, &h->nl));
+      else
+        CU(px::launch_tc_mf_positions(d.pos64, d.Rq, N, d.np, d.op_scale_exp, d.pos4tc, s, &h->nl));
     }
   } else {
     CU(h->b_T64.ensure(np2 * sizeof(double)));
@@ -1111,6 +1120,22 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
       sa.kbar_in_y = (tc && d.op_has_kbar) || d.bem ? 1 : 0;
       sa.yscale = tc_f16 && d.op_has_kbar ? std::ldexp(1.0f, 12 - d.op_scale_exp) : 1.0f;
       sa.W = W;
+      // the tensor-core pair kernel's matvec Y = T X (split of X, then the kernel)
+      auto tc_mf_matvec = [&](cudaStream_t q, long long* cnt) -> cudaError_t {
+        cudaError_t e;
+        if (model == PX_WFQFMU) {
+          e = px::launch_split_xt_mu(X32, ldxa, np, ldxa, N, Xth, Xtl, tc_f16, q, cnt);
+          if (e == cudaSuccess)
+            e = px::launch_tc_mf4(d.pos4tc, np, N, d.mu_self, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
+                                  d.op_scale_exp, h->d_err, q, cnt);
+        } else {
+          e = px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt);
+          if (e == cudaSuccess)
+            e = px::launch_tc_mf(d.pos4tc, np, d.tc_wmax, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
+                                 d.op_scale_exp, h->d_err, q, cnt);
+        }
+        return e;
+      };
       // one Krylov step: j >= 0 eagerly (host-side step index, per-step poll), or
       // j < 0 under capture (kernels read the step index from the device)
       auto enqueue_step = [&](int j, cudaStream_t q, long long* cnt) {
@@ -1125,14 +1150,12 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           e1v = pool_event(h, prof_k++);
           CU(cudaEventRecord(e0v, q));
         }
-        if (d.matfree && model == PX_WFQFMU) {
+        if (d.matfree && tc) {
+          // tensor-core pair kernels: T tiles generated in shared memory as split planes
+          CU(tc_mf_matvec(q, cnt));
+        } else if (d.matfree && model == PX_WFQFMU) {
           if (lowp) CU(px::launch_sgemm_mf4(d.pos4f, d.rm2f, N, d.mu_self, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf4(d.pos4d, d.rm2d, N, d.mu_self, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
-        } else if (d.matfree && tc) {
-          // tensor-core pair kernel: T tiles generated in shared memory as split planes
-          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, q, cnt));
-          CU(px::launch_tc_mf(d.pos4tc, np, d.tc_wmax, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
-                              d.op_scale_exp, h->d_err, q, cnt));
         } else if (d.matfree) {
           if (lowp) CU(px::launch_sgemm_mf(d.pos4f, N, np, X32, ldxa, Y32, ldxa, ldxa, q, cnt));
           else CU(px::launch_dgemm_mf(d.pos4d, N, np, X64, ldxa, Y64, ldxa, ldxa, q, cnt));
@@ -1179,11 +1202,9 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
           CU(px::launch_tc_gemm(d.Thi, d.Tlo, np, Xth, Xtl, ldxa, Y32, ldxa, tc_f16, h->d_err, s,
                                 &nl, -1, nullptr));
         }
-        if (tc && d.matfree && px::tc_mf_tuned_width(np, ldxa, tc_f16) < 0) {
+        if (tc && d.matfree && px::tc_mf_tuned_width(np, ldxa, tc_f16, model == PX_WFQFMU) < 0) {
           // likewise the pair kernel's tile width
-          CU(px::launch_split_xt(X32, ldxa, np, ldxa, Xth, Xtl, tc_f16, s, &nl));
-          CU(px::launch_tc_mf(d.pos4tc, np, d.tc_wmax, Xth, Xtl, ldxa, Y32, ldxa, tc_f16,
-                              d.op_scale_exp, h->d_err, s, &nl));
+          CU(tc_mf_matvec(s, &nl));
         }
         uint32_t wmax_bits = 0;
         std::memcpy(&wmax_bits, &d.tc_wmax, sizeof(wmax_bits));
@@ -1206,7 +1227,7 @@ px_status solve(px_handle* h, int F, const double* omega_ev, const double* alpha
             (uint64_t)(uintptr_t)d.val64, (uint64_t)(uintptr_t)d.val32, (uint64_t)(uintptr_t)d.type,
             (uint64_t)(uintptr_t)d.pos4f, (uint64_t)(uintptr_t)d.pos4d,
             (uint64_t)d.op_has_kbar, (uint64_t)(int64_t)d.op_scale_exp, (uint64_t)d.bem,
-            (uint64_t)(uintptr_t)d.pos4tc, wmax_bits,
+            (uint64_t)(uintptr_t)d.pos4tc, wmax_bits, (uint64_t)d.mu_self,
             (uint64_t)(uintptr_t)dpart, (uint64_t)dpart_elems};
         CycleGraph* cg = nullptr;
         for (size_t k = 0; k < h->graphs.size(); ++k) {

@@ -189,17 +189,37 @@ int tc_tuned_variant(int np, int ncols, bool f16);
 cudaError_t launch_tc_mf(const float4* pos, int np, float wmax, const uint16_t* Xh,
                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
                          int* err, cudaStream_t s, long long* nl);
+// Matrix-free wFQFmu block matvec Y = T X on the tensor cores (Sec. 2.2): the 4 x 4 blocks
+// of T^qq / T^qmu / T^muq / T^mumu generated from the positions of launch_tc_mf4_positions
+// into shared memory as split planes (f16: 2^scale_exp T, 2^scale_exp max|T| <= 2^14; bf16:
+// scale_exp unused), contracted with the atom-blocked split operand of launch_split_xt_mu;
+// Y (charges-first rows, unscaled) is written for the rows of the N real atoms only.
+// mu_self: the Gaussian dipole self term on the T^mumu diagonal.  Tile widths and *err as
+// for launch_tc_mf; np % 128 == 0, N <= np / 4.
+cudaError_t launch_tc_mf4(const float4* pos, int np, int N, int mu_self, const uint16_t* Xh,
+                          const uint16_t* Xl, int ncols, float* Y, int ldy, bool f16, int scale_exp,
+                          int* err, cudaStream_t s, long long* nl);
 // The pair kernel's tile width chosen for a shape on the current device (256 or 128), or -1
-// before the first uncaptured call of that shape (which times both widths).
-int tc_mf_tuned_width(int np, int ncols, bool f16);
+// before the first uncaptured call of that shape (which times both widths); mu: wFQFmu.
+int tc_mf_tuned_width(int np, int ncols, bool f16, bool mu = false);
 // Its positions: pos (bohr) and Rq in internal order -> out (np / 2 atom pairs of 8 floats,
 // [-x0 -x1 -y0 -y1 -z0 -z1 w0 w1], w = R_q^2) scaled by 2^-scale_exp (w by 2^-2 scale_exp),
 // atoms n .. np-1 distinct far-away dummies.
 cudaError_t launch_tc_mf_positions(const double* pos, const double* Rq, int n, int np,
                                    int scale_exp, float4* out, cudaStream_t s, long long* nl);
+// wFQFmu positions: pos (bohr), Rq, Rmu in internal order -> out[2 a] = (x, y, z, R_q^2),
+// out[2 a + 1] = (R_mu^2, 0, 0, 0) for the np / 4 atoms of the padded tiles (atoms n and
+// beyond distinct far-away dummies).
+cudaError_t launch_tc_mf4_positions(const double* pos, const double* Rq, const double* Rmu, int n,
+                                    int np, float4* out, cudaStream_t s, long long* nl);
 // Xh[c][k], Xl[c][k] from X[k][c] (k < np, c < ncols): bf16 hi/lo, or fp16 hi/lo of 2^8 X.
 cudaError_t launch_split_xt(const float* X, int ldx, int np, int ncols, uint16_t* Xh,
                             uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);
+// The same split of a wFQFmu operand (charges-first rows of N atoms) into the atom-blocked K
+// order of launch_tc_mf4: K index 64 g + w is the charge of atom 16 g + w (w < 16), else
+// dipole component (w - 16) % 3 of atom 16 g + (w - 16) / 3; 0 beyond atom N.
+cudaError_t launch_split_xt_mu(const float* X, int ldx, int np, int ncols, int N, uint16_t* Xh,
+                               uint16_t* Xl, bool f16, cudaStream_t s, long long* nl);
 
 // ---------------------------------------------------------------- Krylov workspace
 // The Krylov basis V and the work vector W hold complex numbers in one of three

@@ -447,13 +447,13 @@ px_status px_submit(px_server* s, const px_request* r, uint64_t* req_id) {
   q->pol.assign(r->pol_dir, r->pol_dir + 3 * (size_t)r->n_pol);
   if (r->model != PX_WFQ) q->aib.assign(r->alpha_ib, r->alpha_ib + 2 * (size_t)r->n_types * r->n_freq);
   const size_t B = (size_t)q->F * q->P, N = q->N;
-  // materialised operators when they fit a share of the budget, else on the fly (wFQ)
+  // materialised operators when they fit a share of the budget, else on the fly
   const size_t fmat = footprint(s->opt, q->model, q->N, (int)B, true);
   const size_t ffree = footprint(s->opt, q->model, q->N, (int)B, false);
-  // (on the fly: every precision for wFQ, FP32 / FP64 for wFQFmu)
+  // (on the fly: every precision for wFQ and wFQFmu, FP32 / FP64 for its heterogeneous form)
   const bool split = s->opt.precision == PX_BF16SPLIT || s->opt.precision == PX_FP16SPLIT;
   if (s->opt.mode == PX_MODE_MATFREE || (s->opt.mode == PX_MODE_AUTO && fmat > s->budget / 2 &&
-                                         (q->model == PX_WFQ || !split))) {
+                                         (q->model != PX_WFQFMU_HETERO || !split))) {
     q->mode = PX_MODE_MATFREE;
     q->footprint = ffree;
   } else {

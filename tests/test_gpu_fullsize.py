@@ -68,12 +68,16 @@ def test_na_icosahedron_19931_matrix_free_all_600_columns(precision):
     _check(_solve(w), fidx, ref, w.tol)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
-def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies(precision):
+@pytest.mark.parametrize("precision,mode", [("fp32", None), ("fp16split", None),
+                                            ("fp16split", "matfree")])
+def test_ag_rod_3x3x10_wfqfmu_sampled_frequencies(precision, mode):
     """The rod as configured (FP32 matvec; all 150 frequencies x 3 directions solved),
-    and with the tensor-core FP16-split matvec, against oracle LU at three frequencies."""
+    with the tensor-core FP16-split matvec on the materialised operator, and with the
+    tensor-core pair kernel generating the 4 x 4 blocks on the fly, against oracle LU at
+    three frequencies."""
     w = S.ag_rod_3x3x10()
     w.precision = precision
+    w.mode = mode or w.mode
     fidx, ref = _golden("ag_rod_3x3x10", w.omega_ev.size, 3)
     _check(_solve(w), fidx, ref, w.tol)
 

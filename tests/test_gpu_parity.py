@@ -476,9 +476,12 @@ def test_matfree_wfqfmu_matches_materialised_rod():
                    np.linspace(2.5, 5.0, 12), np.eye(3), el.alpha_ib(np.linspace(2.5, 5.0, 12))[None, :])
     out_mf, _ = _run(w, precision="fp32", tol_rel=1e-9, mode="matfree")
     out_m, _ = _run(w, precision="fp32", tol_rel=1e-9, mode="materialised")
-    assert out_mf["ok"] and out_m["ok"]
-    num = np.linalg.norm(out_mf["alpha"] - out_m["alpha"], axis=1)
-    assert np.max(num / np.linalg.norm(out_m["alpha"], axis=1)) <= 1e-7
+    # the tensor-core pair kernel (FP16-split blocks generated in shared memory)
+    out_tc, _ = _run(w, precision="fp16split", tol_rel=1e-9, mode="matfree")
+    assert out_mf["ok"] and out_m["ok"] and out_tc["ok"]
+    for out in (out_mf, out_tc):
+        num = np.linalg.norm(out["alpha"] - out_m["alpha"], axis=1)
+        assert np.max(num / np.linalg.norm(out_m["alpha"], axis=1)) <= 1e-7
 
 
 def test_wfqfmu_rod_converges_with_dipole_preconditioner():
@@ -555,11 +558,45 @@ def test_matfree_tensor_core_matvec_against_the_oracle_operator():
     assert _alpha_err(outb, ref) <= 1e-2
 
 
-def test_matfree_tensor_core_wfqfmu_not_implemented():
-    from paper_2510_12731_gb300 import PxError, Solver
-    from paper_2510_12731_gb300 import _lib as L
-    w = S.small_cluster(element="Ag", radius=6.0, model="wfqfmu", nfreq=2)
-    with Solver(precision="fp16split", mode="matfree") as s:
-        with pytest.raises(PxError) as e:
-            s.set_structure(w.model, w.xyz_ang, w.type_idx, w.types)
-        assert e.value.status == L.PX_ENOTIMPL
+@pytest.mark.parametrize("precision", ["fp16split", "bf16split"])
+def test_matfree_tensor_core_wfqfmu_parity(precision):
+    """wFQFmu on the tensor-core pair kernel: every 4 x 4 block of T^qq / T^qmu / T^muq /
+    T^mumu (Sec. 2.2) generated in shared memory as split planes, in the atom-blocked order
+    (32-atom row tiles, 16-atom K steps); Ag sphere r = 9 A, N = 177 (6 row tiles and 12 K
+    steps, both ragged), refined to the oracle's LU."""
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfqfmu", nfreq=5, wmin=2.5, wmax=5.0)
+    assert w.natoms % 32 and w.natoms % 16
+    ref, _ = _oracle(w)
+    out, stats = _run(w, precision=precision, tol_rel=1e-9, mode="matfree")
+    assert stats["used_mode"] == 1 and out["ok"]
+    assert _alpha_err(out, ref) <= 1e-7
+    assert np.abs(out["q"] - ref.q).max() <= 1e-5 * np.abs(ref.q).max()
+    assert np.abs(out["mu"] - ref.mu).max() <= 1e-5 * np.abs(ref.mu).max()
+
+
+def test_matfree_tensor_core_wfqfmu_unequal_widths_and_self_term():
+    """R_mu != R_q (four pair widths per close block, and the far-field test over the
+    larger of the two) with the Gaussian dipole self term on the T^mumu diagonal, on the
+    FP16-split pair kernel."""
+    w = S.small_cluster(element="Au", radius=8.0, model="wfqfmu", nfreq=4, wmin=2.5, wmax=5.0)
+    w.types = [{**w.types[0], "Rmu_bohr": 0.8 * w.types[0]["Rq_bohr"]}]
+    st = M.structure_from_types(w.xyz_ang, w.type_idx, w.types)
+    ref = M.solve(st, w.model, w.omega_ev, w.pol_dirs, alpha_ib=w.alpha_ib, mu_self_term=True)
+    out, _ = _run(w, precision="fp16split", tol_rel=1e-9, mode="matfree", mu_self_term=1)
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-7
+
+
+def test_matfree_tensor_core_wfqfmu_before_refinement():
+    """One low-precision round (max_refine = 0): the unrefined solution carries only the
+    generated operator's error, ~22 bits per entry (FP16 split) or ~16 (BF16 split) times
+    the conditioning; a misplaced entry of a 4 x 4 block (swizzle, reordering, sign or
+    transposition of T^qmu / T^muq) gives O(1) errors instead."""
+    w = S.small_cluster(element="Ag", radius=9.0, model="wfqfmu", nfreq=5, wmin=2.5, wmax=5.0)
+    ref, _ = _oracle(w)
+    kw = dict(tol_rel=1e-9, inner_tol=1e-9, max_refine=0, mode="matfree", restart_m=300)
+    out16, _ = _run(w, precision="fp16split", **kw)
+    outb, _ = _run(w, precision="bf16split", **kw)
+    e16, eb = _alpha_err(out16, ref), _alpha_err(outb, ref)
+    assert e16 <= 1e-3 and eb <= 5e-2
+    assert e16 < eb
