@@ -805,72 +805,153 @@ k_tc_mf(const float4* __restrict__ pos, float wmax, float tscale, int N, int mu_
         }
       }
     } else {
-      // ---------------- wFQFmu generators: 4 x 4 blocks in the swizzled K-major layout
+      // ---------------- wFQFmu generators: rows of 4 x 4 blocks in the swizzled K-major layout
+      // Warp gw = 8 hh + 4 o + u writes row component u (0: charge, 1-3: dipole x, y, z) of
+      // the tile's 32 row atoms (one per lane) against column atoms kc .. kc + 3 of the step
+      // (kc = 8 o + 4 hh): per plane one 8-byte store of their 4 charge columns and a 16- and
+      // an 8-byte store of their 12 dipole columns.  Lanes of a warp differ in the row only,
+      // whose swizzle spreads them over the banks.
       const int gw = warp - 4;                       // 0 .. 15
-      const int al = 8 * (gw & 3) + (lane & 7);      // row atom of the tile, 0 .. 31
-      const int bl = 4 * (gw >> 2) + (lane >> 3);    // column atom of the K step, 0 .. 15
-      const int a = blockIdx.y * 32 + al;
+      const int u = gw & 3, o = (gw >> 2) & 1, hh = gw >> 3;
+      const int kdir = u - 1;                        // dipole component of a dipole row
+      const int a = blockIdx.y * 32 + lane;
       const float4 pa = __ldg(pos + 2 * a);
-      const float rma2 = __ldg(pos + 2 * a + 1).x;
-      const float wa = fmaxf(pa.w, rma2);
-      // rows: the charge of atom al, then its dipole components; K: likewise for atom bl
-      const int rows[4] = {al, 32 + 3 * al, 33 + 3 * al, 34 + 3 * al};
-      const int cols[4] = {bl, 16 + 3 * bl, 17 + 3 * bl, 18 + 3 * bl};
+      const float wma = __ldg(pos + 2 * a + 1).x;
+      const float wa = fmaxf(pa.w, wma);
+      const int r = u == 0 ? lane : 32 + 3 * lane + kdir;
+      const int kc = 8 * o + 4 * hh;                 // charge columns kc .. kc + 3
+      const int kd = 16 + 24 * o + 12 * hh;          // dipole columns kd .. kd + 11
+      auto soff = [&](int k) -> uint32_t {
+        return (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
+      };
+      // hh = 0: dipole columns as 8 + 4; hh = 1: as 4 + 8 (16-byte chunks start at kd + 4)
+      const uint32_t oc = soff(kc), od1 = soff(kd), od2 = soff(kd + (hh ? 4 : 8));
+      const float qself = radial::kSqrt2OverPiF * rsqrtf(pa.w);
+      const float vself = mu_self ? 4.0f / (3.0f * 1.7724538509055159f) * rsqrtf(2.0f * wma) /
+                                        (2.0f * wma)
+                                  : 0.0f;
+      const float2 k2048 = make_float2(2048.0f, 2048.0f), km1 = make_float2(-1.0f, -1.0f);
+      auto split2 = [&](float v0, float v1, uint32_t& hw, uint32_t& lw) {
+        const float2 tv = make_float2(v0, v1);
+        if (F16) {
+          const __half2 h = __float22half2_rn(tv);
+          const float2 hf = __half22float2(h);
+          const __half2 l = __float22half2_rn(__fmul2_rn(__ffma2_rn(hf, km1, tv), k2048));
+          hw = *reinterpret_cast<const uint32_t*>(&h);
+          lw = *reinterpret_cast<const uint32_t*>(&l);
+        } else {
+          const __nv_bfloat162 h = __float22bfloat162_rn(tv);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(hf, km1, tv));
+          hw = *reinterpret_cast<const uint32_t*>(&h);
+          lw = *reinterpret_cast<const uint32_t*>(&l);
+        }
+      };
       for (int kt = 0; kt < nk; ++kt) {
         const int s = kt % TC_STAGES;
         const uint32_t ph = (uint32_t)(kt / TC_STAGES) & 1u;
         const int ps = kt % kMfPosSlots;
         if (!mbar_wait(&pfull[ps], (uint32_t)(kt / kMfPosSlots) & 1u, err, abort_flag)) break;
-        const float4 pb = spos[ps * TC_BK + 2 * bl];
-        const float rmb2 = spos[ps * TC_BK + 2 * bl + 1].x;
-        const int b = kt * 16 + bl;
-        const float d[3] = {pa.x - pb.x, pa.y - pb.y, pa.z - pb.z};
-        const float r2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
-        const bool close = a == b || r2 < 25.0f * (wa + fmaxf(pb.w, rmb2));
-        float blk[4][4];
+        float4 pb[4];
+        float wmb[4], d[4][3], r2[4];
+        bool close = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          pb[j] = spos[ps * TC_BK + 2 * (kc + j)];
+          wmb[j] = spos[ps * TC_BK + 2 * (kc + j) + 1].x;
+          d[j][0] = pa.x - pb[j].x;
+          d[j][1] = pa.y - pb[j].y;
+          d[j][2] = pa.z - pb[j].z;
+          r2[j] = fmaf(d[j][0], d[j][0], fmaf(d[j][1], d[j][1], d[j][2] * d[j][2]));
+          close |= a == kt * 16 + kc + j || r2[j] < 25.0f * (wa + fmaxf(pb[j].w, wmb[j]));
+        }
+        float e[4][4];   // e[j][0]: charge column of atom kc + j; e[j][1 + l]: its dipole l
         if (__any_sync(0xffffffffu, close)) {
-          if (a == b) radial::self_block_f(pa.w, rma2, mu_self, blk);
-          else radial::pair_block_f(pa, rma2, pb, rmb2, blk);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (a == kt * 16 + kc + j) {
+              // diagonal block: the T^qq self limit, the T^mumu self term
+              e[j][0] = u == 0 ? qself : 0.0f;
+#pragma unroll
+              for (int l = 0; l < 3; ++l) e[j][1 + l] = (u != 0 && l == kdir) ? vself : 0.0f;
+            } else {
+              const float rj = sqrtf(r2[j]), ir = 1.0f / rj;
+              float G, G1, G2, g, t0, t2;
+              if (u == 0) {
+                // T^qq (widths R_q,a R_q,b); T^qmu_l = -G'/r (R_q,a R_mu,b) d_l
+                radial::eval_f(rj, sqrtf(pa.w + pb[j].w), G, G1, G2, g);
+                if (pb[j].w != wmb[j]) radial::eval_f(rj, sqrtf(pa.w + wmb[j]), t0, G1, t2, g);
+                e[j][0] = G;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) e[j][1 + l] = -G1 * d[j][l];
+              } else {
+                // T^muq_k = G'/r (R_mu,a R_q,b) d_k; T^mumu_kl from G'/r and G'' (R_mu,a R_mu,b)
+                radial::eval_f(rj, sqrtf(wma + wmb[j]), t0, G1, G2, g);
+                float G1m = G1;
+                if (pb[j].w != wmb[j]) radial::eval_f(rj, sqrtf(wma + pb[j].w), t0, G1m, t2, g);
+                const float dk = kdir == 0 ? d[j][0] : (kdir == 1 ? d[j][1] : d[j][2]);
+                e[j][0] = G1m * dk;
+                const float rhk = dk * ir;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                  const float rr = rhk * (d[j][l] * ir);
+                  e[j][1 + l] = -(G2 * rr + G1 * ((l == kdir ? 1.0f : 0.0f) - rr));
+                }
+              }
+            }
+          }
         } else {
-          // r >= 5 R: G = 1/r, G'/r = -1/r^3, G'' = 2/r^3
-          const float ir = rsqrtf(r2), ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
-          blk[0][0] = ir;
 #pragma unroll
-          for (int l = 0; l < 3; ++l) blk[0][1 + l] = ir3 * d[l];
+          for (int j = 0; j < 4; ++j) {
+            // r >= 5 R: G = 1/r, G'/r = -1/r^3, G'' = 2/r^3
+            const float ir = rsqrtf(r2[j]), ir3 = ir * ir * ir;
+            if (u == 0) {
+              e[j][0] = ir;
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            blk[1 + k][0] = -ir3 * d[k];
+              for (int l = 0; l < 3; ++l) e[j][1 + l] = ir3 * d[j][l];
+            } else {
+              const float dk = kdir == 0 ? d[j][0] : (kdir == 1 ? d[j][1] : d[j][2]);
+              const float ir5 = ir3 * ir * ir;
+              e[j][0] = -ir3 * dk;
 #pragma unroll
-            for (int l = 0; l < 3; ++l)
-              blk[1 + k][1 + l] = (k == l ? ir3 : 0.0f) - 3.0f * ir5 * d[k] * d[l];
+              for (int l = 0; l < 3; ++l)
+                e[j][1 + l] = (l == kdir ? ir3 : 0.0f) - 3.0f * ir5 * dk * d[j][l];
+            }
           }
         }
-        const bool real = a < N && b < N;
+        // blocks with a padding atom are zero; the rest scaled by 2^e
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool real = a < N && kt * 16 + kc + j < N;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[j][c] = real ? e[j][c] * tscale : 0.0f;
+        }
+        // charge columns j = 0..3; dipole columns in the order (atom j, component l) = 3 j + l
+        uint32_t ch[2], cl[2], dh[6], dl[6];
+        split2(e[0][0], e[1][0], ch[0], cl[0]);
+        split2(e[2][0], e[3][0], ch[1], cl[1]);
+        split2(e[0][1], e[0][2], dh[0], dl[0]);
+        split2(e[0][3], e[1][1], dh[1], dl[1]);
+        split2(e[1][2], e[1][3], dh[2], dl[2]);
+        split2(e[2][1], e[2][2], dh[3], dl[3]);
+        split2(e[2][3], e[3][1], dh[4], dl[4]);
+        split2(e[3][2], e[3][3], dh[5], dl[5]);
         // the A stage is free once the MMA of step kt - TC_STAGES completed
         if (kt >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, err, abort_flag)) break;
         unsigned char* sth = base + s * STAGE;
         unsigned char* stl = sth + A_TILE;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const float t = real ? blk[u][v] * tscale : 0.0f;
-            uint16_t hv, lv;
-            if (F16) {
-              const __half h = __float2half_rn(t);
-              hv = __half_as_ushort(h);
-              lv = __half_as_ushort(__float2half_rn((t - __half2float(h)) * 2048.0f));
-            } else {
-              const __nv_bfloat16 h = __float2bfloat16_rn(t);
-              hv = __bfloat16_as_ushort(h);
-              lv = __bfloat16_as_ushort(__float2bfloat16_rn(t - __bfloat162float(h)));
-            }
-            const int r = rows[u], k = cols[v];
-            const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) +
-                                 (uint32_t)(k & 7) * 2u;
-            *reinterpret_cast<uint16_t*>(sth + off) = hv;
-            *reinterpret_cast<uint16_t*>(stl + off) = lv;
-          }
+        *reinterpret_cast<uint2*>(sth + oc) = make_uint2(ch[0], ch[1]);
+        *reinterpret_cast<uint2*>(stl + oc) = make_uint2(cl[0], cl[1]);
+        if (hh == 0) {
+          *reinterpret_cast<uint4*>(sth + od1) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+          *reinterpret_cast<uint4*>(stl + od1) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+          *reinterpret_cast<uint2*>(sth + od2) = make_uint2(dh[4], dh[5]);
+          *reinterpret_cast<uint2*>(stl + od2) = make_uint2(dl[4], dl[5]);
+        } else {
+          *reinterpret_cast<uint2*>(sth + od1) = make_uint2(dh[0], dh[1]);
+          *reinterpret_cast<uint2*>(stl + od1) = make_uint2(dl[0], dl[1]);
+          *reinterpret_cast<uint4*>(sth + od2) = make_uint4(dh[2], dh[3], dh[4], dh[5]);
+          *reinterpret_cast<uint4*>(stl + od2) = make_uint4(dl[2], dl[3], dl[4], dl[5]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
