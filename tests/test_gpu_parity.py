@@ -600,3 +600,38 @@ def test_matfree_tensor_core_wfqfmu_before_refinement():
     e16, eb = _alpha_err(out16, ref), _alpha_err(outb, ref)
     assert e16 <= 1e-3 and eb <= 5e-2
     assert e16 < eb
+
+
+def test_matfree_tensor_core_wfqfmu_single_atom_is_interband_polarisability():
+    """One atom: the charge row has no conductance and the dipole row is the interband
+    term alone, so alpha = alpha^IB I (Eq. 7) through a tile of 1 real and 31 padding
+    atoms and a K step of padding only."""
+    w = _single("wfqfmu", [[0.0, 0.0, 0.0]])
+    out, stats = _run(w, precision="fp16split", tol_rel=1e-10, mode="matfree")
+    assert stats["used_mode"] == 1 and out["ok"]
+    for f in range(3):
+        assert np.allclose(out["alpha"][f], w.alpha_ib[0, f] * np.eye(3), rtol=1e-10, atol=0)
+
+
+def test_matfree_tensor_core_wfqfmu_two_atoms():
+    d_ang = 2.892
+    w = _single("wfqfmu", [[-d_ang / 2, 0, 0], [d_ang / 2, 0, 0]])
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp16split", tol_rel=1e-10, mode="matfree")
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-8
+
+
+@pytest.mark.parametrize("n", [16, 32, 33])
+def test_matfree_tensor_core_wfqfmu_tile_boundaries(n):
+    """N = 16 (one K step of real atoms, one of padding), 32 (exactly one row tile and
+    two full K steps) and 33 (one real atom in a second row tile and a third K step):
+    the n atoms of an Ag lattice nearest the origin, against the oracle's LU."""
+    el = S.ELEMENTS["Ag"]
+    xyz = S.sphere("fcc", el.a_ang, 8.0)
+    xyz = xyz[np.argsort(np.linalg.norm(xyz, axis=1), kind="stable")[:n]]
+    w = _single("wfqfmu", xyz, nfreq=4)
+    ref, _ = _oracle(w)
+    out, _ = _run(w, precision="fp16split", tol_rel=1e-10, mode="matfree")
+    assert out["ok"]
+    assert _alpha_err(out, ref) <= 1e-8
